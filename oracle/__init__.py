@@ -1,0 +1,268 @@
+"""FP64 CPU oracle for the path-traced light-transport estimator (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the benchmark's
+CPU-baseline leg are the only callers.  The product path never imports this package, and this
+package never imports the product package: the two share nothing but the seeded scene
+generators' arrays that the caller passes in.
+
+The arithmetic lives in ``oracle.c`` (plain C99, FP64, OpenMP over paths); this module only
+compiles it with gcc and marshals numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MAT_LAMBERT, MAT_GGX, MAT_DIELECTRIC = 0, 1, 2
+BSDF_CODES = {"lambert": 0, "ggx": 1, "ggx_invalid": 2, "reflect": 3, "refract": 4, "tir": 5}
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into _build/liboracle.so (portable flags: no -march, no fast-math,
+    no FP contraction, so x86 and Arm builds round identically)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-Wall", "-Wno-unused-function", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _f(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB_PATH)
+            vp, u32, u64, i64, i32, f32, f64 = (C.c_void_p, C.c_uint32, C.c_uint64, C.c_int64,
+                                                C.c_int, C.c_float, C.c_double)
+            L.or_pcg_hash.restype = u32
+            L.or_pcg_hash.argtypes = [u32]
+            L.or_path_key.restype = u32
+            L.or_path_key.argtypes = [u64, u32, u32]
+            L.or_u01.restype = f64
+            L.or_u01.argtypes = [u32, u32, u32]
+            L.or_u01_batch.argtypes = [u64, vp, vp, vp, vp, i64, vp]
+            L.or_scene_create.restype = vp
+            L.or_scene_create.argtypes = [vp, i64, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp]
+            L.or_scene_destroy.argtypes = [vp]
+            L.or_scene_set_materials.argtypes = [vp, vp, vp]
+            L.or_scene_n_lights.restype = i64
+            L.or_scene_n_lights.argtypes = [vp]
+            L.or_scene_light_area.restype = f64
+            L.or_scene_light_area.argtypes = [vp]
+            L.or_intersect_batch.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp, vp]
+            L.or_occluded_batch.argtypes = [vp, vp, vp, vp, i64, i32, vp]
+            L.or_bsdf_eval.argtypes = [u32, vp, f64, vp, vp, vp, vp]
+            L.or_bsdf_sample.restype = i32
+            L.or_bsdf_sample.argtypes = [u32, vp, f64, f64, vp, vp, vp, f64, f64, f64, vp, vp, vp]
+            L.or_fresnel_dielectric.restype = f64
+            L.or_fresnel_dielectric.argtypes = [f64, f64, f64]
+            L.or_ggx_D.restype = f64
+            L.or_ggx_D.argtypes = [f64, f64]
+            L.or_ggx_G1.restype = f64
+            L.or_ggx_G1.argtypes = [f64, f64]
+            L.or_render_paths.argtypes = [vp, vp, vp, vp, f32, u32, u32, u32, u32, u64, u32, f64, i32,
+                                          vp, i64, i32, vp, vp, i32, vp, vp, vp, vp]
+            L.or_render_pixels.argtypes = [vp, vp, vp, vp, f32, u32, u32, u32, u32, u64, u32, f64, i32,
+                                           vp, i64, i32, vp, vp]
+            L.or_trace_rays.argtypes = [vp, vp, vp, vp, i64, u32, u32, f64, i32, i32, vp, vp, i32, vp, vp]
+            L.or_max_tangents.restype = i32
+            _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------- random numbers
+def pcg_hash(v: int) -> int:
+    return int(lib().or_pcg_hash(v & 0xFFFFFFFF))
+
+
+def path_key(seed: int, pixel: int, sample: int) -> int:
+    return int(lib().or_path_key(seed, pixel, sample))
+
+
+def u01(seed, pixel, sample, bounce, dim) -> np.ndarray:
+    """Uniforms for arrays of (pixel, sample, bounce, dim) under one seed."""
+    px, sm, bo, dm = (_f(np.broadcast_to(a, np.broadcast(pixel, sample, bounce, dim).shape), np.uint32)
+                      for a in (pixel, sample, bounce, dim))
+    out = np.empty(px.shape, np.float64)
+    lib().or_u01_batch(seed, _p(px), _p(sm), _p(bo), _p(dm), px.size, _p(out))
+    return out
+
+
+# ---------------------------------------------------------------- BSDFs (pins)
+def bsdf_eval(mtype, albedo, roughness, n, wo, wi) -> np.ndarray:
+    out = np.empty(3)
+    lib().or_bsdf_eval(mtype, _p(_f(albedo, np.float64)), roughness, _p(_f(n, np.float64)),
+                       _p(_f(wo, np.float64)), _p(_f(wi, np.float64)), _p(out))
+    return out
+
+
+def bsdf_sample(mtype, albedo, roughness, ior, n, ng, wo, u5, u6, u7):
+    wi = np.empty(3)
+    w = np.empty(3)
+    code = np.zeros(1, np.int32)
+    ok = lib().or_bsdf_sample(mtype, _p(_f(albedo, np.float64)), roughness, ior, _p(_f(n, np.float64)),
+                              _p(_f(ng, np.float64)), _p(_f(wo, np.float64)), u5, u6, u7, _p(wi), _p(w),
+                              _p(code))
+    return bool(ok), wi, w, int(code[0])
+
+
+def fresnel_dielectric(ci, eta_i, eta_t) -> float:
+    return float(lib().or_fresnel_dielectric(ci, eta_i, eta_t))
+
+
+def ggx_D(roughness, cos_h) -> float:
+    return float(lib().or_ggx_D(roughness, cos_h))
+
+
+def ggx_G1(roughness, cos_v) -> float:
+    return float(lib().or_ggx_G1(roughness, cos_v))
+
+
+# ---------------------------------------------------------------- scenes
+class Scene:
+    """Oracle scene: triangles (FP32 input, FP64 inside), materials, environment, plain BVH."""
+
+    def __init__(self, verts, tris, tri_mat, mat_type, mat_albedo, mat_emission, mat_roughness,
+                 mat_ior, env):
+        self._keep = [_f(verts, np.float32).reshape(-1, 3), _f(tris, np.uint32).reshape(-1, 3),
+                      _f(tri_mat, np.uint32), _f(mat_type, np.uint32),
+                      _f(mat_albedo, np.float32).reshape(-1, 3), _f(mat_emission, np.float32),
+                      _f(mat_roughness, np.float32), _f(mat_ior, np.float32), _f(env, np.float32)]
+        v, t, tm, mt, ma, me, mr, mi, ev = self._keep
+        self.n_tris = t.shape[0]
+        self.n_mats = mt.shape[0]
+        self.h = lib().or_scene_create(_p(v), v.shape[0], _p(t), t.shape[0], _p(tm), mt.shape[0],
+                                       _p(mt), _p(ma), _p(me), _p(mr), _p(mi), _p(ev))
+
+    @classmethod
+    def from_dict(cls, sc: dict) -> "Scene":
+        return cls(sc["verts"], sc["tris"], sc["tri_mat"], sc["mat_type"], sc["mat_albedo"],
+                   sc["mat_emission"], sc["mat_roughness"], sc["mat_ior"], sc["env"])
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().or_scene_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_lights(self) -> int:
+        return int(lib().or_scene_n_lights(self.h))
+
+    @property
+    def light_area(self) -> float:
+        return float(lib().or_scene_light_area(self.h))
+
+    def set_materials(self, albedo, emission):
+        a = _f(albedo, np.float32).reshape(-1, 3)
+        e = _f(emission, np.float32)
+        self._keep[4], self._keep[5] = a, e
+        lib().or_scene_set_materials(self.h, _p(a), _p(e))
+
+    def intersect(self, o, d, use_bvh=True):
+        o = _f(o, np.float64).reshape(-1, 3)
+        d = _f(d, np.float64).reshape(-1, 3)
+        n = o.shape[0]
+        t, u, v = np.empty(n), np.empty(n), np.empty(n)
+        prim = np.empty(n, np.int64)
+        lib().or_intersect_batch(self.h, _p(o), _p(d), n, int(use_bvh), _p(t), _p(prim), _p(u), _p(v))
+        return t, prim, u, v
+
+    def occluded(self, o, d, tmax, use_bvh=True):
+        o = _f(o, np.float64).reshape(-1, 3)
+        d = _f(d, np.float64).reshape(-1, 3)
+        tm = _f(tmax, np.float64).reshape(-1)
+        out = np.empty(o.shape[0], np.int32)
+        lib().or_occluded_batch(self.h, _p(o), _p(d), _p(tm), o.shape[0], int(use_bvh), _p(out))
+        return out.astype(bool)
+
+    @staticmethod
+    def _cam(cam: dict):
+        return (_f(cam["eye"], np.float32), _f(cam["target"], np.float32), _f(cam["up"], np.float32),
+                float(cam["vfov_deg"]), int(cam["width"]), int(cam["height"]))
+
+    def render_paths(self, cam, spp, max_depth, seed, path_ids, rr_start=3, rr_fixed=0.0,
+                     use_bvh=True, dir_albedo=None, dir_emission=None, n_threads=0):
+        """Per-path radiance, optional directional derivatives, branch signatures, ray counts."""
+        eye, tgt, up, fov, W, H = self._cam(cam)
+        ids = _f(path_ids, np.uint64).reshape(-1)
+        n = ids.size
+        L = np.empty((n, 3))
+        sig = np.empty(n, np.uint32)
+        rays = np.zeros(2, np.uint64)
+        nd = 0 if dir_albedo is None else int(np.asarray(dir_albedo).shape[0])
+        if nd:
+            da = _f(dir_albedo, np.float64).reshape(nd, self.n_mats, 3)
+            de = _f(dir_emission, np.float64).reshape(nd, self.n_mats)
+            dL = np.empty((n, nd, 3))
+            args = (nd, _p(da), _p(de))
+        else:
+            dL = None
+            args = (0, None, None)
+        lib().or_render_paths(self.h, _p(eye), _p(tgt), _p(up), fov, W, H, spp, max_depth, seed,
+                              rr_start, float(rr_fixed), int(use_bvh), _p(ids), n, *args, n_threads,
+                              _p(L), _p(dL) if dL is not None else None, _p(sig), _p(rays))
+        return {"L": L, "dL": dL, "sig": sig, "rays": rays}
+
+    def render_pixels(self, cam, spp, max_depth, seed, pixels=None, rr_start=3, rr_fixed=0.0,
+                      use_bvh=True, n_threads=0):
+        """Mean radiance of the listed pixels (all pixels when None); returns (img (n,3), rays)."""
+        eye, tgt, up, fov, W, H = self._cam(cam)
+        if pixels is None:
+            pixels = np.arange(W * H, dtype=np.uint32)
+        px = _f(pixels, np.uint32).reshape(-1)
+        img = np.empty((px.size, 3))
+        rays = np.zeros(2, np.uint64)
+        lib().or_render_pixels(self.h, _p(eye), _p(tgt), _p(up), fov, W, H, spp, max_depth, seed,
+                               rr_start, float(rr_fixed), int(use_bvh), _p(px), px.size, n_threads,
+                               _p(img), _p(rays))
+        return img, rays
+
+    def trace_rays(self, o, d, keys, max_depth, rr_start=1 << 30, rr_fixed=0.0, use_bvh=True,
+                   dir_albedo=None, dir_emission=None, n_threads=0):
+        o = _f(o, np.float64).reshape(-1, 3)
+        d = _f(d, np.float64).reshape(-1, 3)
+        k = _f(keys, np.uint32).reshape(-1)
+        n = o.shape[0]
+        L = np.empty((n, 3))
+        nd = 0 if dir_albedo is None else int(np.asarray(dir_albedo).shape[0])
+        if nd:
+            da = _f(dir_albedo, np.float64).reshape(nd, self.n_mats, 3)
+            de = _f(dir_emission, np.float64).reshape(nd, self.n_mats)
+            dL = np.empty((n, nd, 3))
+            lib().or_trace_rays(self.h, _p(o), _p(d), _p(k), n, max_depth, rr_start, float(rr_fixed),
+                                int(use_bvh), nd, _p(da), _p(de), n_threads, _p(L), _p(dL))
+            return L, dL
+        lib().or_trace_rays(self.h, _p(o), _p(d), _p(k), n, max_depth, rr_start, float(rr_fixed),
+                            int(use_bvh), 0, None, None, n_threads, _p(L), None)
+        return L, None
