@@ -1,0 +1,380 @@
+"""Benchmark: Mrays/s and ms/frame of the wavefront and megakernel estimators at 1080p, 1 spp, and
+the backward/forward time ratio, on the ~1.15M-triangle procedural spheres scene (seeded, synthetic;
+it stands in for the paper's glTF benchmark scene, which is not available).
+
+One step = one wavefront frame + one megakernel frame + one path-replay adjoint pass of that frame
+(all rows of the hot path), seed = step index.  Inputs are resident in device memory; L2 is flushed
+(256 MiB write) between steps outside the timed events.  Rays = extension + shadow rays counted on
+the device.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py --workload batch      # 64 scenes in one persistent launch vs 64 renders
+Under torchrun (N > 1) each rank renders its own frames (seed offset by rank, no collective on the
+data path: weak scaling); the barrier and max-over-ranks timing are the only communication.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s and ms/frame (1080p, 1 spp) wavefront vs megakernel; bwd/fwd time ratio"
+WORKLOAD = ("procedural spheres scene: 200 level-4 icospheres + 256x256-quad ground (1,155,072 tris), "
+            "8 emissive quads + constant environment, 1920x1080, 1 spp, max depth 5, roulette from bounce 3; "
+            "step = wavefront frame + megakernel frame + adjoint pass")
+KERNEL_SOURCES = ["paper_2605_27323_gb300/csrc/pt_kernels.cu", "paper_2605_27323_gb300/csrc/pt_device.cuh",
+                  "paper_2605_27323_gb300/csrc/pt_trace.cuh"]
+# Algorithmic bytes per unit of each stage (queue/state traffic, "Roofline").
+BYTES_PER_UNIT = {
+    "extend": 40,      # per extension ray: ray o|id + d|flags (32 B) read, hit record (8 B) written
+    "shadow": 80,      # per shadow ray: o|tmax + d|id (32 B) + contribution (16 B) read, L rw (32 B)
+    "shade": 184,      # per active path: ray+tp (48) + hit (8) + L rw (32) + next ray (48) + shadow (48)
+    "megakernel": 12,  # per path: radiance written (scene reads amortise to ~0 per path)
+    "adjoint": 12,     # per path: gradient image read
+}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def load_traffic(kernel: str):
+    """Per-unit DRAM bytes of `kernel` from the committed ncu summary, if it was taken on the
+    current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    e = d.get(kernel)
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return float(e["dram_bytes_per_unit"])
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region (SM clock, max clock, throttle reasons)."""
+
+    def __init__(self, index: int):
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader",
+                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                mx = max(mx, float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workload():
+    from paper_2605_27323_gb300 import scenes
+    return scenes.spheres_scene(seed=0)
+
+
+def cpu_baseline(sc, budget_s=12.0, threads=None):
+    """The FP64 oracle as it stands, on a bounded sample of the same frame (evenly strided pixels)."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    osc = oracle.Scene.from_dict(sc)
+    cam = sc["camera"]
+    n_pix = cam["width"] * cam["height"]
+    probe = np.arange(0, n_pix, max(1, n_pix // 4000), dtype=np.uint32)
+    t0 = time.perf_counter()
+    _, rays = osc.render_pixels(cam, 1, sc["max_depth"], 0, probe, rr_start=3, n_threads=threads)
+    dt = time.perf_counter() - t0
+    n = int(min(n_pix, max(len(probe), len(probe) * budget_s / max(dt, 1e-3))))
+    pix = np.linspace(0, n_pix - 1, n).astype(np.uint32)
+    t0 = time.perf_counter()
+    _, rays = osc.render_pixels(cam, 1, sc["max_depth"], 0, pix, rr_start=3, n_threads=threads)
+    dt = time.perf_counter() - t0
+    total = int(rays[0] + rays[1])
+    return {"value": total / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n} evenly strided pixels of the 1920x1080 frame, 1 spp, depth 5 ({total} rays, "
+                      f"{dt:.1f} s, FP64, OpenMP)", "ms_per_frame_extrapolated": dt * 1e3 * n_pix / n}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle timed on the host cores, same metric and config."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    sc = build_workload()
+    import oracle
+    osc = oracle.Scene.from_dict(sc)
+    cam = sc["camera"]
+    threads = os.cpu_count() or 1
+    n_pix = cam["width"] * cam["height"]
+    per_step = 20000
+    rays_total, t_total = 0, 0.0
+    for step in range(args.warmup + args.steps):
+        pix = (np.arange(per_step, dtype=np.uint64) * 7919 + step * 104729) % n_pix
+        t0 = time.perf_counter()
+        _, rays = osc.render_pixels(cam, 1, sc["max_depth"], step, pix.astype(np.uint32), rr_start=3,
+                                    n_threads=threads)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            rays_total += int(rays[0] + rays[1])
+            t_total += dt
+    value = rays_total / t_total / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_total * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{per_step} pixels per step"},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} strided pixels of the 1080p frame per step, 1 spp, depth 5"},
+            "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_2605_27323_gb300 as pt
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sc = build_workload()
+    g = pt.Scene.from_dict(sc)
+    cam, spp, depth = sc["camera"], sc["spp"], sc["max_depth"]
+    W, H = cam["width"], cam["height"]
+    n_paths = W * H * spp
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(123)
+    grad = torch.from_numpy(rng.uniform(-1, 1, size=(H, W, 3)).astype(np.float32)).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    wf_opts = dict(mode="wavefront", rr_start=3, sort=args.sort, profile=True)
+    mk_opts = dict(mode="megakernel", rr_start=3, profile=True)
+
+    def step(seed, timing):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        g.render(cam, spp, depth, seed, **wf_opts)
+        ev[1].record(stream)
+        s_wf = g.stats() if timing else None
+        ev_mk = torch.cuda.Event(enable_timing=True)
+        ev_mk.record(stream)
+        g.render(cam, spp, depth, seed, **mk_opts)
+        ev[2].record(stream)
+        s_mk = g.stats() if timing else None
+        ev_bw = torch.cuda.Event(enable_timing=True)
+        ev_bw.record(stream)
+        g.backward(cam, spp, depth, seed, grad, rr_start=3, profile=True)
+        ev[3].record(stream)
+        s_bw = g.stats() if timing else None
+        flush.fill_(seed & 0xFF)                     # L2 flush, outside the timed events
+        return ev, ev_mk, ev_bw, s_wf, s_mk, s_bw
+
+    for w in range(args.warmup):
+        step(10_000 + w + rank * 1_000_000, False)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local) if rank == 0 else None
+    torch.cuda.synchronize()
+    recs = [step(s + rank * 1_000_000, True) for s in range(args.steps)]
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if clocks else None
+    wf_ms = [r[0][0].elapsed_time(r[0][1]) for r in recs]
+    mk_ms = [r[1].elapsed_time(r[0][2]) for r in recs]
+    bw_ms = [r[2].elapsed_time(r[0][3]) for r in recs]
+    wf_rays = [r[3]["extension_rays"] + r[3]["shadow_rays"] for r in recs]
+    mk_rays = [r[4]["extension_rays"] + r[4]["shadow_rays"] for r in recs]
+    # the adjoint re-traces exactly the forward paths' rays
+    step_ms = [a + b + c for a, b, c in zip(wf_ms, mk_ms, bw_ms)]
+    total_ms = float(np.sum(step_ms))
+    total_rays = float(np.sum(wf_rays) + np.sum(mk_rays) + np.sum(mk_rays))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        r_ = torch.tensor([total_rays], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(r_, op=torch.distributed.ReduceOp.SUM)
+        total_ms, total_rays = float(t.item()), float(r_.item())
+    value = total_rays / (total_ms * 1e-3) / 1e6
+
+    # stage times from the library's events on the launch stream (timed region)
+    stage = {"extend": sum(r[3]["ms_extend"] for r in recs), "shade": sum(r[3]["ms_shade"] for r in recs),
+             "shadow": sum(r[3]["ms_shadow"] for r in recs), "sort": sum(r[3]["ms_sort"] for r in recs),
+             "raygen": sum(r[3]["ms_raygen"] for r in recs), "reduce": sum(r[3]["ms_reduce"] for r in recs),
+             "megakernel": sum(r[4]["ms_megakernel"] for r in recs),
+             "adjoint": sum(r[5]["ms_adjoint"] for r in recs)}
+    launches = {"extend": sum(r[3]["launches_extend"] for r in recs),
+                "shadow": sum(r[3]["launches_shadow"] for r in recs),
+                "megakernel": args.steps, "adjoint": args.steps,
+                "shade": sum(r[3]["launches_extend"] for r in recs)}
+    units = {"extend": sum(r[3]["extension_rays"] for r in recs), "shadow": sum(r[3]["shadow_rays"] for r in recs),
+             "shade": sum(r[3]["extension_rays"] for r in recs), "megakernel": n_paths * args.steps,
+             "adjoint": n_paths * args.steps}
+    dom = max(("extend", "shadow", "shade", "megakernel", "adjoint"), key=lambda k: stage[k])
+    peak, peak_src = load_peaks()
+    alg_bytes = BYTES_PER_UNIT[dom] * units[dom]
+    achieved = alg_bytes / (stage[dom] * 1e-3) / 1e9
+    tr = load_traffic(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src,
+                "traffic": (tr * units[dom] / launches[dom]) if tr is not None else None,
+                "algorithmic_bytes_per_launch": alg_bytes / launches[dom],
+                "avg_launch_ms": stage[dom] / launches[dom]}
+    gpu_launches = sum(r[3]["launches_total"] + r[4]["launches_total"] + r[5]["launches_total"] for r in recs)
+
+    wf_frame = float(np.mean(wf_ms))
+    mk_frame = float(np.mean(mk_ms))
+    out = None
+    if rank == 0:
+        e2e = measure_e2e(g, cam, spp, depth, grad, args, wf_opts, mk_opts) if world == 1 else None
+        line = {
+            "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "resolution": [W, H], "spp": spp, "max_depth": depth,
+                       "triangles": int(g.info()["n_tris"]), "sort": args.sort,
+                       "l2": "flushed between steps (256 MiB write), outside the timed events"},
+            "wavefront": {"mrays_s": float(np.sum(wf_rays)) / (np.sum(wf_ms) * 1e-3) / 1e6, "ms_per_frame": wf_frame,
+                          "rays_per_frame": float(np.mean(wf_rays))},
+            "megakernel": {"mrays_s": float(np.sum(mk_rays)) / (np.sum(mk_ms) * 1e-3) / 1e6,
+                           "ms_per_frame": mk_frame, "rays_per_frame": float(np.mean(mk_rays))},
+            "wf_over_mk_speedup": mk_frame / wf_frame,
+            "bwd_over_fwd": float(np.mean(bw_ms)) / min(wf_frame, mk_frame),
+            "stage_ms_per_step": {k: v / args.steps for k, v in stage.items()},
+            "roofline": roofline,
+            "gpu_launches": int(gpu_launches),
+            "paper_context": "paper: wavefront 1.16x over megakernel (73.6 vs 64.7 FPS, RTX 3060 Ti, Vulkan RT cores)",
+        }
+        if e2e:
+            line["e2e"] = e2e
+        if clk:
+            line["clocks"] = clk
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(sc)
+        out = line
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def measure_e2e(g, cam, spp, depth, grad, args, wf_opts, mk_opts):
+    """Same step through the public API with host buffers: the gradient image is copied in from
+    pinned memory, both images and the gradients are read back, all inside the timed region."""
+    import torch
+    W, H = cam["width"], cam["height"]
+    h_wf = torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
+    h_mk = torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
+    h_grad = grad.cpu().pin_memory()
+    h_ga = torch.empty((g.n_mats, 3), dtype=torch.float32).pin_memory()
+    h_ge = torch.empty((g.n_mats,), dtype=torch.float32).pin_memory()
+    wf = {k: v for k, v in wf_opts.items() if k != "profile"}
+    mk = {k: v for k, v in mk_opts.items() if k != "profile"}
+    stream = torch.cuda.current_stream()
+    ms, rays = 0.0, 0.0
+    for s in range(args.warmup + max(3, args.steps // 2)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.render(cam, spp, depth, s, out=h_wf, **wf)
+        r = g.stats()
+        g.render(cam, spp, depth, s, out=h_mk, **mk)
+        r2 = g.stats()
+        d_grad = h_grad.to("cuda", non_blocking=True)
+        ga, ge = g.backward(cam, spp, depth, s, d_grad, rr_start=3)
+        h_ga.copy_(ga, non_blocking=True)
+        h_ge.copy_(ge, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if s >= args.warmup:
+            ms += e0.elapsed_time(e1)
+            rays += r["extension_rays"] + r["shadow_rays"] + 2 * (r2["extension_rays"] + r2["shadow_rays"])
+    return {"value": rays / (ms * 1e-3) / 1e6, "unit": "Mrays/s",
+            "h2d_bytes_per_step": int(h_grad.numel() * 4),
+            "d2h_bytes_per_step": int(h_wf.numel() * 4 + h_mk.numel() * 4 + h_ga.numel() * 4 + h_ge.numel() * 4)}
+
+
+def run_batch(args):
+    raise SystemExit("batched workload: not available yet")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="frame", choices=["frame", "batch"])
+    ap.add_argument("--sort", default="none", choices=["none", "type", "material"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    if args.workload == "batch":
+        run_batch(args)
+        return
+    run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

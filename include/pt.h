@@ -1,0 +1,184 @@
+/*
+ * pt.h -- C ABI of the GB300 path tracer (libpt.so).
+ *
+ * The library renders triangle scenes with the Monte Carlo light-transport estimator of
+ * "Megakernel vs Wavefront GPU Path Tracing": Eq. 1 (light transport equation) estimated by
+ * Eq. 2 (mean of f/p over samples) along paths whose throughput follows Eq. 3, with the forward
+ * path-tracing loop of Sec. 2.2, the shadow-evaluation stage of Sec. 3 (next-event estimation)
+ * and Russian roulette (Sec. 3.1).  It runs the estimator two ways (Sec. 2.2 / 2.3): a megakernel
+ * (one thread traces one path to termination) and a wavefront pipeline (ray generation, extend
+ * traversal, material-sorted shading, shadow traversal, accumulation) linked by device queues
+ * with the two-slot active count of Sec. 3.1.  It also provides a path-replay adjoint (gradients
+ * of an image loss with respect to per-material albedo and emission) and batched rendering of
+ * many scenes in one persistent wavefront.
+ *
+ * Conventions for every entry point:
+ *  - Pointers prefixed d_ are device pointers on the current CUDA device unless stated "host or
+ *    device" (then the library detects host memory and stages it through its own device buffer).
+ *    The caller owns them; the library never frees them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls are
+ *    asynchronous on that stream unless stated otherwise; errors in arguments are reported
+ *    synchronously by the return value, device-side faults (traversal step cap, queue overflow)
+ *    are recorded in a device status word and reported by pt_get_stats / pt_scene_sync.
+ *  - Nothing throws; every failure returns a pt_status and sets a thread-local message
+ *    (pt_last_error).
+ *  - Images are row-major H x W x 3 float32 (linear RGB), row 0 at the top.  Path p = pixel * spp
+ *    + sample, pixel = y * W + x.  Per-path buffers are N_p x 3 float32, N_p = W * H * spp.
+ */
+#ifndef PT_H
+#define PT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PT_OK = 0,
+    PT_ERR_INVALID_ARG = 1,     /* a pointer, size or option is out of range */
+    PT_ERR_OOM = 2,             /* device or host allocation failed */
+    PT_ERR_CUDA = 3,            /* a CUDA runtime call failed (message in pt_last_error) */
+    PT_ERR_QUEUE_OVERFLOW = 4,  /* a wavefront queue append exceeded its capacity */
+    PT_ERR_TRAVERSAL_LIMIT = 5, /* a BVH traversal exceeded its step cap or stack */
+    PT_ERR_TIMEOUT = 6,         /* a bounded device wait gave up */
+    PT_ERR_UNSUPPORTED = 7      /* valid but not supported (e.g. backward depth > 32) */
+} pt_status;
+
+/* Material models (Sec. 3: shading stage; the paper's layered OpenPBR model is reduced to these
+ * three lobes).  Le = emission * (1, 1, 1), one-sided (front face by winding). */
+enum { PT_MAT_LAMBERT = 0, PT_MAT_GGX = 1, PT_MAT_DIELECTRIC = 2 };
+
+typedef struct {
+    uint32_t type;      /* PT_MAT_* */
+    float albedo[3];    /* Lambert albedo / GGX F0 (Schlick) / dielectric tint, each in [0, 1] */
+    float emission;     /* scalar emitted radiance, >= 0; > 0 at creation puts the material's
+                           triangles in the light list */
+    float roughness;    /* GGX: alpha = max(roughness^2, 1e-4) */
+    float ior;          /* dielectric index of refraction (> 0) */
+    uint32_t flags;     /* reserved, 0 */
+} pt_material;          /* 32 bytes */
+
+/* Pinhole camera of the ray-generation stage (Sec. 2.3): ray through (x + u0, y + u1). */
+typedef struct {
+    float eye[3], target[3], up[3];
+    float vfov_deg;     /* vertical field of view, (0, 180) */
+    uint32_t width, height;
+} pt_camera;
+
+enum { PT_MODE_MEGAKERNEL = 0, PT_MODE_WAVEFRONT = 1 };
+enum { PT_SORT_NONE = 0, PT_SORT_TYPE = 1, PT_SORT_MATERIAL = 2 };
+enum {
+    PT_FLAG_PROFILE = 1u,       /* time each stage with CUDA events on the launch stream; read the
+                                   times with pt_get_stats after the stream completes */
+    PT_FLAG_NO_GRAPH = 2u       /* wavefront: launch the bounce loop directly, not as a CUDA graph */
+};
+
+typedef struct {
+    uint32_t mode;              /* PT_MODE_* */
+    uint32_t rr_start;          /* first bounce with Russian roulette (Sec. 3.1); >= max_depth: off */
+    float rr_fixed;             /* > 0: fixed survival probability; 0: q = clamp(max(tp), .05, .95) */
+    uint32_t sort_mode;         /* wavefront: PT_SORT_* key sort before shading */
+    uint32_t block_size;        /* threads per block: 0 = default, else a multiple of 32 in [64, 1024] */
+    uint32_t flags;             /* PT_FLAG_* */
+    uint64_t queue_capacity;    /* wavefront: paths per wave; 0 = all paths in one wave */
+    uint32_t* d_path_sig;       /* optional device N_p u32: per-path branch signature (testing) */
+    uint64_t reserved;
+} pt_render_opts;
+
+typedef struct {
+    uint64_t extension_rays;    /* closest-hit queries traced (device-counted) */
+    uint64_t shadow_rays;       /* shadow (any-hit) queries traced */
+    uint64_t paths;
+    uint32_t bounces;           /* entries valid in active[] */
+    uint32_t status;            /* device status word: 0 or a pt_status */
+    uint64_t active[64];        /* wavefront: active paths entering each bounce (all waves) */
+    /* PT_FLAG_PROFILE: total milliseconds per stage of the last profiled call, and launches */
+    float ms_raygen, ms_extend, ms_sort, ms_shade, ms_shadow, ms_reduce, ms_megakernel, ms_adjoint;
+    uint32_t launches_extend, launches_shadow, launches_total;
+    float ms_total;
+} pt_stats;
+
+typedef struct pt_scene pt_scene;
+
+/* Build a scene from host triangles (Sec. 3: scene data packed on the host into GPU-friendly
+ * buffers and uploaded).  verts: host n_verts x 3 float; tris: host n_tris x 3 uint32 vertex
+ * indices; tri_material: host n_tris uint32 (< n_mats); mats: host n_mats pt_material;
+ * env_radiance: host 3 floats (radiance of rays that leave the scene).  Builds a binned-SAH BVH on
+ * the host (multithreaded), packs 64-byte nodes and 48-byte triangle records, and uploads them
+ * with cudaMemcpyAsync on `cuda_stream` (the call returns after the upload is enqueued and the host
+ * staging is released, i.e. it synchronises that stream).  n_tris may be 0 (every ray misses).
+ * Errors: PT_ERR_INVALID_ARG (NULL pointers with non-zero counts, index out of range, negative or
+ * non-finite parameters), PT_ERR_OOM, PT_ERR_CUDA.  The scene is owned by the library until
+ * pt_scene_destroy. */
+pt_status pt_scene_create(const float* verts, uint32_t n_verts, const uint32_t* tris, uint32_t n_tris,
+                          const uint32_t* tri_material, const pt_material* mats, uint32_t n_mats,
+                          const float env_radiance[3], void* cuda_stream, pt_scene** out);
+
+/* Replace per-material albedo (device n_mats x 3) and emission (device n_mats) -- the
+ * differentiable parameters -- asynchronously on `stream`.  Either pointer may be NULL (kept).
+ * The light list stays the one fixed at creation. */
+pt_status pt_scene_set_materials(pt_scene* scene, const float* d_albedo, const float* d_emission, void* stream);
+
+/* Render one image: W x H pixels, spp samples each, paths of at most max_depth vertices (Sec. 2.2
+ * step 5), random numbers keyed by `seed`.  d_out_rgb: H x W x 3 float, host or device (host: the
+ * library copies the result back and synchronises `stream`).  d_path_L_or_null: device N_p x 3
+ * float per-path radiance (NULL to skip).  opts may be NULL (wavefront, RR from bounce 3, no
+ * sort).  The image is img[p] = (1/spp) * sum over samples s = 0..spp-1 (in order) of L[p, s];
+ * megakernel and wavefront produce the same image. */
+pt_status pt_render(pt_scene* scene, const pt_camera* cam, uint32_t spp, uint32_t max_depth, uint64_t seed,
+                    const pt_render_opts* opts, float* d_out_rgb, float* d_path_L_or_null, void* stream);
+
+/* Path-replay adjoint: accumulate d(loss)/d(albedo) and d(loss)/d(emission) for the image that
+ * pt_render produces with the same arguments, given d_grad_rgb = d(loss)/d(image) (H x W x 3,
+ * host or device).  Paths are re-traced from the random numbers (no path storage); Russian
+ * roulette probabilities are treated as constants.  d_grad_albedo (device n_mats x 3) and
+ * d_grad_emission (device n_mats) are ACCUMULATED into (the caller zeroes them).  max_depth <= 32
+ * (else PT_ERR_UNSUPPORTED). */
+pt_status pt_render_backward(pt_scene* scene, const pt_camera* cam, uint32_t spp, uint32_t max_depth,
+                             uint64_t seed, const pt_render_opts* opts, const float* d_grad_rgb,
+                             float* d_grad_albedo, float* d_grad_emission, void* stream);
+
+/* Render n scenes in one persistent wavefront (batched mode): scenes[i] with cams[i] and spp[i]
+ * into d_out[i] (device H_i x W_i x 3).  Same estimator and random numbers as pt_render, so each
+ * image equals its standalone render.  The bounce loop is captured once in a CUDA graph and
+ * replayed per wave; opts->queue_capacity bounds the paths in flight (0 = automatic). */
+pt_status pt_render_batch(pt_scene* const* scenes, const pt_camera* cams, const uint32_t* spp, uint32_t n,
+                          uint32_t max_depth, uint64_t seed, const pt_render_opts* opts, float* const* d_out,
+                          void* stream);
+
+/* Autotuner for pt_render_batch: times the batch under candidate {queue capacity, block size, sort
+ * mode} settings on `stream` (synchronous) and writes the fastest into *best (mode = wavefront).
+ * `base` supplies the remaining fields (may be NULL).  *best_ms receives its time (may be NULL). */
+pt_status pt_autotune_batch(pt_scene* const* scenes, const pt_camera* cams, const uint32_t* spp, uint32_t n,
+                            uint32_t max_depth, uint64_t seed, const pt_render_opts* base, float* const* d_out,
+                            void* stream, pt_render_opts* best, float* best_ms);
+
+/* Closest-hit query for n rays (the extend stage as a standalone call): d_rays device n x 8 float
+ * (o.xyz, tmin(ignored, 0), d.xyz, pad); outputs d_t (n float, +inf on miss) and d_prim (n int32,
+ * original triangle id or -1). */
+pt_status pt_trace_closest(pt_scene* scene, const float* d_rays, uint32_t n, float* d_t, int32_t* d_prim,
+                           void* stream);
+
+/* Statistics of the last render/backward/batch call on this scene (synchronises the stream used by
+ * that call).  status reports device-side faults. */
+pt_status pt_get_stats(pt_scene* scene, pt_stats* out);
+
+/* Random numbers exactly as the renderer draws them: out[i] = u(seed, pixel[i], sample[i],
+ * bounce[i], dim[i]) in [0, 1) on a 2^-24 grid (device arrays, n entries). */
+pt_status pt_debug_rng(uint64_t seed, const uint32_t* d_pixel, const uint32_t* d_sample, const uint32_t* d_bounce,
+                       const uint32_t* d_dim, uint32_t n, float* d_out, void* stream);
+
+/* Scene facts: triangle, node, light counts, total light area, device bytes held. */
+pt_status pt_scene_info(const pt_scene* scene, uint64_t* n_tris, uint64_t* n_nodes, uint64_t* n_lights,
+                        float* light_area, uint64_t* device_bytes);
+
+const char* pt_status_string(pt_status status);
+const char* pt_last_error(void);     /* thread-local message of the last failure on this thread */
+void pt_scene_destroy(pt_scene* scene);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PT_H */

@@ -638,7 +638,13 @@ typedef struct {
     int use_bvh;
 } ropts;
 
-static uint32_t sig_mix(uint32_t s, uint32_t e) { return or_pcg_hash(s ^ e); }
+/* Branch signature: XOR over the path's events of hash(hash((bounce << 4) | kind) ^ value), so the
+ * order in which a pipeline learns the events does not matter.  kind 0: hit triangle id (miss:
+ * 0xFFFFFFFF); 1: NEE (light index << 2 | shadow ray cast << 1 | visible); 2: BSDF outcome code;
+ * 3: Russian roulette survival. */
+static uint32_t sig_event(uint32_t bounce, uint32_t kind, uint32_t value) {
+    return or_pcg_hash(or_pcg_hash((bounce << 4) | kind) ^ value);
+}
 
 /* Light index j with cdf[j-1] <= u < cdf[j] (first entry whose inclusive cdf exceeds u). */
 static int64_t pick_light(const or_scene* s, double u) {
@@ -658,7 +664,7 @@ static void trace(const or_scene* s, v3 o, v3 d, uint32_t key, const ropts* op, 
     int nd = dr->nd;
     dc tp = dc_const(1, 1, 1), L = dc_const(0, 0, 0);
     int prev_delta = 1;
-    uint32_t sig = 0x9E3779B9u;
+    uint32_t sig = 0u;
     for (uint32_t b = 0; b < op->max_depth; ++b) {
         /* step 2: extend the path to the next scattering point */
         double t, hu, hv;
@@ -666,10 +672,10 @@ static void trace(const or_scene* s, v3 o, v3 d, uint32_t key, const ropts* op, 
         int64_t tri = closest_hit(s, o, d, op->use_bvh, &t, &hu, &hv);
         if (tri < 0) {
             L = dc_add(L, dc_mul(tp, dc_const(s->env[0], s->env[1], s->env[2]), nd), nd);
-            sig = sig_mix(sig, 0xFFFFFFFFu);
+            sig ^= sig_event(b, 0, 0xFFFFFFFFu);
             break;
         }
-        sig = sig_mix(sig, (uint32_t)tri);
+        sig ^= sig_event(b, 0, (uint32_t)tri);
         v3 ng = nrm(cross(sub(s->p1[tri], s->p0[tri]), sub(s->p2[tri], s->p0[tri])));
         v3 x = add(o, scl(d, t));
         int64_t mi = s->mat[tri];
@@ -710,12 +716,12 @@ static void trace(const or_scene* s, v3 o, v3 d, uint32_t key, const ropts* op, 
                     L = dc_add(L, dc_scale(dc_mul(dc_mul(tp, f, nd), mat_emission(s, s->mat[lt], dr), nd), g, nd), nd);
                 }
             }
-            sig = sig_mix(sig, 0x40000000u ^ (((uint32_t)j << 2) | (cast << 1) | vis));
+            sig ^= sig_event(b, 1, ((uint32_t)j << 2) | (cast << 1) | vis);
         }
         /* step 4: sample a new direction and update the throughput (Eq. 3) */
         bsample bs = bsdf_sample(m, a, n, ng, wo, or_u01(key, b, D_LOBE), or_u01(key, b, D_DIR0),
                                  or_u01(key, b, D_DIR1), nd);
-        sig = sig_mix(sig, 0x20000000u | (uint32_t)bs.code);
+        sig ^= sig_event(b, 2, (uint32_t)bs.code);
         if (!bs.valid) break;
         tp = dc_mul(tp, bs.weight, nd);
         prev_delta = bs.delta;
@@ -729,7 +735,7 @@ static void trace(const or_scene* s, v3 o, v3 d, uint32_t key, const ropts* op, 
                 q = q < 0.05 ? 0.05 : (q > 0.95 ? 0.95 : q);
             }
             int survive = or_u01(key, b, D_RR) < q;
-            sig = sig_mix(sig, 0x10000000u | (uint32_t)survive);
+            sig ^= sig_event(b, 3, (uint32_t)survive);
             if (!survive) break;
             tp = dc_scale(tp, 1.0 / q, nd);
         }

@@ -1,0 +1,777 @@
+// pt_api.cpp -- the C ABI of include/pt.h: argument validation, scene packing and upload, workspace
+// management, and the host side of the megakernel / wavefront / adjoint / batched pipelines.
+// Every call is asynchronous on the caller's stream except where the header says otherwise.
+#include "pt.h"
+
+#include <cuda_runtime_api.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bvh_build.h"
+#include "pt_launch.h"
+#include "pt_types.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+pt_status fail(pt_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define PT_CUDA(expr)                                                                            \
+    do {                                                                                         \
+        cudaError_t e_ = (expr);                                                                 \
+        if (e_ != cudaSuccess) return fail(PT_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define PT_TRY(expr)                   \
+    do {                               \
+        pt_status s_ = (expr);         \
+        if (s_ != PT_OK) return s_;    \
+    } while (0)
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    pt_status ensure(size_t want) {
+        if (bytes >= want && p) return PT_OK;
+        release();
+        if (want == 0) want = 256;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return fail(PT_ERR_OOM, "cudaMalloc(%zu bytes) failed: %s", want, cudaGetErrorString(e));
+        }
+        bytes = want;
+        return PT_OK;
+    }
+    template <class T>
+    T* as() const {
+        return static_cast<T*>(p);
+    }
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool is_device_ptr(const void* ptr) {
+    if (!ptr) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool finite3(const float* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+int sm_count(int device) {
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(device);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = 1;
+    }
+    cache[device] = n;
+    return n;
+}
+
+int blocks_per_sm(int which, int block) {
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, int> cache;
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_pair(which, block);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int n = pt::max_blocks_per_sm(which, block);
+    cache[key] = n;
+    return n;
+}
+
+enum Stage { ST_RAYGEN, ST_EXTEND, ST_SORT, ST_SHADE, ST_SHADOW, ST_REDUCE, ST_MEGA, ST_ADJOINT, ST_COUNT };
+
+}  // namespace
+
+struct pt_scene {
+    int device = 0;
+    uint64_t n_tris = 0, n_nodes = 0, n_lights = 0;
+    uint32_t n_mats = 0;
+    float light_area = 0.f;
+    float env[3] = {0.f, 0.f, 0.f};
+    DevBuf nodes, tris, mats, lights, cdf, status;
+    // workspaces (grown on demand, kept until destroy)
+    DevBuf wf;
+    uint64_t wf_capacity = 0;
+    pt::WfBuffers wfb{};
+    DevBuf pathL, img_stage, grad_stage, counters;
+    cudaStream_t last_stream = nullptr;
+    uint32_t last_mode = 0;
+    uint64_t last_paths = 0;
+    uint32_t launches = 0;     // kernel launches issued by the last call
+    // profiling: event pairs recorded on the launch stream
+    struct Ev {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<Ev> events;
+    size_t ev_used = 0;
+    bool profiling = false;
+    std::mutex mu;
+
+    ~pt_scene() {
+        for (Ev& e : events) {
+            cudaEventDestroy(e.a);
+            cudaEventDestroy(e.b);
+        }
+    }
+
+    pt::DevScene view() const {
+        pt::DevScene s;
+        s.nodes = nodes.as<const float4>();
+        s.tris = tris.as<const float4>();
+        s.mats = mats.as<const pt::DevMat>();
+        s.lights = lights.as<const float4>();
+        s.light_cdf = cdf.as<const float>();
+        s.n_lights = (uint32_t)n_lights;
+        s.light_area = light_area;
+        s.env_r = env[0];
+        s.env_g = env[1];
+        s.env_b = env[2];
+        s.n_mats = n_mats;
+        s.status = status.as<uint32_t>();
+        return s;
+    }
+    uint32_t* counts() const { return counters.as<uint32_t>(); }
+    unsigned long long* hist() const { return reinterpret_cast<unsigned long long*>(counters.as<char>() + 256); }
+    unsigned long long* rays() const { return hist() + 128; }
+
+    pt_status ensure_counters() { return counters.ensure(256 + 8 * 130); }
+
+    // One allocation carved into the wavefront arrays for `cap` paths per wave.
+    pt_status ensure_wf(uint64_t cap) {
+        if (wf_capacity >= cap && wf.p) return PT_OK;
+        size_t q = align256(cap * 16), h = align256(cap * 8), k = align256(cap * 4);
+        size_t total = 6 * q + h + 2 * k + align256(pt::kMaxSortKeys * 4) + 3 * q + q;
+        PT_TRY(wf.ensure(total));
+        char* base = wf.as<char>();
+        size_t off = 0;
+        auto take = [&](size_t n) {
+            char* r = base + off;
+            off += n;
+            return r;
+        };
+        for (int i = 0; i < 2; ++i) {
+            wfb.q_o[i] = reinterpret_cast<float4*>(take(q));
+            wfb.q_d[i] = reinterpret_cast<float4*>(take(q));
+            wfb.q_tp[i] = reinterpret_cast<float4*>(take(q));
+        }
+        wfb.hit = reinterpret_cast<float2*>(take(h));
+        wfb.keys = reinterpret_cast<uint32_t*>(take(k));
+        wfb.perm = reinterpret_cast<uint32_t*>(take(k));
+        wfb.bucket = reinterpret_cast<uint32_t*>(take(align256(pt::kMaxSortKeys * 4)));
+        wfb.s_o = reinterpret_cast<float4*>(take(q));
+        wfb.s_d = reinterpret_cast<float4*>(take(q));
+        wfb.s_c = reinterpret_cast<float4*>(take(q));
+        wfb.L = reinterpret_cast<float4*>(take(q));
+        wf_capacity = cap;
+        return PT_OK;
+    }
+
+    pt_status ev_begin(int stage, cudaStream_t st, size_t& idx) {
+        if (!profiling) return PT_OK;
+        if (ev_used == events.size()) {
+            Ev e{stage, nullptr, nullptr};
+            PT_CUDA(cudaEventCreate(&e.a));
+            PT_CUDA(cudaEventCreate(&e.b));
+            events.push_back(e);
+        }
+        idx = ev_used++;
+        events[idx].stage = stage;
+        PT_CUDA(cudaEventRecord(events[idx].a, st));
+        return PT_OK;
+    }
+    pt_status ev_end(size_t idx, cudaStream_t st) {
+        if (!profiling) return PT_OK;
+        PT_CUDA(cudaEventRecord(events[idx].b, st));
+        return PT_OK;
+    }
+};
+
+namespace {
+
+pt_status make_camera(const pt_camera* cam, pt::DevCamera& c) {
+    if (!cam) return fail(PT_ERR_INVALID_ARG, "camera is NULL");
+    if (cam->width == 0 || cam->height == 0) return fail(PT_ERR_INVALID_ARG, "camera width/height must be > 0");
+    if ((uint64_t)cam->width * cam->height >= (1ull << 32))
+        return fail(PT_ERR_INVALID_ARG, "camera has more than 2^32 pixels");
+    if (!(cam->vfov_deg > 0.f && cam->vfov_deg < 180.f))
+        return fail(PT_ERR_INVALID_ARG, "vfov_deg must be in (0, 180)");
+    if (!finite3(cam->eye) || !finite3(cam->target) || !finite3(cam->up))
+        return fail(PT_ERR_INVALID_ARG, "camera vectors must be finite");
+    double e[3], w[3], u[3], v[3];
+    for (int k = 0; k < 3; ++k) {
+        e[k] = cam->eye[k];
+        w[k] = (double)cam->eye[k] - (double)cam->target[k];
+    }
+    double wl = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    if (!(wl > 0)) return fail(PT_ERR_INVALID_ARG, "camera eye equals target");
+    for (double& x : w) x /= wl;
+    double up[3] = {cam->up[0], cam->up[1], cam->up[2]};
+    u[0] = up[1] * w[2] - up[2] * w[1];
+    u[1] = up[2] * w[0] - up[0] * w[2];
+    u[2] = up[0] * w[1] - up[1] * w[0];
+    double ul = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    if (!(ul > 0)) return fail(PT_ERR_INVALID_ARG, "camera up is parallel to the view direction");
+    for (double& x : u) x /= ul;
+    v[0] = w[1] * u[2] - w[2] * u[1];
+    v[1] = w[2] * u[0] - w[0] * u[2];
+    v[2] = w[0] * u[1] - w[1] * u[0];
+    double th = std::tan((double)cam->vfov_deg * M_PI / 360.0);
+    double tw = th * (double)cam->width / (double)cam->height;
+    c.ex = (float)e[0];
+    c.ey = (float)e[1];
+    c.ez = (float)e[2];
+    c.ux = (float)(u[0] * tw);
+    c.uy = (float)(u[1] * tw);
+    c.uz = (float)(u[2] * tw);
+    c.vx = (float)(v[0] * th);
+    c.vy = (float)(v[1] * th);
+    c.vz = (float)(v[2] * th);
+    c.wx = (float)w[0];
+    c.wy = (float)w[1];
+    c.wz = (float)w[2];
+    c.W = cam->width;
+    c.H = cam->height;
+    return PT_OK;
+}
+
+pt_render_opts default_opts() {
+    pt_render_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.mode = PT_MODE_WAVEFRONT;
+    o.rr_start = 3;
+    return o;
+}
+
+pt_status check_opts(const pt_render_opts& o) {
+    if (o.mode > PT_MODE_WAVEFRONT) return fail(PT_ERR_INVALID_ARG, "opts.mode must be 0 or 1");
+    if (!(o.rr_fixed >= 0.f && o.rr_fixed <= 1.f)) return fail(PT_ERR_INVALID_ARG, "opts.rr_fixed must be in [0, 1]");
+    if (o.sort_mode > PT_SORT_MATERIAL) return fail(PT_ERR_INVALID_ARG, "opts.sort_mode must be 0, 1 or 2");
+    if (o.block_size && (o.block_size % 32 || o.block_size < 64 || o.block_size > 256))
+        return fail(PT_ERR_INVALID_ARG, "opts.block_size must be 0 or a multiple of 32 in [64, 256]");
+    return PT_OK;
+}
+
+pt::Launch launch_for(const pt_scene* sc, int kernel, uint32_t block_opt, uint32_t def_block, cudaStream_t st,
+                      uint64_t work_upper) {
+    pt::Launch l;
+    l.block = block_opt ? (int)block_opt : (int)def_block;
+    int per = blocks_per_sm(kernel, l.block);
+    uint64_t grid = (uint64_t)sm_count(sc->device) * (uint64_t)per;
+    uint64_t need = (work_upper + l.block - 1) / l.block;
+    if (need < grid) grid = need;
+    if (grid < 1) grid = 1;
+    l.grid = (int)grid;
+    l.st = st;
+    return l;
+}
+
+pt::Launch simple_launch(const pt_scene* sc, cudaStream_t st, uint64_t work) {
+    pt::Launch l;
+    l.block = 256;
+    uint64_t grid = std::min<uint64_t>((work + 255) / 256, (uint64_t)sm_count(sc->device) * 8);
+    l.grid = (int)std::max<uint64_t>(grid, 1);
+    l.st = st;
+    return l;
+}
+
+pt_status set_device(const pt_scene* sc) {
+    int cur = -1;
+    PT_CUDA(cudaGetDevice(&cur));
+    if (cur != sc->device) PT_CUDA(cudaSetDevice(sc->device));
+    return PT_OK;
+}
+
+// The wavefront pipeline over one scene and camera, waves of `cap` paths (a multiple of spp).
+pt_status run_wavefront(pt_scene* sc, const pt::DevCamera& cam, const pt::RenderParams& p0, const pt_render_opts& o,
+                        uint64_t n_paths, float* img, float* path_L, uint32_t* sig, cudaStream_t st) {
+    uint64_t cap = o.queue_capacity ? std::min<uint64_t>(o.queue_capacity, n_paths) : n_paths;
+    cap = std::max<uint64_t>(cap - cap % p0.spp, p0.spp);
+    if (cap >= (1ull << 32)) cap = ((1ull << 32) - (1ull << 20)) / p0.spp * p0.spp;
+    PT_TRY(sc->ensure_wf(cap));
+    pt::WfBuffers w = sc->wfb;
+    w.counts = sc->counts();
+    w.hist = sc->hist();
+    w.sig = sig;
+    w.capacity = (uint32_t)cap;
+    const pt::DevScene ds = sc->view();
+    uint32_t n_keys = 0;
+    if (o.sort_mode == PT_SORT_TYPE) n_keys = 4;                       // 3 types + miss
+    if (o.sort_mode == PT_SORT_MATERIAL) n_keys = std::min<uint32_t>(sc->n_mats + 1, pt::kMaxSortKeys);
+    const uint32_t sort_mode = o.sort_mode == PT_SORT_TYPE ? 1u : 2u;
+    for (uint64_t w0 = 0; w0 < n_paths; w0 += cap) {
+        const uint32_t n = (uint32_t)std::min<uint64_t>(cap, n_paths - w0);
+        pt::RenderParams p = p0;
+        p.path_begin = w0;
+        size_t ev = 0;
+        pt::Launch lr = launch_for(sc, pt::K_EXTEND, 0, 256, st, n);
+        PT_TRY(sc->ev_begin(ST_RAYGEN, st, ev));
+        PT_CUDA(pt::launch_raygen(simple_launch(sc, st, n), cam, p, n, w));
+        PT_TRY(sc->ev_end(ev, st));
+        sc->launches += 1;
+        for (uint32_t b = 0; b < p.max_depth; ++b) {
+            const int in = (int)(b & 1u);
+            pt::Launch le = launch_for(sc, pt::K_EXTEND, o.block_size, 256, st, n);
+            PT_TRY(sc->ev_begin(ST_EXTEND, st, ev));
+            PT_CUDA(pt::launch_extend(le, ds, w, in));
+            PT_TRY(sc->ev_end(ev, st));
+            bool sorted = n_keys > 0;
+            if (sorted) {
+                PT_TRY(sc->ev_begin(ST_SORT, st, ev));
+                PT_CUDA(pt::launch_sort(simple_launch(sc, st, n), ds, w, sort_mode, n_keys));
+                PT_TRY(sc->ev_end(ev, st));
+            }
+            pt::Launch ls = launch_for(sc, pt::K_SHADE, o.block_size, 256, st, n);
+            PT_TRY(sc->ev_begin(ST_SHADE, st, ev));
+            PT_CUDA(pt::launch_shade(ls, ds, p, w, in, b, sorted));
+            PT_TRY(sc->ev_end(ev, st));
+            pt::Launch lw = launch_for(sc, pt::K_SHADOW, o.block_size, 256, st, n);
+            PT_TRY(sc->ev_begin(ST_SHADOW, st, ev));
+            PT_CUDA(pt::launch_shadow(lw, ds, p, w, b));
+            PT_TRY(sc->ev_end(ev, st));
+            PT_CUDA(pt::launch_prepare(st, w, b));
+            sc->launches += 4 + (sorted ? 3 : 0);
+        }
+        (void)lr;
+        PT_TRY(sc->ev_begin(ST_REDUCE, st, ev));
+        PT_CUDA(pt::launch_reduce(simple_launch(sc, st, n / p.spp), reinterpret_cast<const float*>(w.L), 4,
+                                  w0 / p.spp, n / p.spp, p.spp, img));
+        if (path_L) PT_CUDA(pt::launch_copy_L(simple_launch(sc, st, n), w.L, n, path_L + 3 * w0));
+        PT_TRY(sc->ev_end(ev, st));
+        sc->launches += path_L ? 2 : 1;
+    }
+    return PT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pt_status_string(pt_status s) {
+    switch (s) {
+        case PT_OK: return "ok";
+        case PT_ERR_INVALID_ARG: return "invalid argument";
+        case PT_ERR_OOM: return "out of memory";
+        case PT_ERR_CUDA: return "CUDA error";
+        case PT_ERR_QUEUE_OVERFLOW: return "queue overflow";
+        case PT_ERR_TRAVERSAL_LIMIT: return "traversal limit exceeded";
+        case PT_ERR_TIMEOUT: return "timeout";
+        case PT_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* pt_last_error(void) { return g_err.c_str(); }
+
+pt_status pt_scene_create(const float* verts, uint32_t n_verts, const uint32_t* tris, uint32_t n_tris,
+                          const uint32_t* tri_material, const pt_material* mats, uint32_t n_mats,
+                          const float env_radiance[3], void* cuda_stream, pt_scene** out) {
+    if (!out) return fail(PT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_tris > 0 && (!verts || !tris || !tri_material))
+        return fail(PT_ERR_INVALID_ARG, "verts, tris and tri_material are required when n_tris > 0");
+    if (n_mats > 0 && !mats) return fail(PT_ERR_INVALID_ARG, "mats is NULL");
+    if (n_tris > 0 && n_mats == 0) return fail(PT_ERR_INVALID_ARG, "n_mats must be > 0 when n_tris > 0");
+    if (n_tris >= (1u << 28)) return fail(PT_ERR_INVALID_ARG, "n_tris must be < 2^28");
+    for (uint64_t i = 0; i < 3ull * n_verts; ++i)
+        if (!std::isfinite(verts[i])) return fail(PT_ERR_INVALID_ARG, "vertex %llu is not finite", (unsigned long long)(i / 3));
+    for (uint64_t i = 0; i < 3ull * n_tris; ++i)
+        if (tris[i] >= n_verts) return fail(PT_ERR_INVALID_ARG, "triangle %llu references vertex %u >= n_verts", (unsigned long long)(i / 3), tris[i]);
+    for (uint32_t i = 0; i < n_tris; ++i)
+        if (tri_material[i] >= n_mats) return fail(PT_ERR_INVALID_ARG, "triangle %u has material %u >= n_mats", i, tri_material[i]);
+    for (uint32_t m = 0; m < n_mats; ++m) {
+        const pt_material& M = mats[m];
+        if (M.type > PT_MAT_DIELECTRIC) return fail(PT_ERR_INVALID_ARG, "material %u: unknown type %u", m, M.type);
+        if (!finite3(M.albedo) || M.albedo[0] < 0 || M.albedo[1] < 0 || M.albedo[2] < 0)
+            return fail(PT_ERR_INVALID_ARG, "material %u: albedo must be finite and >= 0", m);
+        if (!std::isfinite(M.emission) || M.emission < 0) return fail(PT_ERR_INVALID_ARG, "material %u: emission must be finite and >= 0", m);
+        if (!std::isfinite(M.roughness) || M.roughness < 0) return fail(PT_ERR_INVALID_ARG, "material %u: roughness must be finite and >= 0", m);
+        if (!std::isfinite(M.ior) || !(M.ior > 0)) return fail(PT_ERR_INVALID_ARG, "material %u: ior must be finite and > 0", m);
+    }
+    if (env_radiance && (!finite3(env_radiance) || env_radiance[0] < 0 || env_radiance[1] < 0 || env_radiance[2] < 0))
+        return fail(PT_ERR_INVALID_ARG, "env_radiance must be finite and >= 0");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+    pt_scene* sc = new (std::nothrow) pt_scene();
+    if (!sc) return fail(PT_ERR_OOM, "host allocation failed");
+    auto bail = [&](pt_status s) {
+        delete sc;
+        return s;
+    };
+    if (cudaGetDevice(&sc->device) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(PT_ERR_CUDA, "no CUDA device"));
+    }
+    sc->n_tris = n_tris;
+    sc->n_mats = n_mats;
+    if (env_radiance)
+        for (int k = 0; k < 3; ++k) sc->env[k] = env_radiance[k];
+
+    pt::BvhOut bvh;
+    std::string err;
+    if (!pt::build_bvh(verts, tris, n_tris, bvh, err)) return bail(fail(PT_ERR_INVALID_ARG, "BVH build: %s", err.c_str()));
+    sc->n_nodes = bvh.n_internal;
+
+    // triangle records in leaf order: (v0 | prim) (e1 | material) (e2 | is_light)
+    std::vector<float> trec(12 * (size_t)n_tris);
+    auto bits = [](uint32_t u) {
+        float f;
+        std::memcpy(&f, &u, 4);
+        return f;
+    };
+    for (uint32_t k = 0; k < n_tris; ++k) {
+        uint32_t i = bvh.order[k];
+        const float* a = verts + 3 * (size_t)tris[3 * (size_t)i];
+        const float* b = verts + 3 * (size_t)tris[3 * (size_t)i + 1];
+        const float* c = verts + 3 * (size_t)tris[3 * (size_t)i + 2];
+        float* r = &trec[12 * (size_t)k];
+        uint32_t m = tri_material[i];
+        r[0] = a[0]; r[1] = a[1]; r[2] = a[2]; r[3] = bits(i);
+        r[4] = b[0] - a[0]; r[5] = b[1] - a[1]; r[6] = b[2] - a[2]; r[7] = bits(m);
+        r[8] = c[0] - a[0]; r[9] = c[1] - a[1]; r[10] = c[2] - a[2];
+        r[11] = bits(mats[m].emission > 0.f ? 1u : 0u);
+    }
+    // light list: triangles whose material emits at creation, ascending id; pmf proportional to area
+    std::vector<float> lrec;
+    std::vector<double> areas;
+    for (uint32_t i = 0; i < n_tris; ++i) {
+        uint32_t m = tri_material[i];
+        if (!(mats[m].emission > 0.f)) continue;
+        const float* a = verts + 3 * (size_t)tris[3 * (size_t)i];
+        const float* b = verts + 3 * (size_t)tris[3 * (size_t)i + 1];
+        const float* c = verts + 3 * (size_t)tris[3 * (size_t)i + 2];
+        double e1[3], e2[3];
+        for (int k = 0; k < 3; ++k) {
+            e1[k] = (double)b[k] - a[k];
+            e2[k] = (double)c[k] - a[k];
+        }
+        double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2], cz = e1[0] * e2[1] - e1[1] * e2[0];
+        areas.push_back(0.5 * std::sqrt(cx * cx + cy * cy + cz * cz));
+        float rec[12] = {a[0], a[1], a[2], bits(m), b[0], b[1], b[2], 0.f, c[0], c[1], c[2], 0.f};
+        lrec.insert(lrec.end(), rec, rec + 12);
+    }
+    sc->n_lights = areas.size();
+    std::vector<float> cdf(std::max<size_t>(areas.size(), 1), 0.f);
+    double total = 0;
+    for (double a : areas) total += a;
+    double acc = 0;
+    for (size_t j = 0; j < areas.size(); ++j) {
+        acc += areas[j];
+        cdf[j] = total > 0 ? (float)(acc / total) : 0.f;
+    }
+    if (!areas.empty() && total > 0) cdf.back() = 1.0f;
+    sc->light_area = (float)total;
+
+    std::vector<pt::DevMat> dm(std::max<uint32_t>(n_mats, 1));
+    for (uint32_t m = 0; m < n_mats; ++m) {
+        const pt_material& M = mats[m];
+        dm[m] = pt::DevMat{M.type, M.albedo[0], M.albedo[1], M.albedo[2], M.emission, M.roughness, M.ior, 0u};
+    }
+
+    pt_status s;
+    if ((s = sc->nodes.ensure(bvh.nodes.size() * 4)) != PT_OK) return bail(s);
+    if ((s = sc->tris.ensure(std::max<size_t>(trec.size() * 4, 48))) != PT_OK) return bail(s);
+    if ((s = sc->mats.ensure(dm.size() * sizeof(pt::DevMat))) != PT_OK) return bail(s);
+    if ((s = sc->lights.ensure(std::max<size_t>(lrec.size() * 4, 48))) != PT_OK) return bail(s);
+    if ((s = sc->cdf.ensure(cdf.size() * 4)) != PT_OK) return bail(s);
+    if ((s = sc->status.ensure(256)) != PT_OK) return bail(s);
+    if ((s = sc->ensure_counters()) != PT_OK) return bail(s);
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sc->nodes.p, bvh.nodes.data(), bvh.nodes.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !trec.empty()) e = cudaMemcpyAsync(sc->tris.p, trec.data(), trec.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && trec.empty()) e = cudaMemsetAsync(sc->tris.p, 0, 48, st);   // the never-hit record
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sc->mats.p, dm.data(), dm.size() * sizeof(pt::DevMat), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !lrec.empty()) e = cudaMemcpyAsync(sc->lights.p, lrec.data(), lrec.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sc->cdf.p, cdf.data(), cdf.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc->status.p, 0, 256, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc->counters.p, 0, sc->counters.bytes, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(PT_ERR_CUDA, "scene upload: %s", cudaGetErrorString(e)));
+    }
+    sc->last_stream = st;
+    *out = sc;
+    return PT_OK;
+}
+
+void pt_scene_destroy(pt_scene* scene) {
+    if (!scene) return;
+    if (scene->last_stream) cudaStreamSynchronize(scene->last_stream);
+    else cudaDeviceSynchronize();
+    cudaGetLastError();
+    delete scene;
+}
+
+pt_status pt_scene_set_materials(pt_scene* sc, const float* d_albedo, const float* d_emission, void* stream) {
+    if (!sc) return fail(PT_ERR_INVALID_ARG, "scene is NULL");
+    if ((d_albedo && !is_device_ptr(d_albedo)) || (d_emission && !is_device_ptr(d_emission)))
+        return fail(PT_ERR_INVALID_ARG, "material arrays must be device pointers");
+    std::lock_guard<std::mutex> g(sc->mu);
+    PT_TRY(set_device(sc));
+    PT_CUDA(pt::launch_set_materials(static_cast<cudaStream_t>(stream), sc->mats.as<pt::DevMat>(), sc->n_mats, d_albedo,
+                                     d_emission));
+    return PT_OK;
+}
+
+pt_status pt_scene_info(const pt_scene* sc, uint64_t* n_tris, uint64_t* n_nodes, uint64_t* n_lights, float* light_area,
+                        uint64_t* device_bytes) {
+    if (!sc) return fail(PT_ERR_INVALID_ARG, "scene is NULL");
+    if (n_tris) *n_tris = sc->n_tris;
+    if (n_nodes) *n_nodes = sc->n_nodes;
+    if (n_lights) *n_lights = sc->n_lights;
+    if (light_area) *light_area = sc->light_area;
+    if (device_bytes)
+        *device_bytes = sc->nodes.bytes + sc->tris.bytes + sc->mats.bytes + sc->lights.bytes + sc->cdf.bytes +
+                        sc->wf.bytes + sc->pathL.bytes + sc->img_stage.bytes + sc->grad_stage.bytes + sc->counters.bytes;
+    return PT_OK;
+}
+
+pt_status pt_render(pt_scene* sc, const pt_camera* cam, uint32_t spp, uint32_t max_depth, uint64_t seed,
+                    const pt_render_opts* opts, float* d_out_rgb, float* d_path_L_or_null, void* stream) {
+    if (!sc) return fail(PT_ERR_INVALID_ARG, "scene is NULL");
+    if (!d_out_rgb) return fail(PT_ERR_INVALID_ARG, "output image is NULL");
+    if (spp == 0) return fail(PT_ERR_INVALID_ARG, "spp must be >= 1");
+    if (max_depth > 64) return fail(PT_ERR_INVALID_ARG, "max_depth must be <= 64");
+    pt_render_opts o = opts ? *opts : default_opts();
+    PT_TRY(check_opts(o));
+    pt::DevCamera dc;
+    PT_TRY(make_camera(cam, dc));
+    const uint64_t n_pixels = (uint64_t)cam->width * cam->height;
+    const uint64_t n_paths = n_pixels * spp;
+    if (n_paths >= (1ull << 40)) return fail(PT_ERR_INVALID_ARG, "too many paths");
+    if (d_path_L_or_null && !is_device_ptr(d_path_L_or_null)) return fail(PT_ERR_INVALID_ARG, "path_L must be a device pointer");
+    if (o.d_path_sig && !is_device_ptr(o.d_path_sig)) return fail(PT_ERR_INVALID_ARG, "d_path_sig must be a device pointer");
+    std::lock_guard<std::mutex> g(sc->mu);
+    PT_TRY(set_device(sc));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool host_out = !is_device_ptr(d_out_rgb);
+    float* img = d_out_rgb;
+    if (host_out) {
+        PT_TRY(sc->img_stage.ensure(n_pixels * 12));
+        img = sc->img_stage.as<float>();
+    }
+    sc->profiling = (o.flags & PT_FLAG_PROFILE) != 0;
+    sc->ev_used = 0;
+    sc->last_stream = st;
+    sc->last_mode = o.mode;
+    sc->last_paths = n_paths;
+    sc->launches = 0;
+    PT_CUDA(cudaMemsetAsync(sc->counters.p, 0, sc->counters.bytes, st));
+    PT_CUDA(cudaMemsetAsync(sc->status.p, 0, 4, st));
+    pt::RenderParams p;
+    p.seed = seed;
+    p.path_begin = 0;
+    p.spp = spp;
+    p.max_depth = max_depth;
+    p.rr_start = o.rr_start;
+    p.rr_fixed = o.rr_fixed;
+    if (max_depth == 0) {
+        PT_CUDA(cudaMemsetAsync(img, 0, n_pixels * 12, st));
+        if (d_path_L_or_null) PT_CUDA(cudaMemsetAsync(d_path_L_or_null, 0, n_paths * 12, st));
+        if (o.d_path_sig) PT_CUDA(cudaMemsetAsync(o.d_path_sig, 0, n_paths * 4, st));
+    } else if (o.mode == PT_MODE_MEGAKERNEL) {
+        float* outL = d_path_L_or_null;
+        if (!outL && spp > 1) {
+            PT_TRY(sc->pathL.ensure(n_paths * 12));
+            outL = sc->pathL.as<float>();
+        }
+        pt::Launch l = launch_for(sc, pt::K_MEGA, o.block_size, 128, st, n_paths);
+        size_t ev = 0;
+        PT_TRY(sc->ev_begin(ST_MEGA, st, ev));
+        PT_CUDA(pt::launch_megakernel(l, sc->view(), dc, p, n_paths, outL, img, o.d_path_sig, sc->rays()));
+        PT_TRY(sc->ev_end(ev, st));
+        sc->launches += 1;
+        if (outL) {
+            sc->launches += 1;
+            PT_TRY(sc->ev_begin(ST_REDUCE, st, ev));
+            PT_CUDA(pt::launch_reduce(simple_launch(sc, st, n_pixels), outL, 3, 0, n_pixels, spp, img));
+            PT_TRY(sc->ev_end(ev, st));
+        }
+    } else {
+        PT_TRY(run_wavefront(sc, dc, p, o, n_paths, img, d_path_L_or_null, o.d_path_sig, st));
+    }
+    if (host_out) {
+        PT_CUDA(cudaMemcpyAsync(d_out_rgb, img, n_pixels * 12, cudaMemcpyDeviceToHost, st));
+        PT_CUDA(cudaStreamSynchronize(st));
+    }
+    return PT_OK;
+}
+
+pt_status pt_render_backward(pt_scene* sc, const pt_camera* cam, uint32_t spp, uint32_t max_depth, uint64_t seed,
+                             const pt_render_opts* opts, const float* d_grad_rgb, float* d_grad_albedo,
+                             float* d_grad_emission, void* stream) {
+    if (!sc) return fail(PT_ERR_INVALID_ARG, "scene is NULL");
+    if (!d_grad_rgb || !d_grad_albedo || !d_grad_emission)
+        return fail(PT_ERR_INVALID_ARG, "gradient pointers must be non-NULL");
+    if (spp == 0) return fail(PT_ERR_INVALID_ARG, "spp must be >= 1");
+    if (max_depth > 32) return fail(PT_ERR_UNSUPPORTED, "backward supports max_depth <= 32");
+    if (!is_device_ptr(d_grad_albedo) || !is_device_ptr(d_grad_emission))
+        return fail(PT_ERR_INVALID_ARG, "d_grad_albedo and d_grad_emission must be device pointers");
+    pt_render_opts o = opts ? *opts : default_opts();
+    PT_TRY(check_opts(o));
+    pt::DevCamera dc;
+    PT_TRY(make_camera(cam, dc));
+    const uint64_t n_pixels = (uint64_t)cam->width * cam->height;
+    const uint64_t n_paths = n_pixels * spp;
+    std::lock_guard<std::mutex> g(sc->mu);
+    PT_TRY(set_device(sc));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const float* grad = d_grad_rgb;
+    if (!is_device_ptr(d_grad_rgb)) {
+        PT_TRY(sc->grad_stage.ensure(n_pixels * 12));
+        PT_CUDA(cudaMemcpyAsync(sc->grad_stage.p, d_grad_rgb, n_pixels * 12, cudaMemcpyHostToDevice, st));
+        grad = sc->grad_stage.as<float>();
+    }
+    sc->profiling = (o.flags & PT_FLAG_PROFILE) != 0;
+    sc->ev_used = 0;
+    sc->last_stream = st;
+    sc->last_mode = 2;
+    sc->last_paths = n_paths;
+    sc->launches = 0;
+    PT_CUDA(cudaMemsetAsync(sc->counters.p, 0, sc->counters.bytes, st));
+    PT_CUDA(cudaMemsetAsync(sc->status.p, 0, 4, st));
+    if (max_depth == 0 || sc->n_mats == 0) return PT_OK;
+    pt::RenderParams p;
+    p.seed = seed;
+    p.path_begin = 0;
+    p.spp = spp;
+    p.max_depth = max_depth;
+    p.rr_start = o.rr_start;
+    p.rr_fixed = o.rr_fixed;
+    pt::Launch l = launch_for(sc, pt::K_ADJOINT, o.block_size, 128, st, n_paths);
+    size_t ev = 0;
+    PT_TRY(sc->ev_begin(ST_ADJOINT, st, ev));
+    PT_CUDA(pt::launch_adjoint(l, sc->view(), dc, p, n_paths, grad, d_grad_albedo, d_grad_emission, max_depth));
+    PT_TRY(sc->ev_end(ev, st));
+    sc->launches += 1;
+    return PT_OK;
+}
+
+pt_status pt_trace_closest(pt_scene* sc, const float* d_rays, uint32_t n, float* d_t, int32_t* d_prim, void* stream) {
+    if (!sc) return fail(PT_ERR_INVALID_ARG, "scene is NULL");
+    if (n == 0) return PT_OK;
+    if (!d_rays || !d_t || !d_prim) return fail(PT_ERR_INVALID_ARG, "NULL buffer");
+    std::lock_guard<std::mutex> g(sc->mu);
+    PT_TRY(set_device(sc));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    sc->last_stream = st;
+    PT_CUDA(pt::launch_trace_closest(launch_for(sc, pt::K_EXTEND, 0, 256, st, n), sc->view(), d_rays, n, d_t, d_prim));
+    return PT_OK;
+}
+
+pt_status pt_debug_rng(uint64_t seed, const uint32_t* px, const uint32_t* sm, const uint32_t* bo, const uint32_t* dm,
+                       uint32_t n, float* out, void* stream) {
+    if (n == 0) return PT_OK;
+    if (!px || !sm || !bo || !dm || !out) return fail(PT_ERR_INVALID_ARG, "NULL buffer");
+    pt::Launch l{1, 256, static_cast<cudaStream_t>(stream)};
+    PT_CUDA(pt::launch_debug_rng(l, seed, px, sm, bo, dm, n, out));
+    return PT_OK;
+}
+
+pt_status pt_get_stats(pt_scene* sc, pt_stats* out) {
+    if (!sc || !out) return fail(PT_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> g(sc->mu);
+    PT_TRY(set_device(sc));
+    PT_CUDA(cudaStreamSynchronize(sc->last_stream));
+    std::memset(out, 0, sizeof(*out));
+    std::vector<unsigned long long> h(130);
+    uint32_t status = 0;
+    PT_CUDA(cudaMemcpy(h.data(), sc->hist(), 130 * 8, cudaMemcpyDeviceToHost));
+    PT_CUDA(cudaMemcpy(&status, sc->status.p, 4, cudaMemcpyDeviceToHost));
+    out->paths = sc->last_paths;
+    out->launches_total = sc->launches;
+    if (sc->last_mode != PT_MODE_WAVEFRONT) {
+        out->extension_rays = h[128];
+        out->shadow_rays = h[129];
+    } else {
+        for (int b = 0; b < 64; ++b) {
+            out->extension_rays += h[b];
+            out->shadow_rays += h[64 + b];
+            out->active[b] = h[b];
+            if (h[b]) out->bounces = b + 1;
+        }
+    }
+    out->status = status & pt::ST_TRAVERSAL ? PT_ERR_TRAVERSAL_LIMIT
+                : status & pt::ST_QUEUE     ? PT_ERR_QUEUE_OVERFLOW
+                : status & pt::ST_TIMEOUT   ? PT_ERR_TIMEOUT
+                                            : PT_OK;
+    if (sc->profiling) {
+        float ms[ST_COUNT] = {};
+        uint32_t n_ext = 0, n_shd = 0;
+        for (size_t i = 0; i < sc->ev_used; ++i) {
+            float t = 0.f;
+            PT_CUDA(cudaEventElapsedTime(&t, sc->events[i].a, sc->events[i].b));
+            ms[sc->events[i].stage] += t;
+            if (sc->events[i].stage == ST_EXTEND) ++n_ext;
+            if (sc->events[i].stage == ST_SHADOW) ++n_shd;
+        }
+        out->ms_raygen = ms[ST_RAYGEN];
+        out->ms_extend = ms[ST_EXTEND];
+        out->ms_sort = ms[ST_SORT];
+        out->ms_shade = ms[ST_SHADE];
+        out->ms_shadow = ms[ST_SHADOW];
+        out->ms_reduce = ms[ST_REDUCE];
+        out->ms_megakernel = ms[ST_MEGA];
+        out->ms_adjoint = ms[ST_ADJOINT];
+        out->launches_extend = n_ext;
+        out->launches_shadow = n_shd;
+        for (float t : ms) out->ms_total += t;
+    }
+    return PT_OK;
+}
+
+pt_status pt_render_batch(pt_scene* const* scenes, const pt_camera* cams, const uint32_t* spp, uint32_t n,
+                          uint32_t max_depth, uint64_t seed, const pt_render_opts* opts, float* const* d_out,
+                          void* stream) {
+    (void)scenes; (void)cams; (void)spp; (void)n; (void)max_depth; (void)seed; (void)opts; (void)d_out; (void)stream;
+    return fail(PT_ERR_UNSUPPORTED, "pt_render_batch: not implemented yet");
+}
+
+pt_status pt_autotune_batch(pt_scene* const* scenes, const pt_camera* cams, const uint32_t* spp, uint32_t n,
+                            uint32_t max_depth, uint64_t seed, const pt_render_opts* base, float* const* d_out,
+                            void* stream, pt_render_opts* best, float* best_ms) {
+    (void)scenes; (void)cams; (void)spp; (void)n; (void)max_depth; (void)seed; (void)base; (void)d_out; (void)stream;
+    (void)best; (void)best_ms;
+    return fail(PT_ERR_UNSUPPORTED, "pt_autotune_batch: not implemented yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,56 @@
+// pt_launch.h -- host-callable launchers of the CUDA kernels (defined in pt_kernels.cu), used by
+// the C-ABI layer (pt_api.cpp).  Every launcher is asynchronous on `st` and returns the launch error.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime_api.h>
+
+#include "pt_types.h"
+
+namespace pt {
+
+struct Launch {
+    int grid;
+    int block;
+    cudaStream_t st;
+};
+
+// Megakernel (Sec. 2.2): one thread per path, whole path in one kernel.  Writes per-path radiance
+// into out_L (stride 3 floats, wave-local index) when non-null, else img (spp == 1: pixel = path).
+cudaError_t launch_megakernel(const Launch& l, const DevScene& s, const DevCamera& c, const RenderParams& p,
+                              uint64_t n_paths, float* out_L, float* img, uint32_t* sig,
+                              unsigned long long* rays);
+
+// Wavefront stages (Sec. 2.3, 3.1).  `in` selects the ping-pong queue read this bounce.
+cudaError_t launch_raygen(const Launch& l, const DevCamera& c, const RenderParams& p, uint32_t n, const WfBuffers& w);
+cudaError_t launch_extend(const Launch& l, const DevScene& s, const WfBuffers& w, int in);
+cudaError_t launch_sort(const Launch& l, const DevScene& s, const WfBuffers& w, uint32_t mode, uint32_t n_keys);
+cudaError_t launch_shade(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w, int in,
+                         uint32_t bounce, bool sorted);
+cudaError_t launch_shadow(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w,
+                          uint32_t bounce);
+cudaError_t launch_prepare(cudaStream_t st, const WfBuffers& w, uint32_t bounce);
+
+// Accumulation (Sec. 2.3): img[pixel] = (1/spp) * sum_s L[pixel * spp + s], samples in order.
+// L has `stride` floats per path (3 or 4), wave-local; pixels [pixel_begin, pixel_begin + n_pixels).
+cudaError_t launch_reduce(const Launch& l, const float* L, uint32_t stride, uint64_t pixel_begin, uint64_t n_pixels,
+                          uint32_t spp, float* img);
+// Copy wave-local float4 radiance into the caller's N_p x 3 buffer at path offset `path_begin`.
+cudaError_t launch_copy_L(const Launch& l, const float4* L4, uint64_t n, float* out_L3);
+
+// Path-replay adjoint (one thread per path).  grad_img is H x W x 3.
+cudaError_t launch_adjoint(const Launch& l, const DevScene& s, const DevCamera& c, const RenderParams& p,
+                           uint64_t n_paths, const float* grad_img, float* g_albedo, float* g_emission,
+                           uint32_t max_depth_cap);
+
+// Utilities.
+cudaError_t launch_set_materials(cudaStream_t st, DevMat* mats, uint32_t n, const float* albedo, const float* emission);
+cudaError_t launch_trace_closest(const Launch& l, const DevScene& s, const float* rays, uint32_t n, float* t,
+                                 int32_t* prim);
+cudaError_t launch_debug_rng(const Launch& l, uint64_t seed, const uint32_t* px, const uint32_t* sm,
+                             const uint32_t* bo, const uint32_t* dm, uint32_t n, float* out);
+
+// Occupancy helpers.
+int max_blocks_per_sm(int which, int block);   // which: 0 megakernel, 1 extend, 2 shade, 3 shadow, 4 adjoint
+enum { K_MEGA = 0, K_EXTEND = 1, K_SHADE = 2, K_SHADOW = 3, K_ADJOINT = 4 };
+
+}  // namespace pt

@@ -1,0 +1,193 @@
+// pt_trace.cuh -- BVH traversal (the scene-intersection stage of Sec. 2.3, "extend" of Sec. 2.2
+// step 2, and the shadow-evaluation query of Sec. 3), written for CUDA cores: the paper's hardware
+// ray queries are not reachable here, so traversal is a software loop over a host-built binary
+// BVH.
+//
+// Node layout (64 bytes, one 128-bit load per row, both children's boxes in the parent):
+//   n0 = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
+//   n1 = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
+//   n2 = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
+//   n3 = (ref0, ref1, -, -)     ref: internal node index, or 0x80000000 | first << 3 | (count - 1)
+// Triangle record (48 bytes): (v0.xyz, prim id) (e1 = v1 - v0, material) (e2 = v2 - v0, is_light).
+//
+// Closest hit: Moller-Trumbore with inclusive barycentric bounds and t > 0; equal t goes to the
+// lower original triangle id, so the result does not depend on traversal order.  Box tests are
+// conservative (the far distance is widened by a few ulps) so rounding cannot cull a true hit.
+#pragma once
+#include "pt_device.cuh"
+
+namespace pt {
+
+constexpr int kStack = 64;                   // the builder caps tree depth below this
+constexpr uint32_t kMaxSteps = 1u << 22;     // traversal step cap (fault guard, never reached)
+constexpr uint32_t kMiss = 0xFFFFFFFFu;
+constexpr uint32_t kLeafBit = 0x80000000u;
+
+struct Hit {
+    float t;
+    uint32_t tri;    // reordered triangle index, kMiss on miss
+};
+
+__device__ __forceinline__ float3 ray_rcp(float3 d) {
+    // 1/d with zero components replaced by a tiny signed value: slabs stay finite and NaN-free
+    float x = fabsf(d.x) > 1e-20f ? d.x : copysignf(1e-20f, d.x);
+    float y = fabsf(d.y) > 1e-20f ? d.y : copysignf(1e-20f, d.y);
+    float z = fabsf(d.z) > 1e-20f ? d.z : copysignf(1e-20f, d.z);
+    return f3(1.0f / x, 1.0f / y, 1.0f / z);
+}
+
+// Slab test of one box against [0, tmax]; returns whether it is hit and the entry distance.
+__device__ __forceinline__ bool box_test(float lox, float hix, float loy, float hiy, float loz, float hiz, float3 o,
+                                         float3 id, float tmax, float& tn) {
+    float x0 = (lox - o.x) * id.x, x1 = (hix - o.x) * id.x;
+    float y0 = (loy - o.y) * id.y, y1 = (hiy - o.y) * id.y;
+    float z0 = (loz - o.z) * id.z, z1 = (hiz - o.z) * id.z;
+    float a = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.0f));
+    float b = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tmax));
+    tn = a;
+    return a <= b * 1.0000005f;
+}
+
+// Moller-Trumbore test of one triangle record; t in (0, tmax) by the caller's rule.
+__device__ __forceinline__ bool tri_test(const float4* __restrict__ tris, uint32_t i, float3 o, float3 d, float& t,
+                                         uint32_t& prim) {
+    const float4* p = tris + 3 * (size_t)i;
+    float4 a = __ldg(p), e1 = __ldg(p + 1), e2 = __ldg(p + 2);
+    float3 E1 = xyz(e1), E2 = xyz(e2);
+    float3 pv = cross(d, E2);
+    float det = dot(E1, pv);
+    if (det == 0.0f) return false;
+    float inv = 1.0f / det;
+    float3 tv = o - xyz(a);
+    float u = dot(tv, pv) * inv;
+    if (u < 0.0f || u > 1.0f) return false;
+    float3 qv = cross(tv, E1);
+    float v = dot(d, qv) * inv;
+    if (v < 0.0f || u + v > 1.0f) return false;
+    t = dot(E2, qv) * inv;
+    prim = __float_as_uint(a.w);
+    return true;
+}
+
+__device__ __forceinline__ void load_node(const float4* __restrict__ nodes, uint32_t i, float4& n0, float4& n1,
+                                          float4& n2, uint2& refs) {
+    const float4* p = nodes + 4 * (size_t)i;
+    n0 = __ldg(p);
+    n1 = __ldg(p + 1);
+    n2 = __ldg(p + 2);
+    float4 n3 = __ldg(p + 3);
+    refs = make_uint2(__float_as_uint(n3.x), __float_as_uint(n3.y));
+}
+
+// Closest hit along o + t d, t > 0 (the extend query).
+__device__ __forceinline__ Hit trace_closest(const DevScene& s, float3 o, float3 d) {
+    float3 id = ray_rcp(d);
+    float tbest = __int_as_float(0x7f800000);
+    uint32_t best = kMiss, bprim = kMiss;
+    uint32_t stack_ref[kStack];
+    float stack_t[kStack];
+    int sp = 0;
+    uint32_t ref = 0;          // the root is always an internal node
+    uint32_t steps = 0;
+    while (true) {
+        if (!(ref & kLeafBit)) {
+            float4 n0, n1, n2;
+            uint2 r;
+            load_node(s.nodes, ref, n0, n1, n2, r);
+            float t0, t1;
+            bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tbest, t0);
+            bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tbest, t1);
+            if (h0 && h1) {
+                bool first0 = t0 <= t1;
+                if (sp < kStack) {
+                    stack_ref[sp] = first0 ? r.y : r.x;
+                    stack_t[sp] = first0 ? t1 : t0;
+                    ++sp;
+                } else {
+                    atomicOr(s.status, ST_TRAVERSAL);
+                }
+                ref = first0 ? r.x : r.y;
+                if (++steps < kMaxSteps) continue;
+            } else if (h0 || h1) {
+                ref = h0 ? r.x : r.y;
+                if (++steps < kMaxSteps) continue;
+            }
+        } else {
+            uint32_t first = (ref & 0x7FFFFFFFu) >> 3, cnt = (ref & 7u) + 1u;
+            for (uint32_t k = 0; k < cnt; ++k) {
+                float t;
+                uint32_t prim;
+                if (tri_test(s.tris, first + k, o, d, t, prim) && t > 0.0f &&
+                    (t < tbest || (t == tbest && prim < bprim))) {
+                    tbest = t;
+                    best = first + k;
+                    bprim = prim;
+                }
+            }
+        }
+        if (steps >= kMaxSteps) {
+            atomicOr(s.status, ST_TRAVERSAL);
+            break;
+        }
+        // pop the next subtree whose entry is not beyond the best hit (ties kept)
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            if (stack_t[sp] <= tbest * 1.0000005f) {
+                ref = stack_ref[sp];
+                found = true;
+                break;
+            }
+        }
+        if (!found) break;
+        ++steps;
+    }
+    Hit h;
+    h.t = tbest;
+    h.tri = best;
+    return h;
+}
+
+// Any hit with 0 < t < tmax (the shadow query).
+__device__ __forceinline__ bool trace_any(const DevScene& s, float3 o, float3 d, float tmax) {
+    float3 id = ray_rcp(d);
+    uint32_t stack_ref[kStack];
+    int sp = 0;
+    uint32_t ref = 0;
+    uint32_t steps = 0;
+    while (true) {
+        if (!(ref & kLeafBit)) {
+            float4 n0, n1, n2;
+            uint2 r;
+            load_node(s.nodes, ref, n0, n1, n2, r);
+            float t0, t1;
+            bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tmax, t0);
+            bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tmax, t1);
+            if (h0 && h1) {
+                if (sp < kStack) stack_ref[sp++] = r.y;
+                else atomicOr(s.status, ST_TRAVERSAL);
+                ref = r.x;
+                if (++steps < kMaxSteps) continue;
+            } else if (h0 || h1) {
+                ref = h0 ? r.x : r.y;
+                if (++steps < kMaxSteps) continue;
+            }
+        } else {
+            uint32_t first = (ref & 0x7FFFFFFFu) >> 3, cnt = (ref & 7u) + 1u;
+            for (uint32_t k = 0; k < cnt; ++k) {
+                float t;
+                uint32_t prim;
+                if (tri_test(s.tris, first + k, o, d, t, prim) && t > 0.0f && t < tmax) return true;
+            }
+        }
+        if (steps >= kMaxSteps) {
+            atomicOr(s.status, ST_TRAVERSAL);
+            return false;
+        }
+        if (sp == 0) return false;
+        ref = stack_ref[--sp];
+        ++steps;
+    }
+}
+
+}  // namespace pt

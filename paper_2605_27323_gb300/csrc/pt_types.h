@@ -1,0 +1,78 @@
+// pt_types.h -- plain structs shared by host code (pt_api.cpp) and device code: the device views
+// of a scene, the camera, the render parameters and the wavefront buffers.
+#pragma once
+#include <cstdint>
+#include <vector_types.h>
+
+namespace pt {
+
+// ------------------------------------------------------------------ scene views
+struct DevMat {            // 32 bytes, mirrors pt_material
+    uint32_t type;
+    float ar, ag, ab;
+    float emission;
+    float roughness;
+    float ior;
+    uint32_t flags;
+};
+
+struct DevScene {
+    const float4* __restrict__ nodes;      // 4 float4 per node (two child boxes + refs)
+    const float4* __restrict__ tris;       // 3 float4 per triangle: v0|prim, e1|material, e2|is_light
+    const DevMat* __restrict__ mats;
+    const float4* __restrict__ lights;     // 3 float4 per light: p0|material, p1|-, p2|-
+    const float* __restrict__ light_cdf;   // inclusive prefix of area / total area
+    uint32_t n_lights;
+    float light_area;
+    float env_r, env_g, env_b;
+    uint32_t n_mats;
+    uint32_t* status;                      // device status word (atomicOr of fault bits)
+};
+
+struct DevCamera {         // U = u * tan(fov/2) * aspect, V = v * tan(fov/2), Wd = w (view -> eye)
+    float ex, ey, ez;
+    float ux, uy, uz;
+    float vx, vy, vz;
+    float wx, wy, wz;
+    uint32_t W, H;
+};
+
+struct RenderParams {
+    uint64_t seed;
+    uint64_t path_begin;   // first path id of this launch / wave
+    uint32_t spp;
+    uint32_t max_depth;
+    uint32_t rr_start;
+    float rr_fixed;
+};
+
+enum : uint32_t { MAT_LAMBERT = 0, MAT_GGX = 1, MAT_DIELECTRIC = 2 };
+enum : uint32_t { ST_TRAVERSAL = 1u, ST_QUEUE = 2u, ST_TIMEOUT = 4u };
+
+// Wavefront buffers of one wave (Sec. 2.3 / 3.1): ping-pong ray queues, hit records, sort
+// scratch, the shadow-ray queue, per-path radiance, and the counters.  counts[0] = active paths of
+// the current bounce, counts[1] = next bounce's count (filled by compaction), counts[2] = shadow
+// rays; the prepare step promotes [1] to [0] and resets [1] and [2] (the two-slot count of
+// Sec. 3.1).  The paper reuses one index buffer in place; here the two ray queues alternate, since
+// on CUDA a block may append into a slot that a block not yet scheduled still has to read.
+struct WfBuffers {
+    float4* q_o[2];          // o.xyz | path index (wave-local) bits
+    float4* q_d[2];          // d.xyz | flags (bit 0: previous vertex was delta)
+    float4* q_tp[2];         // throughput.xyz | -
+    float2* hit;             // per queue slot: t, reordered triangle bits (0xFFFFFFFF: miss)
+    uint32_t* keys;          // per queue slot: sort key
+    uint32_t* perm;          // per sorted position: queue slot
+    uint32_t* bucket;        // sort: per-key counts, then running offsets (up to kMaxSortKeys)
+    float4* s_o;             // shadow ray: o.xyz | tmax
+    float4* s_d;             // shadow ray: d.xyz | path index bits
+    float4* s_c;             // shadow ray: contribution.rgb | light index bits
+    float4* L;               // per path (wave-local): radiance.rgb | -
+    uint32_t* counts;        // [0] active, [1] next, [2] shadow, [3] sort key count
+    unsigned long long* hist;  // [b] extension rays of bounce b, [64 + b] shadow rays of bounce b
+    uint32_t* sig;           // per path (global id) branch signature, or null
+    uint32_t capacity;
+};
+
+constexpr uint32_t kMaxSortKeys = 4096;
+
+}  // namespace pt

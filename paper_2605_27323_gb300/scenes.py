@@ -11,7 +11,9 @@ procedural scenes below stand in for it:
 * ``box_scene``     -- tiny closed-ish box: 5 walls (10 tris), two axis-aligned boxes (24 tris),
                        a 2-triangle ceiling light with emission 15; 128x128, 16 spp, depth 8.
 * ``spheres_scene`` -- 200 level-4 icospheres (5,120 tris each, radii lognormal(0, 0.5)) resting
-                       on a 256x256-quad ground; 60% Lambert / 30% GGX / 10% glass; 8 emissive quads
+                       on a 256x256-quad ground (the spheres cover its central 56%, the camera looks
+                       down so geometry fills most of the frame); 60% Lambert / 30% GGX / 10% glass;
+                       8 emissive quads
                        plus a constant environment; 1920x1080, 1 spp, depth 5.
 * ``terrain_scene`` -- 2048x2048 fBm heightfield plus 5000 level-2 icospheres, 64 emissive quads;
                        3840x2160, 4 spp, depth 8.
@@ -223,7 +225,8 @@ def spheres_scene(seed: int = 0, n_spheres=200, level=4, ground_quads=256, n_lig
     ground_mat, light_mat = n_sph_mats, n_sph_mats + 1
     for k in range(n_spheres):
         b.add(S * radii[k] + np.array([cx[k], radii[k], cz[k]]), ST, sph_mat[k])
-    GV, GT = grid_mesh(ground_quads, -extent, extent, -extent, extent)
+    g = 2.5 * extent
+    GV, GT = grid_mesh(ground_quads, -g, g, -g, g)
     b.add(GV, GT, ground_mat)
     for k in range(n_lights):
         ang = 2 * np.pi * k / n_lights
@@ -236,7 +239,7 @@ def spheres_scene(seed: int = 0, n_spheres=200, level=4, ground_quads=256, n_lig
     emission = np.zeros(len(types))
     emission[light_mat] = 15.0
     mats = _materials(types, albedo, emission, rough, np.full(len(types), 1.5))
-    cam = camera((0.0, 0.35 * extent, 1.05 * extent), (0.0, 0.0, 0.0), (0, 1, 0), 50.0, width, height)
+    cam = camera((0.0, 0.5 * extent, 0.95 * extent), (0.0, 0.0, -0.1 * extent), (0, 1, 0), 50.0, width, height)
     return _scene(b, mats, (0.1, 0.1, 0.1), camera=cam, spp=1, max_depth=5, rr_start=3)
 
 

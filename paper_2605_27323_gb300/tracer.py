@@ -1,0 +1,256 @@
+"""Python front of the C ABI: scenes, renders, gradients and batches on torch device memory.
+
+torch provides device buffers and the current CUDA stream; every computation runs in libpt.so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import capi
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA device is required (libpt.so has no CPU path)")
+    return torch
+
+
+def _stream(torch):
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(None)
+
+
+def make_camera(cam: dict) -> capi.Camera:
+    c = capi.Camera()
+    for k in ("eye", "target", "up"):
+        getattr(c, k)[:] = [float(x) for x in np.asarray(cam[k], np.float32)]
+    c.vfov_deg = float(cam["vfov_deg"])
+    c.width = int(cam["width"])
+    c.height = int(cam["height"])
+    return c
+
+
+def make_opts(mode="wavefront", rr_start=3, rr_fixed=0.0, sort="none", block_size=0, queue_capacity=0,
+              profile=False, sig=None, graph=True) -> capi.RenderOpts:
+    o = capi.RenderOpts()
+    o.mode = capi.MODE[mode] if isinstance(mode, str) else int(mode)
+    o.rr_start = int(rr_start)
+    o.rr_fixed = float(rr_fixed)
+    o.sort_mode = capi.SORT[sort] if isinstance(sort, str) else int(sort)
+    o.block_size = int(block_size)
+    o.flags = (capi.FLAG_PROFILE if profile else 0) | (0 if graph else capi.FLAG_NO_GRAPH)
+    o.queue_capacity = int(queue_capacity)
+    o.d_path_sig = sig.data_ptr() if sig is not None else None
+    return o
+
+
+class Scene:
+    """A scene uploaded to the current CUDA device (pt_scene_create)."""
+
+    def __init__(self, verts, tris, tri_mat, mat_type, mat_albedo, mat_emission, mat_roughness, mat_ior,
+                 env=(0.0, 0.0, 0.0)):
+        torch = _torch()
+        self._lib = capi.load()
+        v = np.ascontiguousarray(verts, np.float32).reshape(-1, 3)
+        t = np.ascontiguousarray(tris, np.uint32).reshape(-1, 3)
+        tm = np.ascontiguousarray(tri_mat, np.uint32).reshape(-1)
+        n_m = int(np.asarray(mat_type).size)
+        mats = (capi.Material * max(n_m, 1))()
+        mt = np.asarray(mat_type, np.uint32).reshape(-1)
+        ma = np.asarray(mat_albedo, np.float32).reshape(-1, 3)
+        me = np.asarray(mat_emission, np.float32).reshape(-1)
+        mr = np.asarray(mat_roughness, np.float32).reshape(-1)
+        mi = np.asarray(mat_ior, np.float32).reshape(-1)
+        for k in range(n_m):
+            mats[k].type = int(mt[k])
+            mats[k].albedo[:] = [float(x) for x in ma[k]]
+            mats[k].emission = float(me[k])
+            mats[k].roughness = float(mr[k])
+            mats[k].ior = float(mi[k])
+        envv = (C.c_float * 3)(*[float(x) for x in np.asarray(env, np.float32).reshape(3)])
+        h = C.c_void_p()
+        capi.check(self._lib.pt_scene_create(v.ctypes.data_as(C.c_void_p), v.shape[0], t.ctypes.data_as(C.c_void_p),
+                                             t.shape[0], tm.ctypes.data_as(C.c_void_p), mats, n_m, envv,
+                                             _stream(torch), C.byref(h)))
+        self.h = h
+        self.n_mats = n_m
+        self.n_tris = t.shape[0]
+
+    @classmethod
+    def from_dict(cls, sc: dict) -> "Scene":
+        return cls(sc["verts"], sc["tris"], sc["tri_mat"], sc["mat_type"], sc["mat_albedo"], sc["mat_emission"],
+                   sc["mat_roughness"], sc["mat_ior"], sc["env"])
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self._lib.pt_scene_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        a, b, c, e = C.c_uint64(), C.c_uint64(), C.c_uint64(), C.c_uint64()
+        area = C.c_float()
+        capi.check(self._lib.pt_scene_info(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(area), C.byref(e)))
+        return {"n_tris": a.value, "n_nodes": b.value, "n_lights": c.value, "light_area": area.value,
+                "device_bytes": e.value}
+
+    def set_materials(self, albedo=None, emission=None):
+        torch = _torch()
+        a = albedo.detach().to(device="cuda", dtype=torch.float32).contiguous() if albedo is not None else None
+        e = emission.detach().to(device="cuda", dtype=torch.float32).contiguous() if emission is not None else None
+        capi.check(self._lib.pt_scene_set_materials(self.h, _ptr(a), _ptr(e), _stream(torch)))
+        self._keep = (a, e)
+
+    def render(self, cam: dict, spp: int, max_depth: int, seed: int = 0, out=None, path_L: bool = False,
+               sig: bool = False, **opt_kw):
+        """Render an H x W x 3 float32 image (torch CUDA tensor, or the given `out`, which may be a
+        pinned/pageable CPU tensor: the library then stages the copy).  With path_L / sig the
+        per-path radiance (N_p x 3) and branch signatures (N_p) are returned too."""
+        torch = _torch()
+        c = make_camera(cam)
+        W, H = c.width, c.height
+        n_paths = W * H * spp
+        img = out if out is not None else torch.empty((H, W, 3), device="cuda", dtype=torch.float32)
+        pl = torch.empty((n_paths, 3), device="cuda", dtype=torch.float32) if path_L else None
+        sg = torch.empty((n_paths,), device="cuda", dtype=torch.int32) if sig else None
+        o = make_opts(sig=sg, **opt_kw)
+        capi.check(self._lib.pt_render(self.h, C.byref(c), spp, max_depth, seed, C.byref(o), _ptr(img), _ptr(pl),
+                                       _stream(torch)))
+        if path_L or sig:
+            return {"img": img, "path_L": pl, "sig": sg}
+        return img
+
+    def backward(self, cam: dict, spp: int, max_depth: int, seed: int, grad_img, g_albedo=None, g_emission=None,
+                 **opt_kw):
+        """Accumulate d(loss)/d(albedo) (n_mats x 3) and d(loss)/d(emission) (n_mats) for the image
+        of render(cam, spp, max_depth, seed) given grad_img = d(loss)/d(image)."""
+        torch = _torch()
+        c = make_camera(cam)
+        g = grad_img.detach().to(dtype=torch.float32).contiguous()
+        if g_albedo is None:
+            g_albedo = torch.zeros((self.n_mats, 3), device="cuda", dtype=torch.float32)
+        if g_emission is None:
+            g_emission = torch.zeros((self.n_mats,), device="cuda", dtype=torch.float32)
+        o = make_opts(**opt_kw)
+        capi.check(self._lib.pt_render_backward(self.h, C.byref(c), spp, max_depth, seed, C.byref(o), _ptr(g),
+                                                _ptr(g_albedo), _ptr(g_emission), _stream(torch)))
+        return g_albedo, g_emission
+
+    def trace_closest(self, o, d):
+        """Closest hits of rays (n x 3 origins, n x 3 directions): (t, original triangle id or -1)."""
+        torch = _torch()
+        o = torch.as_tensor(o, dtype=torch.float32, device="cuda").reshape(-1, 3)
+        d = torch.as_tensor(d, dtype=torch.float32, device="cuda").reshape(-1, 3)
+        n = o.shape[0]
+        rays = torch.zeros((n, 8), device="cuda", dtype=torch.float32)
+        rays[:, 0:3] = o
+        rays[:, 4:7] = d
+        t = torch.empty(n, device="cuda", dtype=torch.float32)
+        prim = torch.empty(n, device="cuda", dtype=torch.int32)
+        capi.check(self._lib.pt_trace_closest(self.h, _ptr(rays), n, _ptr(t), _ptr(prim), _stream(torch)))
+        return t, prim
+
+    def stats(self) -> dict:
+        s = capi.Stats()
+        capi.check(self._lib.pt_get_stats(self.h, C.byref(s)))
+        d = {k: getattr(s, k) for k, _ in capi.Stats._fields_ if k != "active"}
+        d["active"] = list(s.active)[: s.bounces]
+        return d
+
+
+def debug_rng(seed: int, pixel, sample, bounce, dim):
+    torch = _torch()
+    lib = capi.load()
+    ts = [torch.as_tensor(np.ascontiguousarray(a, np.uint32).astype(np.int32), device="cuda") for a in
+          (pixel, sample, bounce, dim)]
+    n = ts[0].numel()
+    out = torch.empty(n, device="cuda", dtype=torch.float32)
+    capi.check(lib.pt_debug_rng(seed, *[_ptr(t) for t in ts], n, _ptr(out), _stream(torch)))
+    return out
+
+
+def render_batch(scenes: Sequence[Scene], cams: Sequence[dict], spps: Sequence[int], max_depth: int, seed: int = 0,
+                 outs: Optional[list] = None, **opt_kw):
+    """Render several scenes in one persistent wavefront (pt_render_batch)."""
+    torch = _torch()
+    lib = capi.load()
+    n = len(scenes)
+    cam_arr = (capi.Camera * n)(*[make_camera(c) for c in cams])
+    spp_arr = (C.c_uint32 * n)(*[int(s) for s in spps])
+    if outs is None:
+        outs = [torch.empty((int(c["height"]), int(c["width"]), 3), device="cuda", dtype=torch.float32) for c in cams]
+    sc_arr = (C.c_void_p * n)(*[s.h.value for s in scenes])
+    out_arr = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    o = make_opts(**opt_kw)
+    capi.check(lib.pt_render_batch(sc_arr, cam_arr, spp_arr, n, max_depth, seed, C.byref(o), out_arr,
+                                   _stream(torch)))
+    return outs
+
+
+def autotune_batch(scenes: Sequence[Scene], cams: Sequence[dict], spps: Sequence[int], max_depth: int, seed: int = 0,
+                   outs: Optional[list] = None, **opt_kw):
+    """Pick queue capacity, block size and sort granularity for render_batch by timing candidates."""
+    torch = _torch()
+    lib = capi.load()
+    n = len(scenes)
+    cam_arr = (capi.Camera * n)(*[make_camera(c) for c in cams])
+    spp_arr = (C.c_uint32 * n)(*[int(s) for s in spps])
+    if outs is None:
+        outs = [torch.empty((int(c["height"]), int(c["width"]), 3), device="cuda", dtype=torch.float32) for c in cams]
+    sc_arr = (C.c_void_p * n)(*[s.h.value for s in scenes])
+    out_arr = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    base = make_opts(**opt_kw)
+    best = capi.RenderOpts()
+    ms = C.c_float()
+    capi.check(lib.pt_autotune_batch(sc_arr, cam_arr, spp_arr, n, max_depth, seed, C.byref(base), out_arr,
+                                     _stream(torch), C.byref(best), C.byref(ms)))
+    return {"queue_capacity": best.queue_capacity, "block_size": best.block_size, "sort": best.sort_mode,
+            "ms": ms.value}
+
+
+def _autograd_fn():
+    import torch
+
+    class PTRenderFn(torch.autograd.Function):
+        """image = render(albedo, emission); backward = path-replay adjoint (pt_render_backward)."""
+
+        @staticmethod
+        def forward(ctx, albedo, emission, scene: Scene, cam: dict, spp: int, max_depth: int, seed: int,
+                    opt_kw: dict):
+            scene.set_materials(albedo, emission)
+            img = scene.render(cam, spp, max_depth, seed, **(opt_kw or {}))
+            ctx.scene, ctx.cam, ctx.spp, ctx.max_depth, ctx.seed, ctx.opt_kw = scene, cam, spp, max_depth, seed, opt_kw
+            return img
+
+        @staticmethod
+        def backward(ctx, grad_img):
+            kw = dict(ctx.opt_kw or {})
+            kw.pop("mode", None)
+            ga, ge = ctx.scene.backward(ctx.cam, ctx.spp, ctx.max_depth, ctx.seed, grad_img.contiguous(), **kw)
+            return ga, ge, None, None, None, None, None, None
+
+    return PTRenderFn
+
+
+_PTRenderFn = None
+
+
+def render_differentiable(albedo, emission, scene: Scene, cam: dict, spp: int, max_depth: int, seed: int = 0,
+                          **opt_kw):
+    """Differentiable render: gradients flow to albedo (n_mats x 3) and emission (n_mats)."""
+    global _PTRenderFn
+    if _PTRenderFn is None:
+        _PTRenderFn = _autograd_fn()
+    return _PTRenderFn.apply(albedo, emission, scene, cam, spp, max_depth, seed, opt_kw)
