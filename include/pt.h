@@ -19,7 +19,7 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls are
  *    asynchronous on that stream unless stated otherwise; errors in arguments are reported
  *    synchronously by the return value, device-side faults (traversal step cap, queue overflow)
- *    are recorded in a device status word and reported by pt_get_stats / pt_scene_sync.
+ *    are recorded in a device status word and reported by pt_get_stats.
  *  - Nothing throws; every failure returns a pt_status and sets a thread-local message
  *    (pt_last_error).
  *  - Images are row-major H x W x 3 float32 (linear RGB), row 0 at the top.  Path p = pixel * spp
@@ -80,7 +80,7 @@ typedef struct {
     uint32_t rr_start;          /* first bounce with Russian roulette (Sec. 3.1); >= max_depth: off */
     float rr_fixed;             /* > 0: fixed survival probability; 0: q = clamp(max(tp), .05, .95) */
     uint32_t sort_mode;         /* wavefront: PT_SORT_* key sort before shading */
-    uint32_t block_size;        /* threads per block: 0 = default, else a multiple of 32 in [64, 1024] */
+    uint32_t block_size;        /* threads per block: 0 = default, else a multiple of 32 in [64, 256] */
     uint32_t flags;             /* PT_FLAG_* */
     uint64_t queue_capacity;    /* wavefront: paths per wave; 0 = all paths in one wave */
     uint32_t* d_path_sig;       /* optional device N_p u32: per-path branch signature (testing) */
@@ -169,6 +169,17 @@ pt_status pt_get_stats(pt_scene* scene, pt_stats* out);
  * bounce[i], dim[i]) in [0, 1) on a 2^-24 grid (device arrays, n entries). */
 pt_status pt_debug_rng(uint64_t seed, const uint32_t* d_pixel, const uint32_t* d_sample, const uint32_t* d_bounce,
                        const uint32_t* d_dim, uint32_t n, float* d_out, void* stream);
+
+/* Event logs of selected paths, traced by the megakernel's per-path code (testing aid: find the
+ * first decision where two implementations of the estimator part ways).  d_path_ids: device n
+ * uint64 path ids; d_events: device n x 64 x 2 uint32 pairs (bounce << 4 | kind, value) with kind
+ * 0 = hit (value: triangle id, 0xFFFFFFFF = miss), 1 = NEE (light << 2 | cast << 1 | visible),
+ * 2 = BSDF outcome code, 3 = roulette survival; d_payload: device n x 64 x 2 float diagnostics per
+ * event (hit: t, throughput.x; NEE: the two cosines; BSDF: weight.x, direction.x; roulette: q, u);
+ * d_n_events: device n uint32; d_path_L: device n x 3 float radiance. */
+pt_status pt_debug_trace_paths(pt_scene* scene, const pt_camera* cam, uint32_t spp, uint32_t max_depth, uint64_t seed,
+                               const pt_render_opts* opts, const uint64_t* d_path_ids, uint32_t n, uint32_t* d_events,
+                               float* d_payload, uint32_t* d_n_events, float* d_path_L, void* stream);
 
 /* Scene facts: triangle, node, light counts, total light area, device bytes held. */
 pt_status pt_scene_info(const pt_scene* scene, uint64_t* n_tris, uint64_t* n_nodes, uint64_t* n_lights,

@@ -90,6 +90,8 @@ def lib():
             L.or_render_pixels.argtypes = [vp, vp, vp, vp, f32, u32, u32, u32, u32, u64, u32, f64, i32,
                                            vp, i64, i32, vp, vp]
             L.or_trace_rays.argtypes = [vp, vp, vp, vp, i64, u32, u32, f64, i32, i32, vp, vp, i32, vp, vp]
+            L.or_trace_path_events.argtypes = [vp, vp, vp, vp, f32, u32, u32, u32, u32, u64, u32, f64, vp, i64, vp,
+                                               vp, vp, vp]
             L.or_max_tangents.restype = i32
             _lib = L
     return _lib
@@ -247,6 +249,20 @@ class Scene:
                                rr_start, float(rr_fixed), int(use_bvh), _p(px), px.size, n_threads,
                                _p(img), _p(rays))
         return img, rays
+
+    def path_events(self, cam, spp, max_depth, seed, path_ids, rr_start=3, rr_fixed=0.0):
+        """Event logs of the listed camera paths: list of [(bounce, kind, value, f0, f1), ...]."""
+        eye, tgt, up, fov, W, H = self._cam(cam)
+        ids = _f(path_ids, np.uint64).reshape(-1)
+        n = ids.size
+        ev = np.zeros((n, 64, 2), np.uint32)
+        pay = np.zeros((n, 64, 2))
+        n_ev = np.zeros(n, np.uint32)
+        L = np.zeros((n, 3))
+        lib().or_trace_path_events(self.h, _p(eye), _p(tgt), _p(up), fov, W, H, spp, max_depth, seed, rr_start,
+                                   float(rr_fixed), _p(ids), n, _p(ev), _p(pay), _p(n_ev), _p(L))
+        return [[(int(ev[i, k, 0] >> 4), int(ev[i, k, 0] & 15), int(ev[i, k, 1]), float(pay[i, k, 0]),
+                  float(pay[i, k, 1])) for k in range(n_ev[i])] for i in range(n)], L
 
     def trace_rays(self, o, d, keys, max_depth, rr_start=1 << 30, rr_fixed=0.0, use_bvh=True,
                    dir_albedo=None, dir_emission=None, n_threads=0):

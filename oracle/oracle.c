@@ -638,6 +638,24 @@ typedef struct {
     int use_bvh;
 } ropts;
 
+/* Optional per-path event log (testing aid): up to OR_MAX_EVENTS events of (bounce << 4 | kind,
+ * value) with two diagnostic numbers each. */
+#define OR_MAX_EVENTS 64
+typedef struct {
+    uint32_t* ev;      /* OR_MAX_EVENTS x 2 */
+    double* pay;       /* OR_MAX_EVENTS x 2 */
+    uint32_t n;
+} evlog;
+
+static void log_event(evlog* lg, uint32_t b, uint32_t kind, uint32_t value, double f0, double f1) {
+    if (!lg || lg->n >= OR_MAX_EVENTS) return;
+    lg->ev[2 * lg->n] = (b << 4) | kind;
+    lg->ev[2 * lg->n + 1] = value;
+    lg->pay[2 * lg->n] = f0;
+    lg->pay[2 * lg->n + 1] = f1;
+    lg->n++;
+}
+
 /* Branch signature: XOR over the path's events of hash(hash((bounce << 4) | kind) ^ value), so the
  * order in which a pipeline learns the events does not matter.  kind 0: hit triangle id (miss:
  * 0xFFFFFFFF); 1: NEE (light index << 2 | shadow ray cast << 1 | visible); 2: BSDF outcome code;
@@ -660,7 +678,7 @@ static int64_t pick_light(const or_scene* s, double u) {
 /* One path from ray (o, d).  Adds radiance into L (dual), counts rays, writes the branch
  * signature.  Follows the steps of Sec. 2.2 with NEE (Sec. 3) and Russian roulette (Sec. 3.1). */
 static void trace(const or_scene* s, v3 o, v3 d, uint32_t key, const ropts* op, const dirs_t* dr,
-                  dc* L_out, uint32_t* sig_out, uint64_t rays[2]) {
+                  dc* L_out, uint32_t* sig_out, uint64_t rays[2], evlog* lg) {
     int nd = dr->nd;
     dc tp = dc_const(1, 1, 1), L = dc_const(0, 0, 0);
     int prev_delta = 1;
@@ -673,9 +691,11 @@ static void trace(const or_scene* s, v3 o, v3 d, uint32_t key, const ropts* op, 
         if (tri < 0) {
             L = dc_add(L, dc_mul(tp, dc_const(s->env[0], s->env[1], s->env[2]), nd), nd);
             sig ^= sig_event(b, 0, 0xFFFFFFFFu);
+            log_event(lg, b, 0, 0xFFFFFFFFu, INFINITY, tp.v[0]);
             break;
         }
         sig ^= sig_event(b, 0, (uint32_t)tri);
+        log_event(lg, b, 0, (uint32_t)tri, t, tp.v[0]);
         v3 ng = nrm(cross(sub(s->p1[tri], s->p0[tri]), sub(s->p2[tri], s->p0[tri])));
         v3 x = add(o, scl(d, t));
         int64_t mi = s->mat[tri];
@@ -717,11 +737,13 @@ static void trace(const or_scene* s, v3 o, v3 d, uint32_t key, const ropts* op, 
                 }
             }
             sig ^= sig_event(b, 1, ((uint32_t)j << 2) | (cast << 1) | vis);
+            log_event(lg, b, 1, ((uint32_t)j << 2) | (cast << 1) | vis, cx, cl);
         }
         /* step 4: sample a new direction and update the throughput (Eq. 3) */
         bsample bs = bsdf_sample(m, a, n, ng, wo, or_u01(key, b, D_LOBE), or_u01(key, b, D_DIR0),
                                  or_u01(key, b, D_DIR1), nd);
         sig ^= sig_event(b, 2, (uint32_t)bs.code);
+        log_event(lg, b, 2, (uint32_t)bs.code, bs.weight.v[0], bs.wi.x);
         if (!bs.valid) break;
         tp = dc_mul(tp, bs.weight, nd);
         prev_delta = bs.delta;
@@ -736,6 +758,7 @@ static void trace(const or_scene* s, v3 o, v3 d, uint32_t key, const ropts* op, 
             }
             int survive = or_u01(key, b, D_RR) < q;
             sig ^= sig_event(b, 3, (uint32_t)survive);
+            log_event(lg, b, 3, (uint32_t)survive, q, or_u01(key, b, D_RR));
             if (!survive) break;
             tp = dc_scale(tp, 1.0 / q, nd);
         }
@@ -801,7 +824,7 @@ void or_render_paths(const or_scene* s, const float* eye, const float* target, c
         dc L;
         uint32_t sig;
         uint64_t rays[2] = {0, 0};
-        trace(s, o, d, key, &op, &dr, &L, &sig, rays);
+        trace(s, o, d, key, &op, &dr, &L, &sig, rays, NULL);
         for (int c = 0; c < 3; ++c) L_out[3 * i + c] = L.v[c];
         if (dL_out)
             for (int k = 0; k < dr.nd; ++k)
@@ -832,7 +855,7 @@ void or_render_pixels(const or_scene* s, const float* eye, const float* target, 
             dc L;
             uint32_t sig;
             uint64_t rays[2] = {0, 0};
-            trace(s, o, d, key, &op, &dr, &L, &sig, rays);
+            trace(s, o, d, key, &op, &dr, &L, &sig, rays, NULL);
             for (int c = 0; c < 3; ++c) acc[c] += L.v[c];
             r0 += rays[0];
             r1 += rays[1];
@@ -854,11 +877,35 @@ void or_trace_rays(const or_scene* s, const double* o, const double* d, const ui
         uint32_t sig;
         uint64_t rays[2] = {0, 0};
         trace(s, mk(o[3 * i], o[3 * i + 1], o[3 * i + 2]), nrm(mk(d[3 * i], d[3 * i + 1], d[3 * i + 2])), keys[i],
-              &op, &dr, &L, &sig, rays);
+              &op, &dr, &L, &sig, rays, NULL);
         for (int c = 0; c < 3; ++c) L_out[3 * i + c] = L.v[c];
         if (dL_out)
             for (int k = 0; k < dr.nd; ++k)
                 for (int c = 0; c < 3; ++c) dL_out[((size_t)i * dr.nd + k) * 3 + c] = L.d[k][c];
+    }
+}
+
+/* Event logs of the listed paths (testing aid: locate the first decision where two
+ * implementations part ways).  ev: n x 64 x 2 u32, pay: n x 64 x 2 f64, n_ev: n. */
+void or_trace_path_events(const or_scene* s, const float* eye, const float* target, const float* up, float vfov_deg,
+                          uint32_t W, uint32_t H, uint32_t spp, uint32_t max_depth, uint64_t seed, uint32_t rr_start,
+                          double rr_fixed, const uint64_t* path_ids, int64_t n, uint32_t* ev, double* pay,
+                          uint32_t* n_ev, double* L_out) {
+    ocam cam = make_cam(eye, target, up, vfov_deg, W, H);
+    ropts op = {max_depth, rr_start, rr_fixed, 1};
+    dirs_t dr = {0, s->n_mats, NULL, NULL};
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t pixel = (uint32_t)(path_ids[i] / spp), sample = (uint32_t)(path_ids[i] % spp);
+        uint32_t key = or_path_key(seed, pixel, sample);
+        v3 o, d;
+        camera_ray(&cam, pixel, key, &o, &d);
+        evlog lg = {ev + (size_t)i * 2 * OR_MAX_EVENTS, pay + (size_t)i * 2 * OR_MAX_EVENTS, 0};
+        dc L;
+        uint32_t sig;
+        uint64_t rays[2] = {0, 0};
+        trace(s, o, d, key, &op, &dr, &L, &sig, rays, &lg);
+        n_ev[i] = lg.n;
+        for (int c = 0; c < 3; ++c) L_out[3 * i + c] = L.v[c];
     }
 }
 

@@ -707,6 +707,34 @@ pt_status pt_debug_rng(uint64_t seed, const uint32_t* px, const uint32_t* sm, co
     return PT_OK;
 }
 
+pt_status pt_debug_trace_paths(pt_scene* sc, const pt_camera* cam, uint32_t spp, uint32_t max_depth, uint64_t seed,
+                               const pt_render_opts* opts, const uint64_t* d_path_ids, uint32_t n, uint32_t* d_events,
+                               float* d_payload, uint32_t* d_n_events, float* d_path_L, void* stream) {
+    if (!sc) return fail(PT_ERR_INVALID_ARG, "scene is NULL");
+    if (spp == 0) return fail(PT_ERR_INVALID_ARG, "spp must be >= 1");
+    if (max_depth > 64) return fail(PT_ERR_INVALID_ARG, "max_depth must be <= 64");
+    if (n == 0) return PT_OK;
+    if (!d_path_ids || !d_events || !d_payload || !d_n_events || !d_path_L) return fail(PT_ERR_INVALID_ARG, "NULL buffer");
+    pt_render_opts o = opts ? *opts : default_opts();
+    PT_TRY(check_opts(o));
+    pt::DevCamera dc;
+    PT_TRY(make_camera(cam, dc));
+    std::lock_guard<std::mutex> g(sc->mu);
+    PT_TRY(set_device(sc));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    sc->last_stream = st;
+    pt::RenderParams p;
+    p.seed = seed;
+    p.path_begin = 0;
+    p.spp = spp;
+    p.max_depth = max_depth;
+    p.rr_start = o.rr_start;
+    p.rr_fixed = o.rr_fixed;
+    PT_CUDA(pt::launch_debug_paths(st, sc->view(), dc, p, reinterpret_cast<const unsigned long long*>(d_path_ids), n,
+                                   d_events, d_payload, d_n_events, d_path_L));
+    return PT_OK;
+}
+
 pt_status pt_get_stats(pt_scene* sc, pt_stats* out) {
     if (!sc || !out) return fail(PT_ERR_INVALID_ARG, "NULL argument");
     std::lock_guard<std::mutex> g(sc->mu);

@@ -277,6 +277,7 @@ struct Vertex {
     float3 emit;            // tp * Le when counted
     bool last;              // b == max_depth - 1: stop after emission
     bool nee;               // an NEE light sample was drawn (non-delta material, lights exist)
+    float nee_cx, nee_cl;   // the two cosines that decide whether the shadow ray is cast
     uint32_t light_j;       // light index drawn
     uint32_t light_mat;     // its material
     bool cast;              // shadow ray needed (both cosines positive)
@@ -291,6 +292,7 @@ struct Vertex {
     float3 w;               // throughput multiplier of this vertex (BSDF weight / q)
     float3 dwa;             // d w / d albedo
     int rr;                 // -1: no roulette at this bounce, 0: killed, 1: survived
+    float rr_q;             // survival probability used
     float3 no, nd, ntp;     // continuation ray and throughput
 };
 
@@ -327,6 +329,9 @@ __device__ __forceinline__ Vertex shade_vertex(const DevScene& s, const RenderPa
     V.cast = false;
     V.cont = false;
     V.rr = -1;
+    V.rr_q = 0.f;
+    V.nee_cx = 0.f;
+    V.nee_cl = 0.f;
     V.light_j = 0;
     V.light_mat = 0;
     V.nee_g = f3(0.f, 0.f, 0.f);
@@ -359,6 +364,8 @@ __device__ __forceinline__ Vertex shade_vertex(const DevScene& s, const RenderPa
         float dist2 = dot(dv, dv), dist = sqrtf(dist2);
         float3 wi = dv * (1.0f / dist);
         float cx = dot(n, wi), cl = -dot(wi, nl);
+        V.nee_cx = cx;
+        V.nee_cl = cl;
         if (cx > 0.0f && cl > 0.0f) {
             V.cast = true;
             BsdfEval fe = bsdf_eval(m, n, wo, wi);
@@ -383,6 +390,7 @@ __device__ __forceinline__ Vertex shade_vertex(const DevScene& s, const RenderPa
     V.delta = bs.delta;
     if (b >= p.rr_start) {
         float q = p.rr_fixed > 0.0f ? p.rr_fixed : fminf(fmaxf(maxc(ntp), 0.05f), 0.95f);
+        V.rr_q = q;
         bool survive = u01(key, b, D_RR) < q;
         V.rr = survive ? 1 : 0;
         if (!survive) return V;

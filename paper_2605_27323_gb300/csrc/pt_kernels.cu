@@ -40,67 +40,119 @@ __device__ __forceinline__ void warp_add_u64(unsigned long long* dst, unsigned l
 __device__ __forceinline__ float4 f4(float3 a, float w) { return make_float4(a.x, a.y, a.z, w); }
 
 // ================================================================== megakernel
+// Event recorders of one path (compile-time: the production kernel records nothing).
+struct NoRec {
+    __device__ __forceinline__ void ev(uint32_t, uint32_t, uint32_t, float, float) {}
+};
+struct SigRec {   // order-free branch signature
+    uint32_t sg = 0;
+    __device__ __forceinline__ void ev(uint32_t b, uint32_t k, uint32_t v, float, float) { sg ^= sig_event(b, k, v); }
+};
+struct LogRec {   // event list with two diagnostic numbers per event (testing aid)
+    uint32_t* ev_u;
+    float* ev_f;
+    uint32_t n = 0;
+    __device__ __forceinline__ void ev(uint32_t b, uint32_t k, uint32_t v, float f0, float f1) {
+        if (n >= kMaxEvents) return;
+        ev_u[2 * n] = (b << 4) | k;
+        ev_u[2 * n + 1] = v;
+        ev_f[2 * n] = f0;
+        ev_f[2 * n + 1] = f1;
+        ++n;
+    }
+};
+
+// One whole path (Sec. 2.2 steps 1-5) in registers: the body of the megakernel.
+template <class Rec>
+__device__ __forceinline__ float3 mk_path(const DevScene& s, const DevCamera& c, const RenderParams& p, uint64_t path,
+                                          Rec& rec, unsigned long long& n_ext, unsigned long long& n_shd) {
+    const float3 env = f3(s.env_r, s.env_g, s.env_b);
+    const uint32_t pixel = (uint32_t)(path / p.spp);
+    const uint32_t sample = (uint32_t)(path - (uint64_t)pixel * p.spp);
+    const uint32_t key = path_key(p.seed, pixel, sample);
+    float3 o, d;
+    camera_ray(c, pixel, key, o, d);                           // step 1
+    float3 tp = f3(1.f, 1.f, 1.f), L = f3(0.f, 0.f, 0.f);
+    bool prev_delta = true;
+    for (uint32_t b = 0; b < p.max_depth; ++b) {
+        ++n_ext;
+        Hit h = trace_closest(s, o, d);                        // step 2
+        if (h.tri == kMiss) {
+            L = add_rn(L, mul_rn(tp, env));
+            rec.ev(b, 0, kMiss, __int_as_float(0x7f800000), tp.x);
+            break;
+        }
+        Vertex V = shade_vertex(s, p, key, b, o, d, tp, prev_delta, h.t, h.tri);
+        rec.ev(b, 0, V.prim, h.t, tp.x);
+        if (V.emit_counted) L = add_rn(L, V.emit);             // step 3
+        if (V.last) break;
+        if (V.nee) {                                           // shadow evaluation
+            uint32_t vis = 0;
+            if (V.cast) {
+                ++n_shd;
+                vis = trace_any(s, V.s_o, V.s_d, V.s_tmax) ? 0u : 1u;
+                if (vis) L = add_rn(L, V.contrib);
+            }
+            rec.ev(b, 1, (V.light_j << 2) | ((uint32_t)V.cast << 1) | vis, V.nee_cx, V.nee_cl);
+        }
+        rec.ev(b, 2, V.bsdf_code, V.w.x, V.nd.x);
+        if (V.rr >= 0) rec.ev(b, 3, (uint32_t)V.rr, V.rr_q, u01(key, b, D_RR));
+        if (!V.cont) break;                                    // step 4 done; step 5: repeat
+        o = V.no;
+        d = V.nd;
+        tp = V.ntp;
+        prev_delta = V.delta;
+    }
+    return L;
+}
+
 template <bool SIG>
 __global__ void __launch_bounds__(256) k_megakernel(DevScene s, DevCamera c, RenderParams p, uint64_t n_paths,
                                                     float* __restrict__ out_L, float* __restrict__ img,
                                                     uint32_t* __restrict__ sig, unsigned long long* __restrict__ rays) {
     unsigned long long n_ext = 0, n_shd = 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const float3 env = f3(s.env_r, s.env_g, s.env_b);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_paths; i += stride) {
         const uint64_t path = p.path_begin + i;
-        const uint32_t pixel = (uint32_t)(path / p.spp);
-        const uint32_t sample = (uint32_t)(path - (uint64_t)pixel * p.spp);
-        const uint32_t key = path_key(p.seed, pixel, sample);
-        float3 o, d;
-        camera_ray(c, pixel, key, o, d);                       // step 1
-        float3 tp = f3(1.f, 1.f, 1.f), L = f3(0.f, 0.f, 0.f);
-        bool prev_delta = true;
-        uint32_t sg = 0;
-        for (uint32_t b = 0; b < p.max_depth; ++b) {
-            ++n_ext;
-            Hit h = trace_closest(s, o, d);                    // step 2
-            if (h.tri == kMiss) {
-                L = add_rn(L, mul_rn(tp, env));
-                if (SIG) sg ^= sig_event(b, 0, kMiss);
-                break;
-            }
-            Vertex V = shade_vertex(s, p, key, b, o, d, tp, prev_delta, h.t, h.tri);
-            if (SIG) sg ^= sig_event(b, 0, V.prim);
-            if (V.emit_counted) L = add_rn(L, V.emit);         // step 3
-            if (V.last) break;
-            if (V.nee) {                                       // shadow evaluation
-                uint32_t vis = 0;
-                if (V.cast) {
-                    ++n_shd;
-                    vis = trace_any(s, V.s_o, V.s_d, V.s_tmax) ? 0u : 1u;
-                    if (vis) L = add_rn(L, V.contrib);
-                }
-                if (SIG) sg ^= sig_event(b, 1, (V.light_j << 2) | ((uint32_t)V.cast << 1) | vis);
-            }
-            if (SIG) {
-                sg ^= sig_event(b, 2, V.bsdf_code);
-                if (V.rr >= 0) sg ^= sig_event(b, 3, (uint32_t)V.rr);
-            }
-            if (!V.cont) break;                                // step 4 done; step 5: repeat
-            o = V.no;
-            d = V.nd;
-            tp = V.ntp;
-            prev_delta = V.delta;
+        float3 L;
+        if (SIG) {
+            SigRec r;
+            L = mk_path(s, c, p, path, r, n_ext, n_shd);
+            sig[path] = r.sg;
+        } else {
+            NoRec r;
+            L = mk_path(s, c, p, path, r, n_ext, n_shd);
         }
         if (out_L) {
             out_L[3 * i] = L.x;
             out_L[3 * i + 1] = L.y;
             out_L[3 * i + 2] = L.z;
         } else {
+            const uint32_t pixel = (uint32_t)(path / p.spp);
             img[3 * (size_t)pixel] = L.x;
             img[3 * (size_t)pixel + 1] = L.y;
             img[3 * (size_t)pixel + 2] = L.z;
         }
-        if (SIG) sig[path] = sg;
     }
     warp_add_u64(rays, n_ext);
     warp_add_u64(rays + 1, n_shd);
+}
+
+// Event logs of selected paths (testing aid): the megakernel's path function with a recorder.
+__global__ void k_debug_paths(DevScene s, DevCamera c, RenderParams p, const unsigned long long* __restrict__ ids,
+                              uint32_t n, uint32_t* __restrict__ ev_u, float* __restrict__ ev_f,
+                              uint32_t* __restrict__ n_ev, float* __restrict__ out_L) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long a = 0, b = 0;
+    LogRec r;
+    r.ev_u = ev_u + (size_t)i * 2 * kMaxEvents;
+    r.ev_f = ev_f + (size_t)i * 2 * kMaxEvents;
+    float3 L = mk_path(s, c, p, ids[i], r, a, b);
+    n_ev[i] = r.n;
+    out_L[3 * i] = L.x;
+    out_L[3 * i + 1] = L.y;
+    out_L[3 * i + 2] = L.z;
 }
 
 // ================================================================== wavefront stages
@@ -367,18 +419,40 @@ struct AdjRec {
     uint32_t flags;  // 1: continues, 2: NEE visible, 4: emission counted
 };
 
-__device__ __forceinline__ void adj_add(float* acc, float* g_alb, float* g_em, bool smem, uint32_t m, float3 ga,
-                                        float ge) {
-    if (smem) {
-        if (ga.x != 0.f) atomicAdd(&acc[4 * m], ga.x);
-        if (ga.y != 0.f) atomicAdd(&acc[4 * m + 1], ga.y);
-        if (ga.z != 0.f) atomicAdd(&acc[4 * m + 2], ga.z);
-        if (ge != 0.f) atomicAdd(&acc[4 * m + 3], ge);
-    } else {
-        if (ga.x != 0.f) atomicAdd(&g_alb[3 * m], ga.x);
-        if (ga.y != 0.f) atomicAdd(&g_alb[3 * m + 1], ga.y);
-        if (ga.z != 0.f) atomicAdd(&g_alb[3 * m + 2], ga.z);
-        if (ge != 0.f) atomicAdd(&g_em[m], ge);
+constexpr uint32_t kNoKey = 0xFFFFFFFFu;
+
+// Warp-aggregated accumulation into per-material gradients: lanes holding the same key add their
+// values once (one atomic per distinct key per warp).  All 32 lanes call it; key == kNoKey means
+// nothing to add.  v = (d/d albedo rgb, d/d emission).
+__device__ __forceinline__ void warp_accumulate(float* acc, float* g_alb, float* g_em, bool smem, uint32_t key,
+                                                float4 v) {
+    uint32_t pending = __ballot_sync(0xFFFFFFFFu, key != kNoKey);
+    while (pending) {
+        const uint32_t leader = __ffs(pending) - 1u;
+        const uint32_t k = __shfl_sync(0xFFFFFFFFu, key, leader);
+        const bool mine = key == k;
+        const uint32_t grp = __ballot_sync(0xFFFFFFFFu, mine);
+        float4 sum = mine ? v : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int o = 16; o > 0; o >>= 1) {
+            sum.x += __shfl_xor_sync(0xFFFFFFFFu, sum.x, o);
+            sum.y += __shfl_xor_sync(0xFFFFFFFFu, sum.y, o);
+            sum.z += __shfl_xor_sync(0xFFFFFFFFu, sum.z, o);
+            sum.w += __shfl_xor_sync(0xFFFFFFFFu, sum.w, o);
+        }
+        if (lane_id() == leader) {
+            if (smem) {
+                if (sum.x != 0.f) atomicAdd(&acc[4 * k], sum.x);
+                if (sum.y != 0.f) atomicAdd(&acc[4 * k + 1], sum.y);
+                if (sum.z != 0.f) atomicAdd(&acc[4 * k + 2], sum.z);
+                if (sum.w != 0.f) atomicAdd(&acc[4 * k + 3], sum.w);
+            } else {
+                if (sum.x != 0.f) atomicAdd(&g_alb[3 * k], sum.x);
+                if (sum.y != 0.f) atomicAdd(&g_alb[3 * k + 1], sum.y);
+                if (sum.z != 0.f) atomicAdd(&g_alb[3 * k + 2], sum.z);
+                if (sum.w != 0.f) atomicAdd(&g_em[k], sum.w);
+            }
+        }
+        pending &= ~grp;
     }
 }
 
@@ -388,6 +462,7 @@ __device__ __forceinline__ void adj_add(float* acc, float* g_alb, float* g_em, b
 //   d/d albedo(m_b)   += delta * tp_b * (dw_b/da * R_{b+1} + d(NEE_b)/da)
 //   d/d emission(m_b) += delta . tp_b                (emission counted at b)
 //   d/d emission(light material) += delta . tp_b * f_b G A   (visible NEE)
+// Loops are warp-uniform so that the per-vertex adds can be aggregated across the warp.
 template <int MAXD>
 __global__ void __launch_bounds__(256) k_adjoint(DevScene s, DevCamera c, RenderParams p, uint64_t n_paths,
                                                  const float* __restrict__ grad, float* __restrict__ g_alb,
@@ -396,76 +471,90 @@ __global__ void __launch_bounds__(256) k_adjoint(DevScene s, DevCamera c, Render
     if (smem)
         for (uint32_t k = threadIdx.x; k < 4 * s.n_mats; k += blockDim.x) acc[k] = 0.f;
     __syncthreads();
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const float3 env = f3(s.env_r, s.env_g, s.env_b);
     const float inv_spp = 1.0f / (float)p.spp;
     AdjRec rec[MAXD];
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_paths; i += stride) {
-        const uint64_t path = p.path_begin + i;
-        const uint32_t pixel = (uint32_t)(path / p.spp);
-        const uint32_t sample = (uint32_t)(path - (uint64_t)pixel * p.spp);
-        const uint32_t key = path_key(p.seed, pixel, sample);
-        float3 o, d;
-        camera_ray(c, pixel, key, o, d);
-        float3 tp = f3(1.f, 1.f, 1.f);
-        bool prev_delta = true, end_miss = false;
+    for (uint64_t base = warp * 32; base < n_paths; base += n_warps * 32) {
+        const uint64_t i = base + lane_id();
         int nv = 0;
-        for (uint32_t b = 0; b < p.max_depth && b < (uint32_t)MAXD; ++b) {
-            Hit h = trace_closest(s, o, d);
-            if (h.tri == kMiss) {
-                end_miss = true;
-                break;
+        bool end_miss = false;
+        float3 delta = f3(0.f, 0.f, 0.f);
+        if (i < n_paths) {
+            const uint64_t path = p.path_begin + i;
+            const uint32_t pixel = (uint32_t)(path / p.spp);
+            const uint32_t sample = (uint32_t)(path - (uint64_t)pixel * p.spp);
+            const uint32_t key = path_key(p.seed, pixel, sample);
+            float3 o, d;
+            camera_ray(c, pixel, key, o, d);
+            float3 tp = f3(1.f, 1.f, 1.f);
+            bool prev_delta = true;
+            for (uint32_t b = 0; b < p.max_depth && b < (uint32_t)MAXD; ++b) {
+                Hit h = trace_closest(s, o, d);
+                if (h.tri == kMiss) {
+                    end_miss = true;
+                    break;
+                }
+                Vertex V = shade_vertex(s, p, key, b, o, d, tp, prev_delta, h.t, h.tri);
+                AdjRec& r = rec[nv++];
+                r.tp = tp;
+                r.mat = V.mat;
+                r.flags = V.emit_counted ? 4u : 0u;
+                r.Le = V.emit_counted ? __ldg(&s.mats[V.mat].emission) : 0.f;
+                r.lmat = V.light_mat;
+                r.nee_g = f3(0.f, 0.f, 0.f);
+                r.nee_dfa = r.nee_g;
+                r.w = r.nee_g;
+                r.dwa = r.nee_g;
+                r.Lj = 0.f;
+                if (V.last) break;
+                if (V.nee && V.cast && !trace_any(s, V.s_o, V.s_d, V.s_tmax)) {
+                    r.flags |= 2u;
+                    r.nee_g = V.nee_g;
+                    r.nee_dfa = V.nee_dfa;
+                    r.Lj = __ldg(&s.mats[V.light_mat].emission);
+                }
+                if (!V.cont) break;
+                r.flags |= 1u;
+                r.w = V.w;
+                r.dwa = V.dwa;
+                o = V.no;
+                d = V.nd;
+                tp = V.ntp;
+                prev_delta = V.delta;
             }
-            Vertex V = shade_vertex(s, p, key, b, o, d, tp, prev_delta, h.t, h.tri);
-            AdjRec& r = rec[nv++];
-            r.tp = tp;
-            r.mat = V.mat;
-            r.flags = V.emit_counted ? 4u : 0u;
-            r.Le = V.emit_counted ? __ldg(&s.mats[V.mat].emission) : 0.f;
-            r.lmat = V.light_mat;
-            r.nee_g = f3(0.f, 0.f, 0.f);
-            r.nee_dfa = r.nee_g;
-            r.w = r.nee_g;
-            r.dwa = r.nee_g;
-            r.Lj = 0.f;
-            if (V.last) break;
-            if (V.nee && V.cast && !trace_any(s, V.s_o, V.s_d, V.s_tmax)) {
-                r.flags |= 2u;
-                r.nee_g = V.nee_g;
-                r.nee_dfa = V.nee_dfa;
-                r.Lj = __ldg(&s.mats[V.light_mat].emission);
-            }
-            if (!V.cont) break;
-            r.flags |= 1u;
-            r.w = V.w;
-            r.dwa = V.dwa;
-            o = V.no;
-            d = V.nd;
-            tp = V.ntp;
-            prev_delta = V.delta;
+            delta = f3(grad[3 * (size_t)pixel], grad[3 * (size_t)pixel + 1], grad[3 * (size_t)pixel + 2]) * inv_spp;
         }
-        const float3 delta = f3(grad[3 * (size_t)pixel], grad[3 * (size_t)pixel + 1], grad[3 * (size_t)pixel + 2]) *
-                             inv_spp;
         float3 R = end_miss ? env : f3(0.f, 0.f, 0.f);
-        for (int b = nv - 1; b >= 0; --b) {
-            const AdjRec& r = rec[b];
-            const float3 dtp = delta * r.tp;
-            float3 ga = f3(0.f, 0.f, 0.f);
-            float ge = 0.f;
-            if (r.flags & 1u) {
-                ga = dtp * r.dwa * R;
-                R = r.w * R;
+        const int nmax = __reduce_max_sync(0xFFFFFFFFu, nv);
+        for (int b = nmax - 1; b >= 0; --b) {
+            uint32_t key_m = kNoKey, key_l = kNoKey;
+            float4 vm = make_float4(0.f, 0.f, 0.f, 0.f), vl = vm;
+            if (b < nv) {
+                const AdjRec& r = rec[b];
+                const float3 dtp = delta * r.tp;
+                float3 ga = f3(0.f, 0.f, 0.f);
+                float ge = 0.f;
+                if (r.flags & 1u) {
+                    ga = dtp * r.dwa * R;
+                    R = r.w * R;
+                }
+                if (r.flags & 2u) {
+                    ga = ga + dtp * r.nee_dfa;
+                    key_l = r.lmat;
+                    vl.w = dot(dtp, r.nee_g);
+                    R = R + r.nee_g * r.Lj;
+                }
+                if (r.flags & 4u) {
+                    ge = dtp.x + dtp.y + dtp.z;
+                    R = R + f3(r.Le, r.Le, r.Le);
+                }
+                key_m = r.mat;
+                vm = make_float4(ga.x, ga.y, ga.z, ge);
             }
-            if (r.flags & 2u) {
-                ga = ga + dtp * r.nee_dfa;
-                adj_add(acc, g_alb, g_em, smem != 0, r.lmat, f3(0.f, 0.f, 0.f), dot(dtp, r.nee_g));
-                R = R + r.nee_g * r.Lj;
-            }
-            if (r.flags & 4u) {
-                ge = dtp.x + dtp.y + dtp.z;
-                R = R + f3(r.Le, r.Le, r.Le);
-            }
-            adj_add(acc, g_alb, g_em, smem != 0, r.mat, ga, ge);
+            warp_accumulate(acc, g_alb, g_em, smem != 0, key_m, vm);
+            warp_accumulate(acc, g_alb, g_em, smem != 0, key_l, vl);
         }
     }
     if (smem) {
@@ -515,6 +604,14 @@ cudaError_t launch_megakernel(const Launch& l, const DevScene& s, const DevCamer
                               uint64_t n_paths, float* out_L, float* img, uint32_t* sig, unsigned long long* rays) {
     if (sig) k_megakernel<true><<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays);
     else k_megakernel<false><<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_paths(cudaStream_t st, const DevScene& s, const DevCamera& c, const RenderParams& p,
+                               const unsigned long long* ids, uint32_t n, uint32_t* ev_u, float* ev_f, uint32_t* n_ev,
+                               float* out_L) {
+    if (n == 0) return cudaSuccess;
+    k_debug_paths<<<(n + 63) / 64, 64, 0, st>>>(s, c, p, ids, n, ev_u, ev_f, n_ev, out_L);
     return cudaGetLastError();
 }
 

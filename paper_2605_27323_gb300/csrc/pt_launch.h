@@ -20,6 +20,11 @@ cudaError_t launch_megakernel(const Launch& l, const DevScene& s, const DevCamer
                               uint64_t n_paths, float* out_L, float* img, uint32_t* sig,
                               unsigned long long* rays);
 
+// Event logs of selected paths (testing aid).
+cudaError_t launch_debug_paths(cudaStream_t st, const DevScene& s, const DevCamera& c, const RenderParams& p,
+                               const unsigned long long* ids, uint32_t n, uint32_t* ev_u, float* ev_f, uint32_t* n_ev,
+                               float* out_L);
+
 // Wavefront stages (Sec. 2.3, 3.1).  `in` selects the ping-pong queue read this bounce.
 cudaError_t launch_raygen(const Launch& l, const DevCamera& c, const RenderParams& p, uint32_t n, const WfBuffers& w);
 cudaError_t launch_extend(const Launch& l, const DevScene& s, const WfBuffers& w, int in);

@@ -74,5 +74,6 @@ struct WfBuffers {
 };
 
 constexpr uint32_t kMaxSortKeys = 4096;
+constexpr uint32_t kMaxEvents = 64;     // event-log capacity per path (testing aid)
 
 }  // namespace pt

@@ -162,6 +162,26 @@ class Scene:
         capi.check(self._lib.pt_trace_closest(self.h, _ptr(rays), n, _ptr(t), _ptr(prim), _stream(torch)))
         return t, prim
 
+    def path_events(self, cam: dict, spp: int, max_depth: int, seed: int, path_ids, **opt_kw):
+        """Event logs of the listed paths (testing aid): list of [(bounce, kind, value, f0, f1)], and
+        the paths' radiance."""
+        torch = _torch()
+        c = make_camera(cam)
+        ids = torch.as_tensor(np.ascontiguousarray(path_ids, np.uint64).astype(np.int64), device="cuda")
+        n = ids.numel()
+        ev = torch.zeros((n, 64, 2), device="cuda", dtype=torch.int32)
+        pay = torch.zeros((n, 64, 2), device="cuda", dtype=torch.float32)
+        nev = torch.zeros((n,), device="cuda", dtype=torch.int32)
+        L = torch.zeros((n, 3), device="cuda", dtype=torch.float32)
+        o = make_opts(**opt_kw)
+        capi.check(self._lib.pt_debug_trace_paths(self.h, C.byref(c), spp, max_depth, seed, C.byref(o), _ptr(ids), n,
+                                                  _ptr(ev), _ptr(pay), _ptr(nev), _ptr(L), _stream(torch)))
+        ev = ev.cpu().numpy().astype(np.uint32)
+        pay = pay.cpu().numpy()
+        nev = nev.cpu().numpy()
+        return [[(int(ev[i, k, 0] >> 4), int(ev[i, k, 0] & 15), int(ev[i, k, 1]), float(pay[i, k, 0]),
+                  float(pay[i, k, 1])) for k in range(nev[i])] for i in range(n)], L.cpu().numpy()
+
     def stats(self) -> dict:
         s = capi.Stats()
         capi.check(self._lib.pt_get_stats(self.h, C.byref(s)))
