@@ -33,7 +33,7 @@
  *   - geometric normals only; two-sided intersection; Moller-Trumbore with inclusive
  *     barycentric bounds and t > 0; equal t resolved to the lower triangle id;
  *   - ray offset: origin += eps * n on the outgoing side, eps = 1e-4 * max(1, max|p|);
- *     shadow rays end at (1 - 1e-4) * distance.
+ *     shadow rays end at the light sample lifted by eps (same rule) along the light's normal.
  *
  * Parity pins (tests/test_oracle_*.py): BVH closest hit == brute force; closed-form
  * intersections; Lambert/GGX/dielectric identities (reciprocity, sampled-weight == f cos/pdf,
@@ -729,7 +729,15 @@ static void trace(const or_scene* s, v3 o, v3 d, uint32_t key, const ropts* op, 
             if (cx > 0.0 && cl > 0.0) {
                 cast = 1;
                 rays[1]++;
-                vis = !occluded(s, os, wi, (1.0 - 1e-4) * dist, op->use_bvh);
+                /* the shadow ray ends eps off the light surface, on its emitting side, so that the
+                 * light's own (coplanar) triangles can never occlude it, at any angle */
+                double my = fabs(y.x);
+                if (fabs(y.y) > my) my = fabs(y.y);
+                if (fabs(y.z) > my) my = fabs(y.z);
+                v3 ys = add(y, scl(nl, 1e-4 * (my > 1.0 ? my : 1.0)));
+                v3 sv = sub(ys, os);
+                double sdist = sqrt(dot(sv, sv));
+                vis = !occluded(s, os, scl(sv, 1.0 / sdist), sdist, op->use_bvh);
                 if (vis) {
                     dc f = bsdf_eval(m, a, n, wo, wi, nd);
                     double g = cx * cl * s->light_area / dist2;

@@ -108,10 +108,12 @@ __device__ __forceinline__ void onb(float3 n, float3& t, float3& b) {
 }
 
 __device__ __forceinline__ float ggx_alpha(float r) { return fmaxf(r * r, 1e-4f); }
-// Trowbridge-Reitz normal distribution of cos_h = n.h.
-__device__ __forceinline__ float ggx_D(float alpha, float cos_h) {
+// Trowbridge-Reitz normal distribution from cos^2 and sin^2 of the half-vector angle.  The
+// denominator cos^2 (a^2 - 1) + 1 is evaluated as cos^2 a^2 + sin^2 with sin^2 from a cross product:
+// for sharp lobes (a^2 ~ 1e-5) the first form loses every significant digit in FP32.
+__device__ __forceinline__ float ggx_D(float alpha, float cos2_h, float sin2_h) {
     float a2 = alpha * alpha;
-    float den = cos_h * cos_h * (a2 - 1.0f) + 1.0f;
+    float den = cos2_h * a2 + sin2_h;
     return a2 / (3.14159265358979f * den * den);
 }
 // Smith Lambda of GGX for cos_v = n.v > 0.
@@ -140,7 +142,9 @@ __device__ __forceinline__ BsdfEval bsdf_eval(const MatV& m, float3 n, float3 wo
     }
     float alpha = ggx_alpha(m.roughness);
     float3 h = normalize(wo + wi);
-    float D = ggx_D(alpha, dot(n, h));
+    float ch = dot(n, h);
+    float3 nxh = cross(n, h);
+    float D = ggx_D(alpha, ch * ch, dot(nxh, nxh));
     float G2 = 1.0f / (1.0f + ggx_lambda(alpha, co) + ggx_lambda(alpha, ci));
     float mm = 1.0f - dot(wi, h);
     float m5 = mm * mm * mm * mm * mm;
@@ -375,9 +379,15 @@ __device__ __forceinline__ Vertex shade_vertex(const DevScene& s, const RenderPa
             V.nee_g = fe.f * g;
             V.nee_dfa = fe.dfa * g * lm.emission;
             V.contrib = mul_rn(mul_rn(tp, V.nee_g), Le);
+            // the shadow ray ends eps off the light surface on its emitting side: the light's own
+            // coplanar triangles cannot occlude it, even at grazing angles
+            float my = fmaxf(fabsf(y.x), fmaxf(fabsf(y.y), fabsf(y.z)));
+            float3 ys = y + nl * (1e-4f * fmaxf(my, 1.0f));
+            float3 sv = ys - os;
+            float sdist = sqrtf(dot(sv, sv));
             V.s_o = os;
-            V.s_d = wi;
-            V.s_tmax = (1.0f - 1e-4f) * dist;
+            V.s_d = sv * (1.0f / sdist);
+            V.s_tmax = sdist;
         }
     }
     // step 4: sample a continuation and update the throughput (Eq. 3)

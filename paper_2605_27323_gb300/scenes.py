@@ -164,8 +164,9 @@ def _scene(b: _Builder, mats: dict, env, **extra):
 
 
 # ------------------------------------------------------------------ benchmark scenes
-def box_scene(seed: int = 0, width=128, height=128):
-    """Tiny box: 5 walls + two axis-aligned boxes + a 2-triangle ceiling light (36 tris)."""
+def box_scene(seed: int = 0, width=128, height=128, lift=0.0):
+    """Tiny box: 5 walls + two axis-aligned boxes + a 2-triangle ceiling light (36 tris).  `lift`
+    raises both boxes off the floor (their bottoms are coplanar with it when 0)."""
     rng = np.random.default_rng(seed)
     b = _Builder()
     # walls (inward normals): x in [-1,1], y in [0,2], z in [-1,1], open toward +z
@@ -180,8 +181,8 @@ def box_scene(seed: int = 0, width=128, height=128):
     albedo = rng.uniform(0.1, 0.9, size=(n_surf + 1, 3))
     for k, w in enumerate(walls):
         b.add(*quad(*w), k)
-    b.add(*box_mesh((-0.7, 0.0, -0.1), (-0.1, 0.6, 0.5)), 5)
-    b.add(*box_mesh((0.1, 0.0, -0.7), (0.7, 1.2, -0.1)), 6)
+    b.add(*box_mesh((-0.7, lift, -0.1), (-0.1, 0.6 + lift, 0.5)), 5)
+    b.add(*box_mesh((0.1, lift, -0.7), (0.7, 1.2 + lift, -0.1)), 6)
     # light quad just below the ceiling, facing down
     b.add(*quad((-0.25, 1.98, -0.25), (0.25, 1.98, -0.25), (0.25, 1.98, 0.25), (-0.25, 1.98, 0.25)), 7)
     types = [LAMBERT] * (n_surf + 1)

@@ -70,7 +70,7 @@ def test_adjoint_matches_oracle_dual_numbers_on_crop(pt, torch):
 
 
 def _fd_box():
-    sc = scenes.box_scene(width=48, height=48)
+    sc = scenes.box_scene(width=48, height=48, lift=2e-3)
     sc["mat_type"] = sc["mat_type"].copy()
     sc["mat_roughness"] = sc["mat_roughness"].copy()
     sc["mat_type"][5] = 1

@@ -137,7 +137,9 @@ def test_box_scene_both_modes_vs_oracle(pt, torch):
 
 
 def _mixed_box(width, height):
-    sc = scenes.box_scene(width=width, height=height)
+    # the glass box is lifted off the floor: a bottom face coplanar with the floor makes the
+    # closest hit inside the glass a tie that FP32 and FP64 break differently
+    sc = scenes.box_scene(width=width, height=height, lift=2e-3)
     sc["mat_type"] = sc["mat_type"].copy()
     sc["mat_roughness"] = sc["mat_roughness"].copy()
     sc["mat_albedo"] = sc["mat_albedo"].copy()
