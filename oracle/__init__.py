@@ -79,6 +79,7 @@ def lib():
             L.or_bsdf_eval.argtypes = [u32, vp, f64, vp, vp, vp, vp]
             L.or_bsdf_sample.restype = i32
             L.or_bsdf_sample.argtypes = [u32, vp, f64, f64, vp, vp, vp, f64, f64, f64, vp, vp, vp]
+            L.or_onb.argtypes = [vp, vp, vp]
             L.or_fresnel_dielectric.restype = f64
             L.or_fresnel_dielectric.argtypes = [f64, f64, f64]
             L.or_ggx_D.restype = f64
@@ -131,6 +132,12 @@ def bsdf_sample(mtype, albedo, roughness, ior, n, ng, wo, u5, u6, u7):
                               _p(_f(ng, np.float64)), _p(_f(wo, np.float64)), u5, u6, u7, _p(wi), _p(w),
                               _p(code))
     return bool(ok), wi, w, int(code[0])
+
+
+def onb(n):
+    t, b = np.empty(3), np.empty(3)
+    lib().or_onb(_p(_f(n, np.float64)), _p(t), _p(b))
+    return t, b
 
 
 def fresnel_dielectric(ci, eta_i, eta_t) -> float:

@@ -454,14 +454,40 @@ static dc mat_emission(const or_scene* s, int64_t m, const dirs_t* dr) {
 }
 
 /* ------------------------------------------------------------------ BSDFs */
-/* Orthonormal basis around a unit normal (Duff et al., "Building an Orthonormal Basis,
- * Revisited", JCGT 2017). */
+/* Orthonormal basis around a unit normal: the branch-free construction of Duff et al.
+ * ("Building an Orthonormal Basis, Revisited", JCGT 2017), applied in a fixed rotated frame.
+ * The construction switches between two bases where the normal's z crosses 0; every tangent
+ * field on the sphere is discontinuous somewhere, and here the switch is moved off the coordinate
+ * planes (where floors and walls put their normals) by building the basis for R n and rotating it
+ * back.  R = Rodrigues rotation about (1, 2, 3) / sqrt(14) by 1 radian. */
+static double g_onb_R[3][3];
+
+__attribute__((constructor)) static void init_onb_frame(void) {
+    double k[3] = {1.0, 2.0, 3.0}, l = sqrt(14.0), c = cos(1.0), sn = sin(1.0);
+    for (int i = 0; i < 3; ++i) k[i] /= l;
+    double K[3][3] = {{0.0, -k[2], k[1]}, {k[2], 0.0, -k[0]}, {-k[1], k[0], 0.0}};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) g_onb_R[i][j] = (i == j ? c : 0.0) + sn * K[i][j] + (1.0 - c) * k[i] * k[j];
+}
+
+static v3 rot(v3 a) {   /* R a */
+    return mk(g_onb_R[0][0] * a.x + g_onb_R[0][1] * a.y + g_onb_R[0][2] * a.z,
+              g_onb_R[1][0] * a.x + g_onb_R[1][1] * a.y + g_onb_R[1][2] * a.z,
+              g_onb_R[2][0] * a.x + g_onb_R[2][1] * a.y + g_onb_R[2][2] * a.z);
+}
+static v3 rot_t(v3 a) { /* R^T a */
+    return mk(g_onb_R[0][0] * a.x + g_onb_R[1][0] * a.y + g_onb_R[2][0] * a.z,
+              g_onb_R[0][1] * a.x + g_onb_R[1][1] * a.y + g_onb_R[2][1] * a.z,
+              g_onb_R[0][2] * a.x + g_onb_R[1][2] * a.y + g_onb_R[2][2] * a.z);
+}
+
 static void onb(v3 n, v3* t, v3* b) {
-    double sign = copysign(1.0, n.z);
-    double a = -1.0 / (sign + n.z);
-    double bb = n.x * n.y * a;
-    *t = mk(1.0 + sign * n.x * n.x * a, sign * bb, -sign * n.x);
-    *b = mk(bb, sign + n.y * n.y * a, -n.y);
+    v3 m = rot(n);
+    double sign = copysign(1.0, m.z);
+    double a = -1.0 / (sign + m.z);
+    double bb = m.x * m.y * a;
+    *t = rot_t(mk(1.0 + sign * m.x * m.x * a, sign * bb, -sign * m.x));
+    *b = rot_t(mk(bb, sign + m.y * m.y * a, -m.y));
 }
 
 static double ggx_alpha(double roughness) {
@@ -620,6 +646,13 @@ int or_bsdf_sample(uint32_t type, const double* albedo, double roughness, double
     for (int c = 0; c < 3; ++c) weight_out[c] = s.weight.v[c];
     *code_out = s.code;
     return s.valid;
+}
+
+void or_onb(const double* n, double* t, double* b) {
+    v3 tt, bb;
+    onb(mk(n[0], n[1], n[2]), &tt, &bb);
+    t[0] = tt.x; t[1] = tt.y; t[2] = tt.z;
+    b[0] = bb.x; b[1] = bb.y; b[2] = bb.z;
 }
 
 double or_fresnel_dielectric(double ci, double eta_i, double eta_t) {

@@ -97,14 +97,29 @@ __device__ __forceinline__ MatV load_mat(const DevMat* mats, uint32_t m) {
     return r;
 }
 
-// Orthonormal basis around a unit normal (Duff et al., "Building an Orthonormal Basis, Revisited",
-// JCGT 2017).
+// Orthonormal basis around a unit normal: the branch-free construction of Duff et al. ("Building an
+// Orthonormal Basis, Revisited", JCGT 2017) applied in a fixed rotated frame.  The construction
+// switches basis where z crosses 0; building it for R n and rotating back moves that switch off the
+// coordinate planes, where scene normals (floors, walls) concentrate, so FP32 rounding of an
+// axis-aligned normal cannot flip the sampled direction.  R = Rodrigues rotation about
+// (1, 2, 3) / sqrt(14) by 1 radian (entries rounded to FP32).
+__device__ __forceinline__ float3 onb_rot(float3 a) {
+    return f3(5.731378794e-01f * a.x - 6.090066433e-01f * a.y + 5.482918024e-01f * a.z,
+              7.403488159e-01f * a.x + 6.716445088e-01f * a.y - 2.787928283e-02f * a.z,
+              -3.512785137e-01f * a.x + 4.219058752e-01f * a.y + 8.358222246e-01f * a.z);
+}
+__device__ __forceinline__ float3 onb_rot_t(float3 a) {
+    return f3(5.731378794e-01f * a.x + 7.403488159e-01f * a.y - 3.512785137e-01f * a.z,
+              -6.090066433e-01f * a.x + 6.716445088e-01f * a.y + 4.219058752e-01f * a.z,
+              5.482918024e-01f * a.x - 2.787928283e-02f * a.y + 8.358222246e-01f * a.z);
+}
 __device__ __forceinline__ void onb(float3 n, float3& t, float3& b) {
-    float sign = copysignf(1.0f, n.z);
-    float a = -1.0f / (sign + n.z);
-    float bb = n.x * n.y * a;
-    t = f3(1.0f + sign * n.x * n.x * a, sign * bb, -sign * n.x);
-    b = f3(bb, sign + n.y * n.y * a, -n.y);
+    float3 m = onb_rot(n);
+    float sign = copysignf(1.0f, m.z);
+    float a = -1.0f / (sign + m.z);
+    float bb = m.x * m.y * a;
+    t = onb_rot_t(f3(1.0f + sign * m.x * m.x * a, sign * bb, -sign * m.x));
+    b = onb_rot_t(f3(bb, sign + m.y * m.y * a, -m.y));
 }
 
 __device__ __forceinline__ float ggx_alpha(float r) { return fmaxf(r * r, 1e-4f); }

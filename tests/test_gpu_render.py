@@ -140,6 +140,8 @@ def _mixed_box(width, height):
     # the glass box is lifted off the floor: a bottom face coplanar with the floor makes the
     # closest hit inside the glass a tie that FP32 and FP64 break differently
     sc = scenes.box_scene(width=width, height=height, lift=2e-3)
+    if width > height:   # keep a 40-degree horizontal field of view for wide strips
+        sc["camera"]["vfov_deg"] = float(2 * np.degrees(np.arctan(np.tan(np.radians(20.0)) * height / width)))
     sc["mat_type"] = sc["mat_type"].copy()
     sc["mat_roughness"] = sc["mat_roughness"].copy()
     sc["mat_albedo"] = sc["mat_albedo"].copy()

@@ -156,3 +156,24 @@ def test_schlick_endpoints(oracle_lib):
     wi = _dir(1.5707, np.pi)
     f2 = oracle_lib.bsdf_eval(1, a, 0.5, N, wo, wi)   # h ~ n, cos(wi, h) ~ 0 -> F ~ 1
     assert np.allclose(f2 / f2.max(), 1.0, atol=1e-3)
+
+
+def test_onb_orthonormal_and_continuous_on_axis_planes(oracle_lib):
+    rng = np.random.default_rng(4)
+    ns = rng.normal(size=(500, 3))
+    ns = np.concatenate([ns, np.eye(3), -np.eye(3), [[0.6, 0.8, 0.0], [0.0, -0.6, 0.8]]])
+    for n in ns:
+        n = n / np.linalg.norm(n)
+        t, b = oracle_lib.onb(n)
+        M = np.stack([t, b, n])
+        assert np.allclose(M @ M.T, np.eye(3), atol=1e-12)
+        assert np.allclose(np.cross(t, b), n, atol=1e-12)          # right-handed
+    # the basis does not jump for normals on the coordinate planes (floors, walls): a tilt of
+    # 1e-9 across z = 0, y = 0 or x = 0 moves it by about the tilt
+    for n in (np.array([0.0, 1.0, 0.0]), np.array([1.0, 0.0, 0.0]), np.array([0.6, 0.0, 0.8])):
+        for axis in range(3):
+            e = np.zeros(3)
+            e[axis] = 1e-9
+            t1, b1 = oracle_lib.onb((n + e) / np.linalg.norm(n + e))
+            t2, b2 = oracle_lib.onb((n - e) / np.linalg.norm(n - e))
+            assert np.abs(t1 - t2).max() < 1e-7 and np.abs(b1 - b2).max() < 1e-7
