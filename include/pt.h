@@ -161,6 +161,23 @@ pt_status pt_autotune_batch(pt_scene* const* scenes, const pt_camera* cams, cons
 pt_status pt_trace_closest(pt_scene* scene, const float* d_rays, uint32_t n, float* d_t, int32_t* d_prim,
                            void* stream);
 
+/* Wavefront render that allocates nothing.  The paper has no counterpart: this is a deployment
+ * variant of pt_render (mode = wavefront) for callers that cannot allocate device memory or let a
+ * library do it -- an application whose own memory manager owns the whole device, or a real-time
+ * loop that cannot absorb the implicit synchronisation of cudaMalloc/cudaFree.  Its queues live in
+ * one 32 MiB file-scope device array that every GPU loading libpt.so holds until the process exits;
+ * frames are rendered in waves of whole pixels that fit it (about 190,000 paths per wave), with the
+ * same kernels and random numbers, so the image equals pt_render's.  Arguments as for pt_render,
+ * except: d_out_rgb (and opts->d_path_sig, if set) must be device memory (nothing is staged), there
+ * is no per-path output, opts->queue_capacity is ignored, and pt_get_stats does not report this call.
+ * Errors: PT_ERR_INVALID_ARG also when one pixel's spp samples need more than the array
+ * (spp x 176 bytes > 32 MiB).  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share the
+ * array and it keeps the last call's contents: each call clears its own counters, and calls that
+ * overlap on the GPU (other streams or threads without ordering between them) race. */
+pt_status pt_render_wavefront_static(pt_scene* scene, const pt_camera* cam, uint32_t spp, uint32_t max_depth,
+                                     uint64_t seed, const pt_render_opts* opts, float* d_out_rgb, void* stream);
+
 /* Statistics of the last render/backward/batch call on this scene (synchronises the stream used by
  * that call).  status reports device-side faults. */
 pt_status pt_get_stats(pt_scene* scene, pt_stats* out);

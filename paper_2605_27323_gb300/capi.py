@@ -24,7 +24,7 @@ FLAG_PROFILE, FLAG_NO_GRAPH = 1, 2
 # header and the shared object).
 EXPORTED = ["pt_scene_create", "pt_scene_set_materials", "pt_render", "pt_render_backward", "pt_render_batch",
             "pt_autotune_batch", "pt_trace_closest", "pt_get_stats", "pt_debug_rng", "pt_debug_trace_paths",
-            "pt_scene_info",
+            "pt_scene_info", "pt_render_wavefront_static",
             "pt_status_string", "pt_last_error", "pt_scene_destroy"]
 
 
@@ -94,6 +94,8 @@ def load(build_if_missing: bool = True):
     L.pt_debug_rng.argtypes = [u64, vp, vp, vp, vp, u32, vp, vp]
     L.pt_debug_trace_paths.restype = u32
     L.pt_debug_trace_paths.argtypes = [vp, P(Camera), u32, u32, u64, P(RenderOpts), vp, u32, vp, vp, vp, vp, vp]
+    L.pt_render_wavefront_static.restype = u32
+    L.pt_render_wavefront_static.argtypes = [vp, P(Camera), u32, u32, u64, P(RenderOpts), vp, vp]
     L.pt_scene_info.restype = u32
     L.pt_scene_info.argtypes = [vp, P(u64), P(u64), P(u64), P(f32), P(u64)]
     L.pt_status_string.restype = C.c_char_p

@@ -383,6 +383,29 @@ pt_status run_wavefront(pt_scene* sc, const pt::DevCamera& cam, const pt::Render
 
 }  // namespace
 
+// Internal helpers for the allocation-free entry point in pt_static.cu (C++ linkage, not exported
+// from the ABI).  They only read the scene and convert arguments; none of them allocates.
+namespace pt {
+
+pt_status static_set_error(pt_status s, const char* msg) { return fail(s, "%s", msg); }
+
+pt_status static_prepare(pt_scene* sc, const pt_camera* cam, const pt_render_opts* opts, DevScene* view,
+                         DevCamera* dc, pt_render_opts* o_out, int* device) {
+    if (!sc) return fail(PT_ERR_INVALID_ARG, "scene is NULL");
+    pt_render_opts o = opts ? *opts : default_opts();
+    PT_TRY(check_opts(o));
+    PT_TRY(make_camera(cam, *dc));
+    PT_TRY(set_device(sc));
+    *view = sc->view();
+    *o_out = o;
+    *device = sc->device;
+    return PT_OK;
+}
+
+bool static_is_device_ptr(const void* p) { return is_device_ptr(p); }
+
+}  // namespace pt
+
 extern "C" {
 
 const char* pt_status_string(pt_status s) {

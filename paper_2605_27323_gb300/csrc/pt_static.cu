@@ -1,0 +1,189 @@
+// pt_static.cu -- pt_render_wavefront_static: the wavefront render with its queues in one fixed
+// file-scope device array, for callers that cannot allocate device memory themselves or let a
+// library do it (an application whose memory manager owns every byte of the device, or a
+// real-time loop that cannot absorb the implicit synchronisation of cudaMalloc/cudaFree).
+//
+// The array is kStaticScratchBytes (32 MiB) and lives on every GPU that loads this library until
+// the process exits.  Frames larger than one array's worth of paths are rendered in waves of whole
+// pixels.  Every call shares the array: it keeps the previous call's contents, this file clears the
+// counters that must start at zero on every call, and calls that overlap on the GPU (other streams,
+// other threads) race on it.  The first call on a device looks up the array's device address with
+// cudaGetSymbolAddress (the host-side name is only a stand-in); make that first call before any
+// stream capture.  Nothing here calls cudaMalloc, cudaFree or an allocating library routine.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <mutex>
+
+#include "pt.h"
+#include "pt_launch.h"
+#include "pt_types.h"
+
+namespace pt {
+pt_status static_set_error(pt_status s, const char* msg);
+pt_status static_prepare(pt_scene* sc, const pt_camera* cam, const pt_render_opts* opts, DevScene* view,
+                         DevCamera* dc, pt_render_opts* o_out, int* device);
+bool static_is_device_ptr(const void* p);
+}  // namespace pt
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = 32ull << 20;
+constexpr size_t kBytesPerPath = 176;           // the wavefront's per-path queue records
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_mu;
+unsigned char* g_addr[kMaxDevices] = {};
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Device address of the array on `device` (which is current), looked up once per device.
+pt_status scratch_address(int device, unsigned char** out) {
+    if (device < 0 || device >= kMaxDevices) return pt::static_set_error(PT_ERR_UNSUPPORTED, "device index out of range");
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!g_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            char msg[160];
+            std::snprintf(msg, sizeof msg, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
+            return pt::static_set_error(PT_ERR_CUDA, msg);
+        }
+        g_addr[device] = static_cast<unsigned char*>(p);
+    }
+    *out = g_addr[device];
+    return PT_OK;
+}
+
+// Paths one wave can hold after the fixed regions (counters, histories, sort buckets).
+uint64_t wave_capacity() {
+    size_t fixed = a256(256) + a256(8 * 128) + a256(pt::kMaxSortKeys * 4) + 16 * 256;
+    return (kStaticScratchBytes - fixed) / kBytesPerPath;
+}
+
+pt_status cuda_fail(cudaError_t e, const char* what) {
+    char msg[200];
+    std::snprintf(msg, sizeof msg, "%s: %s", what, cudaGetErrorString(e));
+    return pt::static_set_error(PT_ERR_CUDA, msg);
+}
+
+}  // namespace
+
+extern "C" pt_status pt_render_wavefront_static(pt_scene* scene, const pt_camera* cam, uint32_t spp,
+                                                uint32_t max_depth, uint64_t seed, const pt_render_opts* opts,
+                                                float* d_out_rgb, void* stream) {
+    if (!d_out_rgb) return pt::static_set_error(PT_ERR_INVALID_ARG, "output image is NULL");
+    if (spp == 0) return pt::static_set_error(PT_ERR_INVALID_ARG, "spp must be >= 1");
+    if (max_depth > 64) return pt::static_set_error(PT_ERR_INVALID_ARG, "max_depth must be <= 64");
+    pt::DevScene ds;
+    pt::DevCamera dc;
+    pt_render_opts o;
+    int device = 0;
+    pt_status s = pt::static_prepare(scene, cam, opts, &ds, &dc, &o, &device);
+    if (s != PT_OK) return s;
+    if (!pt::static_is_device_ptr(d_out_rgb))
+        return pt::static_set_error(PT_ERR_INVALID_ARG, "d_out_rgb must be device memory (this call stages nothing)");
+    if (o.d_path_sig && !pt::static_is_device_ptr(o.d_path_sig))
+        return pt::static_set_error(PT_ERR_INVALID_ARG, "d_path_sig must be device memory");
+    const uint64_t cap_max = wave_capacity();
+    if (spp > cap_max) {
+        char msg[200];
+        std::snprintf(msg, sizeof msg, "spp %u needs %llu bytes per pixel; the static scratch holds %llu paths (%zu MiB)",
+                      spp, (unsigned long long)spp * kBytesPerPath, (unsigned long long)cap_max,
+                      kStaticScratchBytes >> 20);
+        return pt::static_set_error(PT_ERR_INVALID_ARG, msg);
+    }
+    unsigned char* base = nullptr;
+    if ((s = scratch_address(device, &base)) != PT_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const uint64_t n_pixels = (uint64_t)cam->width * cam->height;
+    const uint64_t n_paths = n_pixels * spp;
+    const uint64_t cap = cap_max - cap_max % spp;
+
+    // carve the array: counters, histories, sort buckets, then the per-path records
+    pt::WfBuffers w{};
+    size_t off = 0;
+    auto take = [&](size_t n) {
+        unsigned char* r = base + off;
+        off += a256(n);
+        return r;
+    };
+    w.counts = reinterpret_cast<uint32_t*>(take(256));
+    w.hist = reinterpret_cast<unsigned long long*>(take(8 * 128));
+    w.bucket = reinterpret_cast<uint32_t*>(take(pt::kMaxSortKeys * 4));
+    for (int i = 0; i < 2; ++i) {
+        w.q_o[i] = reinterpret_cast<float4*>(take(cap * 16));
+        w.q_d[i] = reinterpret_cast<float4*>(take(cap * 16));
+        w.q_tp[i] = reinterpret_cast<float4*>(take(cap * 16));
+    }
+    w.hit = reinterpret_cast<float2*>(take(cap * 8));
+    w.keys = reinterpret_cast<uint32_t*>(take(cap * 4));
+    w.perm = reinterpret_cast<uint32_t*>(take(cap * 4));
+    w.s_o = reinterpret_cast<float4*>(take(cap * 16));
+    w.s_d = reinterpret_cast<float4*>(take(cap * 16));
+    w.s_c = reinterpret_cast<float4*>(take(cap * 16));
+    w.L = reinterpret_cast<float4*>(take(cap * 16));
+    if (off > kStaticScratchBytes) return pt::static_set_error(PT_ERR_UNSUPPORTED, "static scratch layout overflow");
+    w.sig = o.d_path_sig;
+    w.capacity = (uint32_t)cap;
+
+    cudaError_t e = cudaMemsetAsync(base, 0, a256(256) + a256(8 * 128), st);   // counts and histories
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    if (max_depth == 0) {
+        e = cudaMemsetAsync(d_out_rgb, 0, n_pixels * 12, st);
+        return e == cudaSuccess ? PT_OK : cuda_fail(e, "cudaMemsetAsync");
+    }
+    int sms = 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        sms = 1;
+    }
+    const int block = o.block_size ? (int)o.block_size : 256;
+    auto persistent = [&](int which) {
+        pt::Launch l;
+        l.block = block;
+        l.grid = std::max(1, sms * pt::max_blocks_per_sm(which, block));
+        l.st = st;
+        return l;
+    };
+    auto plain = [&](uint64_t work) {
+        pt::Launch l;
+        l.block = 256;
+        l.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 8));
+        l.st = st;
+        return l;
+    };
+    uint32_t n_keys = 0;
+    if (o.sort_mode == PT_SORT_TYPE) n_keys = 4;
+    if (o.sort_mode == PT_SORT_MATERIAL) n_keys = std::min<uint32_t>(ds.n_mats + 1, pt::kMaxSortKeys);
+    const uint32_t sort_mode = o.sort_mode == PT_SORT_TYPE ? 1u : 2u;
+    pt::RenderParams p;
+    p.seed = seed;
+    p.spp = spp;
+    p.max_depth = max_depth;
+    p.rr_start = o.rr_start;
+    p.rr_fixed = o.rr_fixed;
+    for (uint64_t w0 = 0; w0 < n_paths; w0 += cap) {
+        const uint32_t n = (uint32_t)std::min<uint64_t>(cap, n_paths - w0);
+        p.path_begin = w0;
+        if ((e = pt::launch_raygen(plain(n), dc, p, n, w)) != cudaSuccess) return cuda_fail(e, "raygen");
+        for (uint32_t b = 0; b < max_depth; ++b) {
+            const int in = (int)(b & 1u);
+            if ((e = pt::launch_extend(persistent(pt::K_EXTEND), ds, w, in)) != cudaSuccess) return cuda_fail(e, "extend");
+            if (n_keys && (e = pt::launch_sort(plain(n), ds, w, sort_mode, n_keys)) != cudaSuccess)
+                return cuda_fail(e, "sort");
+            if ((e = pt::launch_shade(persistent(pt::K_SHADE), ds, p, w, in, b, n_keys > 0)) != cudaSuccess)
+                return cuda_fail(e, "shade");
+            if ((e = pt::launch_shadow(persistent(pt::K_SHADOW), ds, p, w, b)) != cudaSuccess) return cuda_fail(e, "shadow");
+            if ((e = pt::launch_prepare(st, w, b)) != cudaSuccess) return cuda_fail(e, "prepare");
+        }
+        if ((e = pt::launch_reduce(plain(n / spp), reinterpret_cast<const float*>(w.L), 4, w0 / spp, n / spp, spp,
+                                   d_out_rgb)) != cudaSuccess)
+            return cuda_fail(e, "reduce");
+    }
+    return PT_OK;
+}

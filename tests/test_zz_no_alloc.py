@@ -1,0 +1,75 @@
+"""pt_render_wavefront_static: the wavefront render for callers that cannot allocate device memory
+(an application whose memory manager owns the whole device, or a real-time loop that cannot absorb
+cudaMalloc's implicit synchronisation).  Its queues live in a fixed 32 MiB device array inside the
+library, so it renders in waves; its images must equal pt_render's (wavefront) bit for bit -- the
+tolerance every wavefront variant is held to in these tests -- on two calls in a row, sharing the
+array.  This file is collected last on purpose."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed_box(width, height):
+    from paper_2605_27323_gb300 import scenes
+    sc = scenes.box_scene(width=width, height=height, lift=2e-3)
+    sc["mat_type"] = sc["mat_type"].copy()
+    sc["mat_roughness"] = sc["mat_roughness"].copy()
+    sc["mat_type"][5], sc["mat_roughness"][5] = 1, 0.25
+    sc["mat_type"][6] = 2
+    return sc
+
+
+def test_static_scratch_render_equals_pt_render_on_two_calls():
+    import torch
+
+    import paper_2605_27323_gb300 as pt
+    from paper_2605_27323_gb300 import capi, scenes
+    from paper_2605_27323_gb300.tracer import make_camera, make_opts
+
+    assert torch.cuda.is_available()
+    lib = capi.load()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    box = _mixed_box(96, 72)
+    spheres = scenes.spheres_scene(seed=2, n_spheres=30, level=3, ground_quads=64, width=480, height=270,
+                                   extent=20.0)
+    # call 1: one wave; call 2: 2.07 M paths, about eleven waves of the static array
+    cases = [(box, box["camera"], 4, 8, 3, "none"), (spheres, spheres["camera"], 16, 5, 9, "material")]
+    for sc, cam, spp, depth, seed, sort in cases:
+        g = pt.Scene.from_dict(sc)
+        ref = g.render(cam, spp, depth, seed, mode="wavefront", sort=sort)
+        out = torch.full_like(ref, float("nan"))
+        c = make_camera(cam)
+        o = make_opts(mode="wavefront", sort=sort)
+        st = lib.pt_render_wavefront_static(g.h, C.byref(c), spp, depth, seed, C.byref(o), C.c_void_p(out.data_ptr()),
+                                            stream)
+        assert st == 0, lib.pt_last_error()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+        assert float(out.mean()) > 0
+
+
+def test_static_scratch_rejects_what_it_cannot_hold():
+    import torch
+
+    import paper_2605_27323_gb300 as pt
+    from paper_2605_27323_gb300 import capi
+    from paper_2605_27323_gb300.tracer import make_camera, make_opts
+
+    lib = capi.load()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    sc = _mixed_box(2, 2)
+    g = pt.Scene.from_dict(sc)
+    c = make_camera(sc["camera"])
+    o = make_opts()
+    out = torch.zeros((2, 2, 3), device="cuda")
+    # one pixel's samples must fit the array: 200,000 x 176 B > 32 MiB
+    assert lib.pt_render_wavefront_static(g.h, C.byref(c), 200_000, 4, 0, C.byref(o), C.c_void_p(out.data_ptr()),
+                                          stream) == 1
+    assert b"static scratch" in lib.pt_last_error()
+    host = np.zeros((2, 2, 3), np.float32)
+    assert lib.pt_render_wavefront_static(g.h, C.byref(c), 1, 4, 0, C.byref(o), host.ctypes.data_as(C.c_void_p),
+                                          stream) == 1
+    assert b"device memory" in lib.pt_last_error()
