@@ -118,6 +118,34 @@ int blocks_per_sm(int which, int block) {
 
 enum Stage { ST_RAYGEN, ST_EXTEND, ST_SORT, ST_SHADE, ST_SHADOW, ST_REDUCE, ST_MEGA, ST_ADJOINT, ST_COUNT };
 
+// One device allocation carved into the wavefront arrays for `cap` paths (176 bytes each).
+pt_status carve_wavefront(DevBuf& buf, uint64_t cap, pt::WfBuffers& w) {
+    size_t q = align256(cap * 16), h = align256(cap * 8), k = align256(cap * 4);
+    size_t total = 6 * q + h + 2 * k + align256(pt::kMaxSortKeys * 4) + 3 * q + q;
+    PT_TRY(buf.ensure(total));
+    char* base = buf.as<char>();
+    size_t off = 0;
+    auto take = [&](size_t n) {
+        char* r = base + off;
+        off += n;
+        return r;
+    };
+    for (int i = 0; i < 2; ++i) {
+        w.q_o[i] = reinterpret_cast<float4*>(take(q));
+        w.q_d[i] = reinterpret_cast<float4*>(take(q));
+        w.q_tp[i] = reinterpret_cast<float4*>(take(q));
+    }
+    w.hit = reinterpret_cast<float2*>(take(h));
+    w.keys = reinterpret_cast<uint32_t*>(take(k));
+    w.perm = reinterpret_cast<uint32_t*>(take(k));
+    w.bucket = reinterpret_cast<uint32_t*>(take(align256(pt::kMaxSortKeys * 4)));
+    w.s_o = reinterpret_cast<float4*>(take(q));
+    w.s_d = reinterpret_cast<float4*>(take(q));
+    w.s_c = reinterpret_cast<float4*>(take(q));
+    w.L = reinterpret_cast<float4*>(take(q));
+    return PT_OK;
+}
+
 }  // namespace
 
 struct pt_scene {
@@ -178,29 +206,7 @@ struct pt_scene {
     // One allocation carved into the wavefront arrays for `cap` paths per wave.
     pt_status ensure_wf(uint64_t cap) {
         if (wf_capacity >= cap && wf.p) return PT_OK;
-        size_t q = align256(cap * 16), h = align256(cap * 8), k = align256(cap * 4);
-        size_t total = 6 * q + h + 2 * k + align256(pt::kMaxSortKeys * 4) + 3 * q + q;
-        PT_TRY(wf.ensure(total));
-        char* base = wf.as<char>();
-        size_t off = 0;
-        auto take = [&](size_t n) {
-            char* r = base + off;
-            off += n;
-            return r;
-        };
-        for (int i = 0; i < 2; ++i) {
-            wfb.q_o[i] = reinterpret_cast<float4*>(take(q));
-            wfb.q_d[i] = reinterpret_cast<float4*>(take(q));
-            wfb.q_tp[i] = reinterpret_cast<float4*>(take(q));
-        }
-        wfb.hit = reinterpret_cast<float2*>(take(h));
-        wfb.keys = reinterpret_cast<uint32_t*>(take(k));
-        wfb.perm = reinterpret_cast<uint32_t*>(take(k));
-        wfb.bucket = reinterpret_cast<uint32_t*>(take(align256(pt::kMaxSortKeys * 4)));
-        wfb.s_o = reinterpret_cast<float4*>(take(q));
-        wfb.s_d = reinterpret_cast<float4*>(take(q));
-        wfb.s_c = reinterpret_cast<float4*>(take(q));
-        wfb.L = reinterpret_cast<float4*>(take(q));
+        PT_TRY(carve_wavefront(wf, cap, wfb));
         wf_capacity = cap;
         return PT_OK;
     }
@@ -351,12 +357,12 @@ pt_status run_wavefront(pt_scene* sc, const pt::DevCamera& cam, const pt::Render
             const int in = (int)(b & 1u);
             pt::Launch le = launch_for(sc, pt::K_EXTEND, o.block_size, 256, st, n);
             PT_TRY(sc->ev_begin(ST_EXTEND, st, ev));
-            PT_CUDA(pt::launch_extend(le, ds, w, in));
+            PT_CUDA(pt::launch_extend(le, ds, w, in, p));
             PT_TRY(sc->ev_end(ev, st));
             bool sorted = n_keys > 0;
             if (sorted) {
                 PT_TRY(sc->ev_begin(ST_SORT, st, ev));
-                PT_CUDA(pt::launch_sort(simple_launch(sc, st, n), ds, w, sort_mode, n_keys));
+                PT_CUDA(pt::launch_sort(simple_launch(sc, st, n), ds, w, in, sort_mode, n_keys, p));
                 PT_TRY(sc->ev_end(ev, st));
             }
             pt::Launch ls = launch_for(sc, pt::K_SHADE, o.block_size, 256, st, n);
@@ -405,6 +411,217 @@ pt_status static_prepare(pt_scene* sc, const pt_camera* cam, const pt_render_opt
 bool static_is_device_ptr(const void* p) { return is_device_ptr(p); }
 
 }  // namespace pt
+
+// ------------------------------------------------------------------ batched rendering
+// Process-wide state of pt_render_batch on one device: the wavefront workspace, the device tables
+// (scene views, cameras, path and pixel offsets, spp, output pointers, wave segments), counters, a
+// private non-blocking stream for graph capture, and the captured bounce-loop graph.
+namespace {
+
+struct BatchCtx {
+    DevBuf wf, tables, counters;
+    pt::WfBuffers wfb{};
+    uint64_t capacity = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<uint64_t> graph_key;
+    std::mutex mu;
+};
+
+BatchCtx* batch_ctx(int device) {
+    static std::mutex mu;
+    static std::map<int, BatchCtx*> ctxs;   // kept for the life of the process
+    std::lock_guard<std::mutex> g(mu);
+    BatchCtx*& c = ctxs[device];
+    if (!c) c = new BatchCtx();
+    return c;
+}
+
+template <class T>
+size_t put(std::vector<char>& blob, const T* v, size_t count) {
+    size_t off = align256(blob.size());
+    blob.resize(off + sizeof(T) * count);
+    if (count) std::memcpy(blob.data() + off, v, sizeof(T) * count);
+    return off;
+}
+
+}  // namespace
+
+pt_status batch_render(pt_scene* const* scenes, const pt_camera* cams, const uint32_t* spp, uint32_t n,
+                       uint32_t max_depth, uint64_t seed, const pt_render_opts* opts, float* const* d_out,
+                       void* stream) {
+    if (!scenes || !cams || !spp || !d_out || n == 0) return fail(PT_ERR_INVALID_ARG, "empty batch or NULL arrays");
+    if (max_depth > 64) return fail(PT_ERR_INVALID_ARG, "max_depth must be <= 64");
+    pt_render_opts o = opts ? *opts : default_opts();
+    PT_TRY(check_opts(o));
+    const int device = scenes[0] ? scenes[0]->device : -1;
+    std::vector<pt::DevScene> views(n);
+    std::vector<pt::DevCamera> dcs(n);
+    std::vector<unsigned long long> off(n + 1, 0), px_off(n + 1, 0);
+    std::vector<uint32_t> spps(n);
+    std::vector<float*> outs(n);
+    uint32_t max_mats = 1;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!scenes[i]) return fail(PT_ERR_INVALID_ARG, "scene %u is NULL", i);
+        if (scenes[i]->device != device) return fail(PT_ERR_INVALID_ARG, "scene %u is on another device", i);
+        if (spp[i] == 0) return fail(PT_ERR_INVALID_ARG, "spp[%u] must be >= 1", i);
+        PT_TRY(make_camera(&cams[i], dcs[i]));
+        if (!d_out[i] || !is_device_ptr(d_out[i])) return fail(PT_ERR_INVALID_ARG, "d_out[%u] must be device memory", i);
+        views[i] = scenes[i]->view();
+        spps[i] = spp[i];
+        outs[i] = d_out[i];
+        max_mats = std::max(max_mats, scenes[i]->n_mats);
+        const uint64_t px = (uint64_t)cams[i].width * cams[i].height;
+        px_off[i + 1] = px_off[i] + px;
+        off[i + 1] = off[i] + px * spp[i];
+    }
+    const uint64_t total = off[n];
+    if (total >= (1ull << 40)) return fail(PT_ERR_INVALID_ARG, "too many paths");
+    PT_TRY(set_device(scenes[0]));
+    BatchCtx* ctx = batch_ctx(device);
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint64_t cap = o.queue_capacity ? std::min<uint64_t>(o.queue_capacity, total) : std::min<uint64_t>(total, 1ull << 24);
+    cap = std::max<uint64_t>(cap, 1);
+    if (cap >= (1ull << 32)) cap = (1ull << 32) - (1ull << 20);
+    if (ctx->capacity < cap || !ctx->wf.p) {
+        if (ctx->graph) {
+            cudaGraphExecDestroy(ctx->graph);
+            ctx->graph = nullptr;
+        }
+        PT_CUDA(cudaStreamSynchronize(st));
+        PT_TRY(carve_wavefront(ctx->wf, cap, ctx->wfb));
+        ctx->capacity = cap;
+    }
+    PT_TRY(ctx->counters.ensure(256 + 8 * 130));
+    // wave segments: runs of pixels of one scene inside each wave
+    std::vector<pt::BatchSegment> segs;
+    struct Wave {
+        uint64_t w0, w1, flat;
+        uint32_t seg0, nseg;
+    };
+    std::vector<Wave> waves;
+    for (uint64_t w0 = 0; w0 < total; w0 += cap) {
+        const uint64_t w1 = std::min(total, w0 + cap);
+        Wave wv{w0, w1, 0, (uint32_t)segs.size(), 0};
+        for (uint32_t s = 0; s < n; ++s) {
+            if (off[s + 1] <= w0 || off[s] >= w1 || off[s + 1] == off[s]) continue;
+            const uint64_t a = std::max(w0, (uint64_t)off[s]) - off[s], b = std::min(w1, (uint64_t)off[s + 1]) - off[s];
+            const uint64_t p0 = a / spps[s], p1 = (b + spps[s] - 1) / spps[s];
+            pt::BatchSegment sg{s, 0, p0, p1 - p0, wv.flat};
+            segs.push_back(sg);
+            wv.flat += p1 - p0;
+            wv.nseg++;
+        }
+        waves.push_back(wv);
+    }
+    std::vector<char> blob;
+    const size_t o_sc = put(blob, views.data(), n), o_cam = put(blob, dcs.data(), n), o_off = put(blob, off.data(), n + 1),
+                 o_spp = put(blob, spps.data(), n), o_out = put(blob, outs.data(), n),
+                 o_px = put(blob, px_off.data(), n + 1), o_seg = put(blob, segs.data(), segs.size());
+    const unsigned long long seed64 = seed;
+    const size_t o_seed = put(blob, &seed64, 1);
+    if (ctx->tables.bytes < blob.size() && ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    if (ctx->tables.bytes < blob.size()) PT_CUDA(cudaStreamSynchronize(st));
+    PT_TRY(ctx->tables.ensure(std::max<size_t>(blob.size(), 1 << 16)));
+    PT_CUDA(cudaMemcpyAsync(ctx->tables.p, blob.data(), blob.size(), cudaMemcpyHostToDevice, st));
+    char* tb = ctx->tables.as<char>();
+    pt::BatchTables t;
+    t.scenes = reinterpret_cast<const pt::DevScene*>(tb + o_sc);
+    t.cams = reinterpret_cast<const pt::DevCamera*>(tb + o_cam);
+    t.off = reinterpret_cast<const unsigned long long*>(tb + o_off);
+    t.spp = reinterpret_cast<const uint32_t*>(tb + o_spp);
+    t.out = reinterpret_cast<float* const*>(tb + o_out);
+    t.n = n;
+    t.wave_base = reinterpret_cast<unsigned long long*>(ctx->counters.as<char>() + 128);
+    t.seed = reinterpret_cast<const unsigned long long*>(tb + o_seed);
+    const unsigned long long* px_dev = reinterpret_cast<const unsigned long long*>(tb + o_px);
+    const pt::BatchSegment* seg_dev = reinterpret_cast<const pt::BatchSegment*>(tb + o_seg);
+    pt::WfBuffers w = ctx->wfb;
+    w.counts = ctx->counters.as<uint32_t>();
+    w.hist = reinterpret_cast<unsigned long long*>(ctx->counters.as<char>() + 256);
+    w.sig = nullptr;
+    w.capacity = (uint32_t)cap;
+    PT_CUDA(cudaMemsetAsync(ctx->counters.p, 0, ctx->counters.bytes, st));
+    for (uint32_t i = 0; i < n; ++i) PT_CUDA(cudaMemsetAsync(outs[i], 0, (px_off[i + 1] - px_off[i]) * 12, st));
+    if (max_depth == 0) return PT_OK;
+    pt::RenderParams p;
+    p.seed = seed;
+    p.path_begin = 0;
+    p.spp = 1;
+    p.max_depth = max_depth;
+    p.rr_start = o.rr_start;
+    p.rr_fixed = o.rr_fixed;
+    uint32_t n_keys = 0;
+    if (o.sort_mode == PT_SORT_TYPE) n_keys = 4;
+    if (o.sort_mode == PT_SORT_MATERIAL) n_keys = std::min<uint32_t>(max_mats + 1, pt::kMaxSortKeys);
+    const uint32_t sort_mode = o.sort_mode == PT_SORT_TYPE ? 1u : 2u;
+    const uint32_t block = o.block_size ? o.block_size : 256;
+    const int sms = sm_count(device);
+    auto persistent = [&](int which, cudaStream_t s_) {
+        pt::Launch l;
+        l.block = (int)block;
+        l.grid = std::max(1, sms * blocks_per_sm(which, (int)block));
+        l.st = s_;
+        return l;
+    };
+    auto plain = [&](uint64_t work, cudaStream_t s_) {
+        pt::Launch l;
+        l.block = 256;
+        l.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 8));
+        l.st = s_;
+        return l;
+    };
+    auto bounce_loop = [&](cudaStream_t s_) -> pt_status {
+        for (uint32_t b = 0; b < max_depth; ++b)
+            PT_CUDA(pt::launch_bounce_batch(persistent(pt::K_EXTEND_BATCH, s_), persistent(pt::K_SHADE_BATCH, s_),
+                                            persistent(pt::K_SHADOW_BATCH, s_), plain(cap, s_), t, p, w, b, sort_mode,
+                                            n_keys));
+        return PT_OK;
+    };
+    const bool use_graph = !(o.flags & PT_FLAG_NO_GRAPH);
+    if (use_graph) {
+        // the captured loop depends only on these; tables and counters are read from device memory
+        std::vector<uint64_t> key = {cap, max_depth, n_keys, sort_mode, block, o.rr_start,
+                                     (uint64_t)__builtin_bit_cast(uint32_t, o.rr_fixed),
+                                     (uint64_t)(uintptr_t)ctx->tables.p, (uint64_t)(uintptr_t)ctx->wf.p, n};
+        if (!ctx->graph || ctx->graph_key != key) {
+            if (ctx->graph) {
+                cudaGraphExecDestroy(ctx->graph);
+                ctx->graph = nullptr;
+            }
+            if (!ctx->cap_stream) PT_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+            cudaGraph_t graph = nullptr;
+            PT_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+            pt_status cs = bounce_loop(ctx->cap_stream);
+            cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
+            if (cs != PT_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return cs;
+            }
+            if (ce != cudaSuccess) return fail(PT_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&ctx->graph, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) {
+                ctx->graph = nullptr;
+                return fail(PT_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+            }
+            ctx->graph_key = key;
+        }
+    }
+    for (const Wave& wv : waves) {
+        const uint32_t nw = (uint32_t)(wv.w1 - wv.w0);
+        PT_CUDA(pt::launch_raygen_batch(plain(nw, st), t, p, wv.w0, nw, w));
+        if (use_graph) PT_CUDA(cudaGraphLaunch(ctx->graph, st));
+        else PT_TRY(bounce_loop(st));
+        PT_CUDA(pt::launch_reduce_batch(plain(wv.flat, st), t, w.L, seg_dev + wv.seg0, wv.nseg, wv.w0, wv.w1, wv.flat));
+    }
+    PT_CUDA(pt::launch_scale_batch(plain(px_off[n], st), t, px_dev, px_off[n]));
+    return PT_OK;
+}
 
 extern "C" {
 
@@ -813,16 +1030,86 @@ pt_status pt_get_stats(pt_scene* sc, pt_stats* out) {
 pt_status pt_render_batch(pt_scene* const* scenes, const pt_camera* cams, const uint32_t* spp, uint32_t n,
                           uint32_t max_depth, uint64_t seed, const pt_render_opts* opts, float* const* d_out,
                           void* stream) {
-    (void)scenes; (void)cams; (void)spp; (void)n; (void)max_depth; (void)seed; (void)opts; (void)d_out; (void)stream;
-    return fail(PT_ERR_UNSUPPORTED, "pt_render_batch: not implemented yet");
+    return batch_render(scenes, cams, spp, n, max_depth, seed, opts, d_out, stream);
 }
 
 pt_status pt_autotune_batch(pt_scene* const* scenes, const pt_camera* cams, const uint32_t* spp, uint32_t n,
                             uint32_t max_depth, uint64_t seed, const pt_render_opts* base, float* const* d_out,
                             void* stream, pt_render_opts* best, float* best_ms) {
-    (void)scenes; (void)cams; (void)spp; (void)n; (void)max_depth; (void)seed; (void)base; (void)d_out; (void)stream;
-    (void)best; (void)best_ms;
-    return fail(PT_ERR_UNSUPPORTED, "pt_autotune_batch: not implemented yet");
+    if (!best) return fail(PT_ERR_INVALID_ARG, "best is NULL");
+    pt_render_opts o = base ? *base : default_opts();
+    PT_TRY(check_opts(o));
+    o.mode = PT_MODE_WAVEFRONT;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint64_t total = 0;
+    if (!scenes || !cams || !spp || n == 0) return fail(PT_ERR_INVALID_ARG, "empty batch");
+    for (uint32_t i = 0; i < n; ++i) total += (uint64_t)cams[i].width * cams[i].height * spp[i];
+    cudaEvent_t e0, e1;
+    PT_CUDA(cudaEventCreate(&e0));
+    PT_CUDA(cudaEventCreate(&e1));
+    auto time_it = [&](const pt_render_opts& c, float& ms) -> pt_status {
+        PT_TRY(batch_render(scenes, cams, spp, n, max_depth, seed, &c, d_out, stream));   // warm-up, capture
+        float best_t = 1e30f;
+        for (int r = 0; r < 2; ++r) {
+            PT_CUDA(cudaEventRecord(e0, st));
+            PT_TRY(batch_render(scenes, cams, spp, n, max_depth, seed, &c, d_out, stream));
+            PT_CUDA(cudaEventRecord(e1, st));
+            PT_CUDA(cudaEventSynchronize(e1));
+            float t = 0.f;
+            PT_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            best_t = std::min(best_t, t);
+        }
+        ms = best_t;
+        return PT_OK;
+    };
+    // coordinate descent: queue capacity, then block size, then sort granularity
+    std::vector<uint64_t> caps;
+    for (uint64_t c : {1ull << 21, 1ull << 22, 1ull << 23, 1ull << 24, 1ull << 25})
+        if (c < total) caps.push_back(c);
+    caps.push_back(std::min<uint64_t>(total, 1ull << 26));
+    pt_render_opts cur = o;
+    cur.sort_mode = PT_SORT_NONE;
+    cur.block_size = 256;
+    float cur_ms = 1e30f;
+    pt_status s = PT_OK;
+    for (uint64_t c : caps) {
+        pt_render_opts t = cur;
+        t.queue_capacity = c;
+        float ms;
+        if ((s = time_it(t, ms)) != PT_OK) break;
+        if (ms < cur_ms) {
+            cur_ms = ms;
+            cur.queue_capacity = c;
+        }
+    }
+    for (uint32_t bs : {128u}) {
+        if (s != PT_OK) break;
+        pt_render_opts t = cur;
+        t.block_size = bs;
+        float ms;
+        if ((s = time_it(t, ms)) != PT_OK) break;
+        if (ms < cur_ms) {
+            cur_ms = ms;
+            cur.block_size = bs;
+        }
+    }
+    for (uint32_t sm : {(uint32_t)PT_SORT_TYPE, (uint32_t)PT_SORT_MATERIAL}) {
+        if (s != PT_OK) break;
+        pt_render_opts t = cur;
+        t.sort_mode = sm;
+        float ms;
+        if ((s = time_it(t, ms)) != PT_OK) break;
+        if (ms < cur_ms) {
+            cur_ms = ms;
+            cur.sort_mode = sm;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != PT_OK) return s;
+    *best = cur;
+    if (best_ms) *best_ms = cur_ms;
+    return PT_OK;
 }
 
 }  // extern "C"

@@ -156,54 +156,125 @@ __global__ void k_debug_paths(DevScene s, DevCamera c, RenderParams p, const uns
 }
 
 // ================================================================== wavefront stages
-// Ray generation: one queue record per path of the wave, radiance zeroed, active count = n.
-__global__ void __launch_bounds__(256) k_raygen(DevCamera c, RenderParams p, uint32_t n, WfBuffers w) {
+// Scene sources: where a wavefront kernel finds the scene, camera and path numbering of a queue
+// entry.  SingleSrc: one scene passed by value (pt_render).  TableSrc: many scenes in device
+// tables, the scene found from the global path id by binary search over the scenes' first path ids
+// (pt_render_batch).  The per-path arithmetic is the same shared device code either way.
+struct PathLoc {
+    uint64_t path;     // global path id (signature index)
+    uint32_t pixel, sample, sid;
+};
+
+struct SingleSrc {
+    DevScene s;
+    DevCamera c;
+    RenderParams p;
+    __device__ __forceinline__ uint64_t base() const { return p.path_begin; }
+    __device__ __forceinline__ uint32_t sid_of(uint64_t, uint32_t) const { return 0; }
+    __device__ __forceinline__ PathLoc locate(uint64_t base, uint32_t pid) const {
+        PathLoc l;
+        l.path = base + pid;
+        l.pixel = (uint32_t)(l.path / p.spp);
+        l.sample = (uint32_t)(l.path - (uint64_t)l.pixel * p.spp);
+        l.sid = 0;
+        return l;
+    }
+    __device__ __forceinline__ DevScene scene(uint32_t) const { return s; }
+    __device__ __forceinline__ DevCamera camera(uint32_t) const { return c; }
+    __device__ __forceinline__ RenderParams params(uint32_t) const { return p; }
+};
+
+struct TableSrc {
+    BatchTables t;
+    RenderParams p;    // depth and roulette (spp per scene and the seed from the tables)
+    __device__ __forceinline__ uint64_t base() const { return *t.wave_base; }
+    __device__ __forceinline__ uint32_t sid_of(uint64_t base, uint32_t pid) const {
+        const uint64_t g = base + pid;
+        uint32_t lo = 0, hi = t.n - 1;                  // last scene with off[s] <= g
+        while (lo < hi) {
+            uint32_t mid = (lo + hi + 1) >> 1;
+            if (__ldg(t.off + mid) <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    }
+    __device__ __forceinline__ PathLoc locate(uint64_t base, uint32_t pid) const {
+        PathLoc l;
+        l.sid = sid_of(base, pid);
+        l.path = base + pid;
+        const uint64_t local = l.path - __ldg(t.off + l.sid);
+        const uint32_t spp = __ldg(t.spp + l.sid);
+        l.pixel = (uint32_t)(local / spp);
+        l.sample = (uint32_t)(local - (uint64_t)l.pixel * spp);
+        return l;
+    }
+    __device__ __forceinline__ DevScene scene(uint32_t sid) const { return t.scenes[sid]; }
+    __device__ __forceinline__ DevCamera camera(uint32_t sid) const { return t.cams[sid]; }
+    __device__ __forceinline__ RenderParams params(uint32_t sid) const {
+        RenderParams q = p;
+        q.spp = __ldg(t.spp + sid);
+        q.seed = __ldg(t.seed);
+        return q;
+    }
+};
+
+// Ray generation: one queue record per path of the wave, radiance zeroed, active count = n.  The
+// wave's first path id is a launch argument here and is published to device memory (wave_base_dev)
+// for the kernels of the bounce loop.
+template <class Src>
+__global__ void __launch_bounds__(256) k_raygen(Src src, uint64_t base, uint32_t n, WfBuffers w,
+                                                unsigned long long* wave_base_dev) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint64_t path = p.path_begin + i;
-        const uint32_t pixel = (uint32_t)(path / p.spp);
-        const uint32_t sample = (uint32_t)(path - (uint64_t)pixel * p.spp);
-        const uint32_t key = path_key(p.seed, pixel, sample);
+        const PathLoc l = src.locate(base, i);
+        const RenderParams p = src.params(l.sid);
+        const uint32_t key = path_key(p.seed, l.pixel, l.sample);
         float3 o, d;
-        camera_ray(c, pixel, key, o, d);
+        camera_ray(src.camera(l.sid), l.pixel, key, o, d);
         w.q_o[0][i] = f4(o, __uint_as_float(i));
         w.q_d[0][i] = f4(d, __uint_as_float(1u));            // previous vertex "delta": the camera
         w.q_tp[0][i] = make_float4(1.f, 1.f, 1.f, 0.f);
         w.L[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (w.sig) w.sig[path] = 0u;
+        if (w.sig) w.sig[l.path] = 0u;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         w.counts[0] = n;
         w.counts[1] = 0u;
         w.counts[2] = 0u;
+        if (wave_base_dev) *wave_base_dev = base;
     }
 }
 
 // Extend: closest hit of every active ray (scene-intersection stage); hit records per queue slot.
-__global__ void __launch_bounds__(256) k_extend(DevScene s, WfBuffers w, int in) {
+template <class Src>
+__global__ void __launch_bounds__(256) k_extend(Src src, WfBuffers w, int in) {
     const uint32_t n = min(w.counts[0], w.capacity);
+    const uint64_t base = src.base();
     const float4* __restrict__ qo = w.q_o[in];
     const float4* __restrict__ qd = w.q_d[in];
     float2* __restrict__ hit = w.hit;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         float4 o4 = qo[j], d4 = qd[j];
-        Hit h = trace_closest(s, xyz(o4), xyz(d4));
+        Hit h = trace_closest(src.scene(src.sid_of(base, __float_as_uint(o4.w))), xyz(o4), xyz(d4));
         hit[j] = make_float2(h.t, __uint_as_float(h.tri));
     }
 }
 
 // Key sort before shading (counting sort): keys + block histograms, scan, scatter into `perm`.
-__global__ void __launch_bounds__(256) k_sort_keys(DevScene s, WfBuffers w, uint32_t mode, uint32_t n_keys) {
+template <class Src>
+__global__ void __launch_bounds__(256) k_sort_keys(Src src, WfBuffers w, int in, uint32_t mode, uint32_t n_keys) {
     extern __shared__ uint32_t hist_s[];
     for (uint32_t k = threadIdx.x; k < n_keys; k += blockDim.x) hist_s[k] = 0u;
     __syncthreads();
     const uint32_t n = min(w.counts[0], w.capacity);
+    const uint64_t base = src.base();
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         uint32_t tri = __float_as_uint(w.hit[j].y);
         uint32_t key = n_keys - 1u;                          // misses last
         if (tri != kMiss) {
+            const DevScene s = src.scene(src.sid_of(base, __float_as_uint(w.q_o[in][j].w)));
             uint32_t m = __float_as_uint(__ldg(s.tris + 3 * (size_t)tri + 1).w);
             key = mode == 1u ? __float_as_uint(__ldg(reinterpret_cast<const float*>(s.mats + m))) : m;
             key = min(key, n_keys - 2u);
@@ -261,16 +332,15 @@ __global__ void __launch_bounds__(256) k_sort_scatter(WfBuffers w) {
 }
 
 // Shade: emission, NEE sample (-> shadow queue), BSDF sample, roulette, compaction of survivors.
-template <bool SIG>
-__global__ void __launch_bounds__(256) k_shade(DevScene s, RenderParams p, WfBuffers w, int in, uint32_t b,
-                                               bool sorted) {
+template <class Src, bool SIG>
+__global__ void __launch_bounds__(256) k_shade(Src src, WfBuffers w, int in, uint32_t b, bool sorted) {
     const uint32_t n = min(w.counts[0], w.capacity);
+    const uint64_t base = src.base();
     const int out = in ^ 1;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
-    const float3 env = f3(s.env_r, s.env_g, s.env_b);
-    for (uint32_t base = warp * 32u; base < n; base += n_warps * 32u) {
-        const uint32_t j = base + lane_id();
+    for (uint32_t wb = warp * 32u; wb < n; wb += n_warps * 32u) {
+        const uint32_t j = wb + lane_id();
         bool want_ray = false, want_shadow = false;
         float4 ro, rd, rtp, so, sd, sc;
         if (j < n) {
@@ -278,17 +348,17 @@ __global__ void __launch_bounds__(256) k_shade(DevScene s, RenderParams p, WfBuf
             const float4 o4 = w.q_o[in][slot], d4 = w.q_d[in][slot], tp4 = w.q_tp[in][slot];
             const float2 hh = w.hit[slot];
             const uint32_t pid = __float_as_uint(o4.w);
-            const uint64_t path = p.path_begin + pid;
+            const PathLoc l = src.locate(base, pid);
+            const DevScene s = src.scene(l.sid);
             const float3 tp = xyz(tp4);
             const uint32_t tri = __float_as_uint(hh.y);
             if (tri == kMiss) {
-                float3 L = add_rn(xyz(w.L[pid]), mul_rn(tp, env));
+                float3 L = add_rn(xyz(w.L[pid]), mul_rn(tp, f3(s.env_r, s.env_g, s.env_b)));
                 w.L[pid] = f4(L, 0.f);
-                if (SIG) w.sig[path] ^= sig_event(b, 0, kMiss);
+                if (SIG) w.sig[l.path] ^= sig_event(b, 0, kMiss);
             } else {
-                const uint32_t pixel = (uint32_t)(path / p.spp);
-                const uint32_t sample = (uint32_t)(path - (uint64_t)pixel * p.spp);
-                const uint32_t key = path_key(p.seed, pixel, sample);
+                const RenderParams p = src.params(l.sid);
+                const uint32_t key = path_key(p.seed, l.pixel, l.sample);
                 Vertex V = shade_vertex(s, p, key, b, xyz(o4), xyz(d4), tp, (__float_as_uint(d4.w) & 1u) != 0u,
                                         hh.x, tri);
                 if (V.emit_counted) {
@@ -319,7 +389,7 @@ __global__ void __launch_bounds__(256) k_shade(DevScene s, RenderParams p, WfBuf
                         rtp = f4(V.ntp, 0.f);
                     }
                 }
-                if (SIG) w.sig[path] ^= sg;
+                if (SIG) w.sig[l.path] ^= sg;
             }
         }
         const uint32_t k = warp_append(&w.counts[2], want_shadow);
@@ -329,7 +399,7 @@ __global__ void __launch_bounds__(256) k_shade(DevScene s, RenderParams p, WfBuf
                 w.s_d[k] = sd;
                 w.s_c[k] = sc;
             } else {
-                atomicOr(s.status, ST_QUEUE);
+                atomicOr(src.scene(0).status, ST_QUEUE);
             }
         }
         const uint32_t q = warp_append(&w.counts[1], want_ray);
@@ -339,7 +409,7 @@ __global__ void __launch_bounds__(256) k_shade(DevScene s, RenderParams p, WfBuf
                 w.q_d[out][q] = rd;
                 w.q_tp[out][q] = rtp;
             } else {
-                atomicOr(s.status, ST_QUEUE);
+                atomicOr(src.scene(0).status, ST_QUEUE);
             }
         }
     }
@@ -347,14 +417,15 @@ __global__ void __launch_bounds__(256) k_shade(DevScene s, RenderParams p, WfBuf
 
 // Shadow: any-hit test of each queued shadow ray; unoccluded contributions are added to the path.
 // At most one shadow ray per path per bounce, so the read-modify-write of L needs no atomics.
-template <bool SIG>
-__global__ void __launch_bounds__(256) k_shadow(DevScene s, RenderParams p, WfBuffers w, uint32_t b) {
+template <class Src, bool SIG>
+__global__ void __launch_bounds__(256) k_shadow(Src src, WfBuffers w, uint32_t b) {
     const uint32_t n = min(w.counts[2], w.capacity);
+    const uint64_t base = src.base();
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         const float4 so = w.s_o[j], sd = w.s_d[j];
-        const bool occ = trace_any(s, xyz(so), xyz(sd), so.w);
         const uint32_t pid = __float_as_uint(sd.w);
+        const bool occ = trace_any(src.scene(src.sid_of(base, pid)), xyz(so), xyz(sd), so.w);
         if (!occ) {
             const float4 sc = w.s_c[j];
             float3 L = add_rn(xyz(w.L[pid]), xyz(sc));
@@ -362,7 +433,7 @@ __global__ void __launch_bounds__(256) k_shadow(DevScene s, RenderParams p, WfBu
         }
         if (SIG) {
             const uint32_t lj = __float_as_uint(w.s_c[j].w);
-            w.sig[p.path_begin + pid] ^= sig_event(b, 1, (lj << 2) | 2u | (occ ? 0u : 1u));
+            w.sig[base + pid] ^= sig_event(b, 1, (lj << 2) | 2u | (occ ? 0u : 1u));
         }
     }
 }
@@ -403,6 +474,60 @@ __global__ void k_copy_L(const float4* __restrict__ L4, uint64_t n, float* __res
         out[3 * i] = v.x;
         out[3 * i + 1] = v.y;
         out[3 * i + 2] = v.z;
+    }
+}
+
+// Batched accumulation: add this wave's samples of each pixel, in sample order, to the pixel's
+// running FP32 sum in its scene's output image (zeroed before the first wave).  A pixel split
+// between two waves continues from the stored partial sum, so the additions are exactly those of
+// the single-scene reduce.
+__global__ void __launch_bounds__(256) k_reduce_batch(BatchTables t, const float4* __restrict__ L,
+                                                      const BatchSegment* __restrict__ seg, uint32_t n_seg,
+                                                      unsigned long long w0, unsigned long long w1,
+                                                      unsigned long long n_flat) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < n_flat; f += stride) {
+        uint32_t lo = 0, hi = n_seg - 1;
+        while (lo < hi) {
+            uint32_t mid = (lo + hi + 1) >> 1;
+            if (seg[mid].flat_begin <= f) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchSegment sg = seg[lo];
+        const uint64_t px = sg.px_begin + (f - sg.flat_begin);
+        const uint32_t spp = t.spp[sg.scene];
+        const uint64_t first = t.off[sg.scene] + px * spp;
+        const uint64_t a = first > w0 ? first : w0;
+        const uint64_t e = first + spp < w1 ? first + spp : w1;
+        float* o = t.out[sg.scene] + 3 * px;
+        float r = o[0], g = o[1], bl = o[2];
+        for (uint64_t q = a; q < e; ++q) {
+            const float4 v = L[q - w0];
+            r = __fadd_rn(r, v.x);
+            g = __fadd_rn(g, v.y);
+            bl = __fadd_rn(bl, v.z);
+        }
+        o[0] = r;
+        o[1] = g;
+        o[2] = bl;
+    }
+}
+
+// Batched accumulation, last step: sums -> means (the single-scene reduce's final multiply).
+__global__ void k_scale_batch(BatchTables t, const unsigned long long* __restrict__ px_off, unsigned long long total) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += stride) {
+        uint32_t lo = 0, hi = t.n - 1;
+        while (lo < hi) {
+            uint32_t mid = (lo + hi + 1) >> 1;
+            if (px_off[mid] <= f) lo = mid;
+            else hi = mid - 1;
+        }
+        const float inv = 1.0f / (float)t.spp[lo];
+        float* o = t.out[lo] + 3 * (f - px_off[lo]);
+        o[0] = __fmul_rn(o[0], inv);
+        o[1] = __fmul_rn(o[1], inv);
+        o[2] = __fmul_rn(o[2], inv);
     }
 }
 
@@ -616,19 +741,23 @@ cudaError_t launch_debug_paths(cudaStream_t st, const DevScene& s, const DevCame
 }
 
 cudaError_t launch_raygen(const Launch& l, const DevCamera& c, const RenderParams& p, uint32_t n, const WfBuffers& w) {
-    k_raygen<<<l.grid, l.block, 0, l.st>>>(c, p, n, w);
+    SingleSrc src{DevScene{}, c, p};
+    k_raygen<SingleSrc><<<l.grid, l.block, 0, l.st>>>(src, p.path_begin, n, w, nullptr);
     return cudaGetLastError();
 }
 
-cudaError_t launch_extend(const Launch& l, const DevScene& s, const WfBuffers& w, int in) {
-    k_extend<<<l.grid, l.block, 0, l.st>>>(s, w, in);
+cudaError_t launch_extend(const Launch& l, const DevScene& s, const WfBuffers& w, int in, const RenderParams& p) {
+    SingleSrc src{s, DevCamera{}, p};
+    k_extend<SingleSrc><<<l.grid, l.block, 0, l.st>>>(src, w, in);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sort(const Launch& l, const DevScene& s, const WfBuffers& w, uint32_t mode, uint32_t n_keys) {
+cudaError_t launch_sort(const Launch& l, const DevScene& s, const WfBuffers& w, int in, uint32_t mode, uint32_t n_keys,
+                        const RenderParams& p) {
     cudaError_t e = cudaMemsetAsync(w.bucket, 0, sizeof(uint32_t) * n_keys, l.st);
     if (e != cudaSuccess) return e;
-    k_sort_keys<<<l.grid, l.block, sizeof(uint32_t) * n_keys, l.st>>>(s, w, mode, n_keys);
+    SingleSrc src{s, DevCamera{}, p};
+    k_sort_keys<SingleSrc><<<l.grid, l.block, sizeof(uint32_t) * n_keys, l.st>>>(src, w, in, mode, n_keys);
     k_sort_scan<<<1, 1024, 0, l.st>>>(w, n_keys);
     k_sort_scatter<<<l.grid, l.block, 0, l.st>>>(w);
     return cudaGetLastError();
@@ -636,15 +765,57 @@ cudaError_t launch_sort(const Launch& l, const DevScene& s, const WfBuffers& w, 
 
 cudaError_t launch_shade(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w, int in,
                          uint32_t bounce, bool sorted) {
-    if (w.sig) k_shade<true><<<l.grid, l.block, 0, l.st>>>(s, p, w, in, bounce, sorted);
-    else k_shade<false><<<l.grid, l.block, 0, l.st>>>(s, p, w, in, bounce, sorted);
+    SingleSrc src{s, DevCamera{}, p};
+    if (w.sig) k_shade<SingleSrc, true><<<l.grid, l.block, 0, l.st>>>(src, w, in, bounce, sorted);
+    else k_shade<SingleSrc, false><<<l.grid, l.block, 0, l.st>>>(src, w, in, bounce, sorted);
     return cudaGetLastError();
 }
 
 cudaError_t launch_shadow(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w,
                           uint32_t bounce) {
-    if (w.sig) k_shadow<true><<<l.grid, l.block, 0, l.st>>>(s, p, w, bounce);
-    else k_shadow<false><<<l.grid, l.block, 0, l.st>>>(s, p, w, bounce);
+    SingleSrc src{s, DevCamera{}, p};
+    if (w.sig) k_shadow<SingleSrc, true><<<l.grid, l.block, 0, l.st>>>(src, w, bounce);
+    else k_shadow<SingleSrc, false><<<l.grid, l.block, 0, l.st>>>(src, w, bounce);
+    return cudaGetLastError();
+}
+
+// ---- batched (TableSrc) launchers
+cudaError_t launch_raygen_batch(const Launch& l, const BatchTables& t, const RenderParams& p, uint64_t base, uint32_t n,
+                                const WfBuffers& w) {
+    TableSrc src{t, p};
+    k_raygen<TableSrc><<<l.grid, l.block, 0, l.st>>>(src, base, n, w, t.wave_base);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bounce_batch(const Launch& le, const Launch& ls, const Launch& lw, const Launch& lk,
+                                const BatchTables& t, const RenderParams& p, const WfBuffers& w, uint32_t b,
+                                uint32_t sort_mode, uint32_t n_keys) {
+    TableSrc src{t, p};
+    const int in = (int)(b & 1u);
+    k_extend<TableSrc><<<le.grid, le.block, 0, le.st>>>(src, w, in);
+    if (n_keys) {
+        cudaError_t e = cudaMemsetAsync(w.bucket, 0, sizeof(uint32_t) * n_keys, lk.st);
+        if (e != cudaSuccess) return e;
+        k_sort_keys<TableSrc><<<lk.grid, lk.block, sizeof(uint32_t) * n_keys, lk.st>>>(src, w, in, sort_mode, n_keys);
+        k_sort_scan<<<1, 1024, 0, lk.st>>>(w, n_keys);
+        k_sort_scatter<<<lk.grid, lk.block, 0, lk.st>>>(w);
+    }
+    k_shade<TableSrc, false><<<ls.grid, ls.block, 0, ls.st>>>(src, w, in, b, n_keys > 0);
+    k_shadow<TableSrc, false><<<lw.grid, lw.block, 0, lw.st>>>(src, w, b);
+    k_prepare<<<1, 1, 0, le.st>>>(w, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_batch(const Launch& l, const BatchTables& t, const float4* L, const BatchSegment* seg,
+                                uint32_t n_seg, uint64_t w0, uint64_t w1, uint64_t n_flat) {
+    if (n_flat == 0) return cudaSuccess;
+    k_reduce_batch<<<l.grid, l.block, 0, l.st>>>(t, L, seg, n_seg, w0, w1, n_flat);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_batch(const Launch& l, const BatchTables& t, const unsigned long long* px_off, uint64_t total) {
+    if (total == 0) return cudaSuccess;
+    k_scale_batch<<<l.grid, l.block, 0, l.st>>>(t, px_off, total);
     return cudaGetLastError();
 }
 
@@ -702,9 +873,12 @@ int max_blocks_per_sm(int which, int block) {
     cudaError_t e = cudaErrorInvalidValue;
     switch (which) {
         case K_MEGA: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_megakernel<false>, block, 0); break;
-        case K_EXTEND: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend, block, 0); break;
-        case K_SHADE: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<false>, block, 0); break;
-        case K_SHADOW: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shadow<false>, block, 0); break;
+        case K_EXTEND: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend<SingleSrc>, block, 0); break;
+        case K_SHADE: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<SingleSrc, false>, block, 0); break;
+        case K_SHADOW: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shadow<SingleSrc, false>, block, 0); break;
+        case K_EXTEND_BATCH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend<TableSrc>, block, 0); break;
+        case K_SHADE_BATCH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<TableSrc, false>, block, 0); break;
+        case K_SHADOW_BATCH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shadow<TableSrc, false>, block, 0); break;
         case K_ADJOINT: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adjoint<16>, block, 16 * 1024); break;
         default: break;
     }

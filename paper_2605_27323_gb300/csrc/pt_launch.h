@@ -27,13 +27,26 @@ cudaError_t launch_debug_paths(cudaStream_t st, const DevScene& s, const DevCame
 
 // Wavefront stages (Sec. 2.3, 3.1).  `in` selects the ping-pong queue read this bounce.
 cudaError_t launch_raygen(const Launch& l, const DevCamera& c, const RenderParams& p, uint32_t n, const WfBuffers& w);
-cudaError_t launch_extend(const Launch& l, const DevScene& s, const WfBuffers& w, int in);
-cudaError_t launch_sort(const Launch& l, const DevScene& s, const WfBuffers& w, uint32_t mode, uint32_t n_keys);
+cudaError_t launch_extend(const Launch& l, const DevScene& s, const WfBuffers& w, int in, const RenderParams& p);
+cudaError_t launch_sort(const Launch& l, const DevScene& s, const WfBuffers& w, int in, uint32_t mode, uint32_t n_keys,
+                        const RenderParams& p);
 cudaError_t launch_shade(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w, int in,
                          uint32_t bounce, bool sorted);
 cudaError_t launch_shadow(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w,
                           uint32_t bounce);
 cudaError_t launch_prepare(cudaStream_t st, const WfBuffers& w, uint32_t bounce);
+
+// Batched wavefront over device scene tables (TableSrc): raygen of one wave (publishes the wave
+// base), one bounce of extend/(sort)/shade/shadow/prepare (capturable: no host-varying arguments),
+// accumulation of a wave into the scenes' running sums, and the final sums -> means.
+cudaError_t launch_raygen_batch(const Launch& l, const BatchTables& t, const RenderParams& p, uint64_t base, uint32_t n,
+                                const WfBuffers& w);
+cudaError_t launch_bounce_batch(const Launch& le, const Launch& ls, const Launch& lw, const Launch& lk,
+                                const BatchTables& t, const RenderParams& p, const WfBuffers& w, uint32_t b,
+                                uint32_t sort_mode, uint32_t n_keys);
+cudaError_t launch_reduce_batch(const Launch& l, const BatchTables& t, const float4* L, const BatchSegment* seg,
+                                uint32_t n_seg, uint64_t w0, uint64_t w1, uint64_t n_flat);
+cudaError_t launch_scale_batch(const Launch& l, const BatchTables& t, const unsigned long long* px_off, uint64_t total);
 
 // Accumulation (Sec. 2.3): img[pixel] = (1/spp) * sum_s L[pixel * spp + s], samples in order.
 // L has `stride` floats per path (3 or 4), wave-local; pixels [pixel_begin, pixel_begin + n_pixels).
@@ -56,6 +69,7 @@ cudaError_t launch_debug_rng(const Launch& l, uint64_t seed, const uint32_t* px,
 
 // Occupancy helpers.
 int max_blocks_per_sm(int which, int block);   // which: 0 megakernel, 1 extend, 2 shade, 3 shadow, 4 adjoint
-enum { K_MEGA = 0, K_EXTEND = 1, K_SHADE = 2, K_SHADOW = 3, K_ADJOINT = 4 };
+enum { K_MEGA = 0, K_EXTEND = 1, K_SHADE = 2, K_SHADOW = 3, K_ADJOINT = 4, K_EXTEND_BATCH = 5, K_SHADE_BATCH = 6,
+       K_SHADOW_BATCH = 7 };
 
 }  // namespace pt

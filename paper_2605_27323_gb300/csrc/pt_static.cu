@@ -173,8 +173,8 @@ extern "C" pt_status pt_render_wavefront_static(pt_scene* scene, const pt_camera
         if ((e = pt::launch_raygen(plain(n), dc, p, n, w)) != cudaSuccess) return cuda_fail(e, "raygen");
         for (uint32_t b = 0; b < max_depth; ++b) {
             const int in = (int)(b & 1u);
-            if ((e = pt::launch_extend(persistent(pt::K_EXTEND), ds, w, in)) != cudaSuccess) return cuda_fail(e, "extend");
-            if (n_keys && (e = pt::launch_sort(plain(n), ds, w, sort_mode, n_keys)) != cudaSuccess)
+            if ((e = pt::launch_extend(persistent(pt::K_EXTEND), ds, w, in, p)) != cudaSuccess) return cuda_fail(e, "extend");
+            if (n_keys && (e = pt::launch_sort(plain(n), ds, w, in, sort_mode, n_keys, p)) != cudaSuccess)
                 return cuda_fail(e, "sort");
             if ((e = pt::launch_shade(persistent(pt::K_SHADE), ds, p, w, in, b, n_keys > 0)) != cudaSuccess)
                 return cuda_fail(e, "shade");

@@ -73,6 +73,29 @@ struct WfBuffers {
     uint32_t capacity;
 };
 
+// Device tables of a batched render (many scenes in one wavefront): per scene its view, camera,
+// first global path id (off[n] = total), spp and output image; the current wave's first global path
+// id lives in device memory so that one captured bounce loop serves every wave.
+struct BatchTables {
+    const DevScene* scenes;
+    const DevCamera* cams;
+    const unsigned long long* off;     // n + 1 entries
+    const uint32_t* spp;
+    float* const* out;
+    uint32_t n;
+    unsigned long long* wave_base;
+    const unsigned long long* seed;    // device copy of the seed (graph replays stay valid across seeds)
+};
+
+// One run of whole or partial pixels of one scene inside a wave (batched accumulation).
+struct BatchSegment {
+    uint32_t scene;
+    uint32_t pad;
+    unsigned long long px_begin;
+    unsigned long long px_count;
+    unsigned long long flat_begin;     // prefix of px_count over the wave's segments
+};
+
 constexpr uint32_t kMaxSortKeys = 4096;
 constexpr uint32_t kMaxEvents = 64;     // event-log capacity per path (testing aid)
 
