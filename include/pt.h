@@ -132,8 +132,12 @@ pt_status pt_render(pt_scene* scene, const pt_camera* cam, uint32_t spp, uint32_
 
 /* Path-replay adjoint: accumulate d(loss)/d(albedo) and d(loss)/d(emission) for the image that
  * pt_render produces with the same arguments, given d_grad_rgb = d(loss)/d(image) (H x W x 3,
- * host or device).  Paths are re-traced from the random numbers (no path storage); Russian
- * roulette probabilities are treated as constants.  d_grad_albedo (device n_mats x 3) and
+ * host or device).  Paths are re-traced from the random numbers (no path storage between forward
+ * and backward); Russian roulette probabilities are treated as constants.  opts->mode selects the
+ * replay: PT_MODE_WAVEFRONT (default) re-runs the wavefront stages with shading that writes a
+ * 64-byte record per path and vertex into a library workspace (waves are sized to keep it under
+ * 8 GiB), then walks each path's records backward; PT_MODE_MEGAKERNEL replays each path in one
+ * thread with the records in thread-local memory.  d_grad_albedo (device n_mats x 3) and
  * d_grad_emission (device n_mats) are ACCUMULATED into (the caller zeroes them).  max_depth <= 32
  * (else PT_ERR_UNSUPPORTED). */
 pt_status pt_render_backward(pt_scene* scene, const pt_camera* cam, uint32_t spp, uint32_t max_depth,

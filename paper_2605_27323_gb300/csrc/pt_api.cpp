@@ -159,7 +159,7 @@ struct pt_scene {
     DevBuf wf;
     uint64_t wf_capacity = 0;
     pt::WfBuffers wfb{};
-    DevBuf pathL, img_stage, grad_stage, counters;
+    DevBuf pathL, img_stage, grad_stage, counters, adj;
     cudaStream_t last_stream = nullptr;
     uint32_t last_mode = 0;
     uint64_t last_paths = 0;
@@ -917,12 +917,48 @@ pt_status pt_render_backward(pt_scene* sc, const pt_camera* cam, uint32_t spp, u
     p.max_depth = max_depth;
     p.rr_start = o.rr_start;
     p.rr_fixed = o.rr_fixed;
-    pt::Launch l = launch_for(sc, pt::K_ADJOINT, o.block_size, 128, st, n_paths);
     size_t ev = 0;
     PT_TRY(sc->ev_begin(ST_ADJOINT, st, ev));
-    PT_CUDA(pt::launch_adjoint(l, sc->view(), dc, p, n_paths, grad, d_grad_albedo, d_grad_emission, max_depth));
+    if (o.mode == PT_MODE_MEGAKERNEL) {
+        pt::Launch l = launch_for(sc, pt::K_ADJOINT, o.block_size, 128, st, n_paths);
+        PT_CUDA(pt::launch_adjoint(l, sc->view(), dc, p, n_paths, grad, d_grad_albedo, d_grad_emission, max_depth));
+        sc->launches += 1;
+    } else {
+        // wavefront replay: the forward stages with record-writing shading, then one reverse pass per wave
+        const uint64_t per_path = 180 + 64ull * max_depth;
+        uint64_t cap = std::min<uint64_t>(n_paths, (8ull << 30) / per_path);
+        cap = std::max<uint64_t>(cap - cap % spp, spp);
+        if (cap >= (1ull << 32)) cap = ((1ull << 32) - (1ull << 20)) / spp * spp;
+        PT_TRY(sc->ensure_wf(cap));
+        const size_t rec_bytes = align256(cap * max_depth * 64);
+        PT_TRY(sc->adj.ensure(rec_bytes + align256(cap * 4)));
+        pt::WfBuffers w = sc->wfb;
+        w.counts = sc->counts();
+        w.hist = sc->hist();
+        w.sig = nullptr;
+        w.capacity = (uint32_t)cap;
+        pt::AdjBuffers ab;
+        ab.rec = sc->adj.as<float4>();
+        ab.pend = reinterpret_cast<uint32_t*>(sc->adj.as<char>() + rec_bytes);
+        const pt::DevScene ds = sc->view();
+        for (uint64_t w0 = 0; w0 < n_paths; w0 += cap) {
+            const uint32_t n = (uint32_t)std::min<uint64_t>(cap, n_paths - w0);
+            pt::RenderParams pw = p;
+            pw.path_begin = w0;
+            PT_CUDA(pt::launch_raygen(simple_launch(sc, st, n), dc, pw, n, w));
+            for (uint32_t b = 0; b < max_depth; ++b) {
+                const int in = (int)(b & 1u);
+                PT_CUDA(pt::launch_extend(launch_for(sc, pt::K_EXTEND, o.block_size, 256, st, n), ds, w, in, pw));
+                PT_CUDA(pt::launch_shade_adj(launch_for(sc, pt::K_SHADE_ADJ, o.block_size, 256, st, n), ds, pw, w, ab, in, b));
+                PT_CUDA(pt::launch_shadow_adj(launch_for(sc, pt::K_SHADOW_ADJ, o.block_size, 256, st, n), ds, pw, w, ab, b));
+                PT_CUDA(pt::launch_prepare(st, w, b));
+            }
+            PT_CUDA(pt::launch_adjoint_reverse(simple_launch(sc, st, n), ds, pw, w, ab, n, grad, d_grad_albedo,
+                                               d_grad_emission));
+            sc->launches += 2 + 4 * max_depth;
+        }
+    }
     PT_TRY(sc->ev_end(ev, st));
-    sc->launches += 1;
     return PT_OK;
 }
 

@@ -438,6 +438,99 @@ __global__ void __launch_bounds__(256) k_shadow(Src src, WfBuffers w, uint32_t b
     }
 }
 
+// ---- wavefront adjoint: shading that records what the reverse pass needs instead of adding
+// radiance (the same shade_vertex decisions, so the replay follows the forward paths exactly).
+__global__ void __launch_bounds__(256) k_shade_adj(SingleSrc src, WfBuffers w, AdjBuffers a, int in, uint32_t b) {
+    const uint32_t n = min(w.counts[0], w.capacity);
+    const uint64_t base = src.base();
+    const int out = in ^ 1;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    const size_t cap = w.capacity;
+    for (uint32_t wb = warp * 32u; wb < n; wb += n_warps * 32u) {
+        const uint32_t j = wb + lane_id();
+        bool want_ray = false, want_shadow = false;
+        float4 ro, rd, rtp, so, sd;
+        if (j < n) {
+            const float4 o4 = w.q_o[in][j], d4 = w.q_d[in][j], tp4 = w.q_tp[in][j];
+            const float2 hh = w.hit[j];
+            const uint32_t pid = __float_as_uint(o4.w);
+            const uint32_t tri = __float_as_uint(hh.y);
+            if (tri == kMiss) {
+                a.pend[pid] = b | (1u << 8);
+            } else {
+                const PathLoc l = src.locate(base, pid);
+                const RenderParams& p = src.p;
+                const uint32_t key = path_key(p.seed, l.pixel, l.sample);
+                Vertex V = shade_vertex(src.s, p, key, b, xyz(o4), xyz(d4), xyz(tp4), (__float_as_uint(d4.w) & 1u) != 0u,
+                                        hh.x, tri);
+                uint32_t flags = V.emit_counted ? 4u : 0u;
+                const float Le = V.emit_counted ? __ldg(&src.s.mats[V.mat].emission) : 0.f;
+                float Lj = 0.f;
+                float4 r1 = make_float4(0.f, 0.f, 0.f, 0.f), r2 = r1;
+                if (!V.last) {
+                    if (V.nee && V.cast) {
+                        want_shadow = true;
+                        flags |= 8u;
+                        so = f4(V.s_o, V.s_tmax);
+                        sd = f4(V.s_d, __uint_as_float(pid));
+                        r2 = f4(V.nee_g, V.nee_dfa.x);
+                        Lj = __ldg(&src.s.mats[V.light_mat].emission);
+                    }
+                    if (V.cont) {
+                        want_ray = true;
+                        flags |= 1u;
+                        r1 = f4(V.w, V.dwa.x);
+                        ro = f4(V.no, __uint_as_float(pid));
+                        rd = f4(V.nd, __uint_as_float(V.delta ? 1u : 0u));
+                        rtp = f4(V.ntp, 0.f);
+                    }
+                }
+                float4* r = a.rec + 4 * ((size_t)b * cap + pid);
+                r[0] = make_float4(tp4.x, tp4.y, tp4.z, __uint_as_float(V.mat));
+                r[1] = r1;
+                r[2] = r2;
+                r[3] = make_float4(Le, Lj, __uint_as_float(V.light_mat), __uint_as_float(flags));
+                if (!V.cont || V.last) a.pend[pid] = b + 1u;
+            }
+        }
+        const uint32_t k = warp_append(&w.counts[2], want_shadow);
+        if (want_shadow) {
+            if (k < w.capacity) {
+                w.s_o[k] = so;
+                w.s_d[k] = sd;
+            } else {
+                atomicOr(src.s.status, ST_QUEUE);
+            }
+        }
+        const uint32_t q = warp_append(&w.counts[1], want_ray);
+        if (want_ray) {
+            if (q < w.capacity) {
+                w.q_o[out][q] = ro;
+                w.q_d[out][q] = rd;
+                w.q_tp[out][q] = rtp;
+            } else {
+                atomicOr(src.s.status, ST_QUEUE);
+            }
+        }
+    }
+}
+
+// Wavefront adjoint shadow stage: mark the vertex's NEE sample visible when unoccluded.
+__global__ void __launch_bounds__(256) k_shadow_adj(SingleSrc src, WfBuffers w, AdjBuffers a, uint32_t b) {
+    const uint32_t n = min(w.counts[2], w.capacity);
+    const size_t cap = w.capacity;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const float4 so = w.s_o[j], sd = w.s_d[j];
+        if (!trace_any(src.s, xyz(so), xyz(sd), so.w)) {
+            const uint32_t pid = __float_as_uint(sd.w);
+            float* fl = reinterpret_cast<float*>(a.rec + 4 * ((size_t)b * cap + pid) + 3) + 3;
+            *fl = __uint_as_float(__float_as_uint(*fl) | 2u);
+        }
+    }
+}
+
 // Prepare (Sec. 3.1): record this bounce's counts, promote the next count, reset the slots.
 __global__ void k_prepare(WfBuffers w, uint32_t b) {
     w.hist[b] += w.counts[0];
@@ -695,6 +788,80 @@ __global__ void __launch_bounds__(256) k_adjoint(DevScene s, DevCamera c, Render
     }
 }
 
+// Wavefront adjoint, reverse pass: one thread per path of the wave (consecutive paths per warp, so
+// record loads coalesce and neighbouring pixels share materials), walking the vertex records
+// backward with the recursion of k_adjoint.
+__global__ void __launch_bounds__(256) k_adjoint_reverse(DevScene s, RenderParams p, WfBuffers w, AdjBuffers a,
+                                                         uint32_t n, const float* __restrict__ grad,
+                                                         float* __restrict__ g_alb, float* __restrict__ g_em,
+                                                         int smem) {
+    extern __shared__ float acc[];
+    if (smem)
+        for (uint32_t k = threadIdx.x; k < 4 * s.n_mats; k += blockDim.x) acc[k] = 0.f;
+    __syncthreads();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    const float3 env = f3(s.env_r, s.env_g, s.env_b);
+    const float inv_spp = 1.0f / (float)p.spp;
+    const size_t cap = w.capacity;
+    for (uint32_t wb = warp * 32u; wb < n; wb += n_warps * 32u) {
+        const uint32_t pid = wb + lane_id();
+        int nv = 0;
+        float3 delta = f3(0.f, 0.f, 0.f), R = f3(0.f, 0.f, 0.f);
+        if (pid < n) {
+            const uint32_t pe = a.pend[pid];
+            nv = (int)(pe & 0xFFu);
+            if (pe & 0x100u) R = env;
+            const uint64_t path = p.path_begin + pid;
+            const uint32_t pixel = (uint32_t)(path / p.spp);
+            delta = f3(grad[3 * (size_t)pixel], grad[3 * (size_t)pixel + 1], grad[3 * (size_t)pixel + 2]) * inv_spp;
+        }
+        const int nmax = __reduce_max_sync(0xFFFFFFFFu, nv);
+        for (int b = nmax - 1; b >= 0; --b) {
+            uint32_t key_m = kNoKey, key_l = kNoKey;
+            float4 vm = make_float4(0.f, 0.f, 0.f, 0.f), vl = vm;
+            if (b < nv) {
+                const float4* r = a.rec + 4 * ((size_t)b * cap + pid);
+                const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3];
+                const uint32_t flags = __float_as_uint(r3.w);
+                const float3 dtp = delta * xyz(r0);
+                float3 ga = f3(0.f, 0.f, 0.f);
+                float ge = 0.f;
+                if (flags & 1u) {
+                    ga = dtp * R * r1.w;
+                    R = xyz(r1) * R;
+                }
+                if ((flags & 10u) == 10u) {            // cast and visible
+                    const float3 ng = xyz(r2);
+                    ga = ga + dtp * r2.w;
+                    key_l = __float_as_uint(r3.z);
+                    vl.w = dot(dtp, ng);
+                    R = R + ng * r3.y;
+                }
+                if (flags & 4u) {
+                    ge = dtp.x + dtp.y + dtp.z;
+                    R = R + f3(r3.x, r3.x, r3.x);
+                }
+                key_m = __float_as_uint(r0.w);
+                vm = make_float4(ga.x, ga.y, ga.z, ge);
+            }
+            warp_accumulate(acc, g_alb, g_em, smem != 0, key_m, vm);
+            warp_accumulate(acc, g_alb, g_em, smem != 0, key_l, vl);
+        }
+    }
+    if (smem) {
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < 4 * s.n_mats; k += blockDim.x) {
+            float v = acc[k];
+            if (v != 0.f) {
+                uint32_t m = k >> 2, ch = k & 3u;
+                if (ch < 3u) atomicAdd(&g_alb[3 * m + ch], v);
+                else atomicAdd(&g_em[m], v);
+            }
+        }
+    }
+}
+
 // ================================================================== utilities
 __global__ void k_set_materials(DevMat* mats, uint32_t n, const float* albedo, const float* emission) {
     uint32_t m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -850,6 +1017,29 @@ cudaError_t launch_adjoint(const Launch& l, const DevScene& s, const DevCamera& 
     return cudaGetLastError();
 }
 
+cudaError_t launch_shade_adj(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w,
+                             const AdjBuffers& a, int in, uint32_t bounce) {
+    SingleSrc src{s, DevCamera{}, p};
+    k_shade_adj<<<l.grid, l.block, 0, l.st>>>(src, w, a, in, bounce);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shadow_adj(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w,
+                              const AdjBuffers& a, uint32_t bounce) {
+    SingleSrc src{s, DevCamera{}, p};
+    k_shadow_adj<<<l.grid, l.block, 0, l.st>>>(src, w, a, bounce);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_reverse(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w,
+                                   const AdjBuffers& a, uint32_t n, const float* grad, float* g_albedo,
+                                   float* g_emission) {
+    size_t smem_bytes = sizeof(float) * 4 * (size_t)s.n_mats;
+    int smem = smem_bytes <= 32 * 1024 ? 1 : 0;
+    k_adjoint_reverse<<<l.grid, l.block, smem ? smem_bytes : 0, l.st>>>(s, p, w, a, n, grad, g_albedo, g_emission, smem);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_set_materials(cudaStream_t st, DevMat* mats, uint32_t n, const float* albedo, const float* emission) {
     if (n == 0) return cudaSuccess;
     k_set_materials<<<(n + 255) / 256, 256, 0, st>>>(mats, n, albedo, emission);
@@ -880,6 +1070,8 @@ int max_blocks_per_sm(int which, int block) {
         case K_SHADE_BATCH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<TableSrc, false>, block, 0); break;
         case K_SHADOW_BATCH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shadow<TableSrc, false>, block, 0); break;
         case K_ADJOINT: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adjoint<16>, block, 16 * 1024); break;
+        case K_SHADE_ADJ: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade_adj, block, 0); break;
+        case K_SHADOW_ADJ: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shadow_adj, block, 0); break;
         default: break;
     }
     return (e == cudaSuccess && nb > 0) ? nb : 1;

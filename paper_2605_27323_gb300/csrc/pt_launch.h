@@ -60,6 +60,16 @@ cudaError_t launch_adjoint(const Launch& l, const DevScene& s, const DevCamera& 
                            uint64_t n_paths, const float* grad_img, float* g_albedo, float* g_emission,
                            uint32_t max_depth_cap);
 
+// Wavefront adjoint: shading that writes per-vertex records, the shadow stage that marks visible
+// NEE samples, and the reverse pass over one wave's paths.
+cudaError_t launch_shade_adj(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w,
+                             const AdjBuffers& a, int in, uint32_t bounce);
+cudaError_t launch_shadow_adj(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w,
+                              const AdjBuffers& a, uint32_t bounce);
+cudaError_t launch_adjoint_reverse(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w,
+                                   const AdjBuffers& a, uint32_t n, const float* grad, float* g_albedo,
+                                   float* g_emission);
+
 // Utilities.
 cudaError_t launch_set_materials(cudaStream_t st, DevMat* mats, uint32_t n, const float* albedo, const float* emission);
 cudaError_t launch_trace_closest(const Launch& l, const DevScene& s, const float* rays, uint32_t n, float* t,
@@ -70,6 +80,6 @@ cudaError_t launch_debug_rng(const Launch& l, uint64_t seed, const uint32_t* px,
 // Occupancy helpers.
 int max_blocks_per_sm(int which, int block);   // which: 0 megakernel, 1 extend, 2 shade, 3 shadow, 4 adjoint
 enum { K_MEGA = 0, K_EXTEND = 1, K_SHADE = 2, K_SHADOW = 3, K_ADJOINT = 4, K_EXTEND_BATCH = 5, K_SHADE_BATCH = 6,
-       K_SHADOW_BATCH = 7 };
+       K_SHADOW_BATCH = 7, K_SHADE_ADJ = 8, K_SHADOW_ADJ = 9 };
 
 }  // namespace pt

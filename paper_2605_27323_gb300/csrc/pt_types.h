@@ -96,6 +96,16 @@ struct BatchSegment {
     unsigned long long flat_begin;     // prefix of px_count over the wave's segments
 };
 
+// Wavefront adjoint: one 64-byte record per path and vertex, bounce-major (rec[b * cap + pid]):
+//   r0 = throughput arriving at the vertex | material,  r1 = continuation weight w | dw/dalbedo,
+//   r2 = f G A of the NEE sample | d(f G A Le)/dalbedo,  r3 = (Le, Le_light, light material, flags);
+// flags: 1 continues, 2 NEE visible, 4 emission counted, 8 shadow ray cast.  pend[pid] = number of
+// vertices | (path ended in a miss) << 8.
+struct AdjBuffers {
+    float4* rec;
+    uint32_t* pend;
+};
+
 constexpr uint32_t kMaxSortKeys = 4096;
 constexpr uint32_t kMaxEvents = 64;     // event-log capacity per path (testing aid)
 

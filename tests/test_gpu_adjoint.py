@@ -152,6 +152,23 @@ def test_autograd_l2_loss_against_hidden_target(pt, torch):
     assert float(A.grad.abs().sum()) > 0
 
 
+@pytest.mark.parametrize("spp,depth,rr", [(4, 6, 0.0), (1, 12, 0.8)])
+def test_wavefront_and_megakernel_replays_agree(pt, torch, spp, depth, rr):
+    """The two replays of the adjoint (wavefront stages writing vertex records, and one thread per
+    path with thread-local records) compute the same gradients; only the order of the FP32 atomic
+    additions differs."""
+    sc = _c5_scene()
+    cam = dict(sc["camera"], width=160, height=90)
+    g = pt.Scene.from_dict(sc)
+    rng = np.random.default_rng(3)
+    delta = torch.from_numpy(rng.uniform(0.0, 1.0, size=(90, 160, 3)).astype(np.float32)).cuda()
+    ga_w, ge_w = g.backward(cam, spp, depth, 4, delta, rr_start=2, rr_fixed=rr, mode="wavefront")
+    ga_m, ge_m = g.backward(cam, spp, depth, 4, delta, rr_start=2, rr_fixed=rr, mode="megakernel")
+    assert torch.allclose(ga_w, ga_m, rtol=1e-4, atol=1e-6 * float(ga_m.abs().max()))
+    assert torch.allclose(ge_w, ge_m, rtol=1e-4, atol=1e-6 * float(ge_m.abs().max()))
+    assert float(ga_w.abs().sum()) > 0
+
+
 def test_backward_argument_errors(pt, torch):
     from paper_2605_27323_gb300 import capi
     sc = scenes.box_scene(width=8, height=8)
