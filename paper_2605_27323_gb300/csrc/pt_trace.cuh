@@ -79,26 +79,42 @@ __device__ __forceinline__ void load_node(const float4* __restrict__ nodes, uint
     refs = make_uint2(__float_as_uint(n3.x), __float_as_uint(n3.y));
 }
 
-// Closest hit along o + t d, t > 0 (the extend query).
+constexpr uint32_t kDone = 0x7FFFFFFFu;     // "traversal finished" (no internal node has this index)
+constexpr uint32_t kNoLeaf = 0u;            // no postponed leaf (0 is the root, never a leaf ref)
+
+// Closest hit along o + t d, t > 0 (the extend query).  "While-while" order (after Aila & Laine,
+// "Understanding the Efficiency of Ray Traversal on GPUs", 2009): each lane walks internal nodes,
+// setting aside the first leaf it reaches, until every lane of the warp holds a leaf; then the
+// lanes test their leaves together.  Keeping node steps and triangle steps in separate loops keeps
+// the warp on one code path; the hit found does not depend on the visiting order (ties on t go to
+// the lower triangle id).
 __device__ __forceinline__ Hit trace_closest(const DevScene& s, float3 o, float3 d) {
-    float3 id = ray_rcp(d);
+    const float3 id = ray_rcp(d);
     float tbest = __int_as_float(0x7f800000);
     uint32_t best = kMiss, bprim = kMiss;
     uint32_t stack_ref[kStack];
     float stack_t[kStack];
     int sp = 0;
-    uint32_t ref = 0;          // the root is always an internal node
+    uint32_t node = 0, leaf = kNoLeaf;
     uint32_t steps = 0;
-    while (true) {
-        if (!(ref & kLeafBit)) {
+    auto pop = [&]() -> uint32_t {
+        while (sp > 0) {
+            --sp;
+            if (stack_t[sp] <= tbest * 1.0000005f) return stack_ref[sp];
+        }
+        return kDone;
+    };
+    while (node != kDone || leaf != kNoLeaf) {
+        // walk internal nodes; set aside the first leaf reached
+        while (node != kDone && !(node & kLeafBit)) {
             float4 n0, n1, n2;
             uint2 r;
-            load_node(s.nodes, ref, n0, n1, n2, r);
+            load_node(s.nodes, node, n0, n1, n2, r);
             float t0, t1;
-            bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tbest, t0);
-            bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tbest, t1);
+            const bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tbest, t0);
+            const bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tbest, t1);
             if (h0 && h1) {
-                bool first0 = t0 <= t1;
+                const bool first0 = t0 <= t1;
                 if (sp < kStack) {
                     stack_ref[sp] = first0 ? r.y : r.x;
                     stack_t[sp] = first0 ? t1 : t0;
@@ -106,14 +122,26 @@ __device__ __forceinline__ Hit trace_closest(const DevScene& s, float3 o, float3
                 } else {
                     atomicOr(s.status, ST_TRAVERSAL);
                 }
-                ref = first0 ? r.x : r.y;
-                if (++steps < kMaxSteps) continue;
+                node = first0 ? r.x : r.y;
             } else if (h0 || h1) {
-                ref = h0 ? r.x : r.y;
-                if (++steps < kMaxSteps) continue;
+                node = h0 ? r.x : r.y;
+            } else {
+                node = pop();
             }
-        } else {
-            uint32_t first = (ref & 0x7FFFFFFFu) >> 3, cnt = (ref & 7u) + 1u;
+            if (node != kDone && (node & kLeafBit) && leaf == kNoLeaf) {
+                leaf = node;
+                node = pop();
+            }
+            if (++steps >= kMaxSteps) {
+                atomicOr(s.status, ST_TRAVERSAL);
+                node = kDone;
+                leaf = kNoLeaf;
+            }
+            if (!__any_sync(__activemask(), leaf == kNoLeaf)) break;
+        }
+        // test the set-aside leaf, then any leaves that follow directly
+        while (leaf != kNoLeaf) {
+            const uint32_t first = (leaf & 0x7FFFFFFFu) >> 3, cnt = (leaf & 7u) + 1u;
             for (uint32_t k = 0; k < cnt; ++k) {
                 float t;
                 uint32_t prim;
@@ -124,23 +152,12 @@ __device__ __forceinline__ Hit trace_closest(const DevScene& s, float3 o, float3
                     bprim = prim;
                 }
             }
-        }
-        if (steps >= kMaxSteps) {
-            atomicOr(s.status, ST_TRAVERSAL);
-            break;
-        }
-        // pop the next subtree whose entry is not beyond the best hit (ties kept)
-        bool found = false;
-        while (sp > 0) {
-            --sp;
-            if (stack_t[sp] <= tbest * 1.0000005f) {
-                ref = stack_ref[sp];
-                found = true;
-                break;
+            leaf = kNoLeaf;
+            if (node != kDone && (node & kLeafBit)) {
+                leaf = node;
+                node = pop();
             }
         }
-        if (!found) break;
-        ++steps;
     }
     Hit h;
     h.t = tbest;
@@ -148,46 +165,57 @@ __device__ __forceinline__ Hit trace_closest(const DevScene& s, float3 o, float3
     return h;
 }
 
-// Any hit with 0 < t < tmax (the shadow query).
+// Any hit with 0 < t < tmax (the shadow query), in the same while-while order; returns at the
+// first hit.
 __device__ __forceinline__ bool trace_any(const DevScene& s, float3 o, float3 d, float tmax) {
-    float3 id = ray_rcp(d);
+    const float3 id = ray_rcp(d);
     uint32_t stack_ref[kStack];
     int sp = 0;
-    uint32_t ref = 0;
+    uint32_t node = 0, leaf = kNoLeaf;
     uint32_t steps = 0;
-    while (true) {
-        if (!(ref & kLeafBit)) {
+    auto pop = [&]() -> uint32_t { return sp > 0 ? stack_ref[--sp] : kDone; };
+    while (node != kDone || leaf != kNoLeaf) {
+        while (node != kDone && !(node & kLeafBit)) {
             float4 n0, n1, n2;
             uint2 r;
-            load_node(s.nodes, ref, n0, n1, n2, r);
+            load_node(s.nodes, node, n0, n1, n2, r);
             float t0, t1;
-            bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tmax, t0);
-            bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tmax, t1);
+            const bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tmax, t0);
+            const bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tmax, t1);
             if (h0 && h1) {
                 if (sp < kStack) stack_ref[sp++] = r.y;
                 else atomicOr(s.status, ST_TRAVERSAL);
-                ref = r.x;
-                if (++steps < kMaxSteps) continue;
+                node = r.x;
             } else if (h0 || h1) {
-                ref = h0 ? r.x : r.y;
-                if (++steps < kMaxSteps) continue;
+                node = h0 ? r.x : r.y;
+            } else {
+                node = pop();
             }
-        } else {
-            uint32_t first = (ref & 0x7FFFFFFFu) >> 3, cnt = (ref & 7u) + 1u;
+            if (node != kDone && (node & kLeafBit) && leaf == kNoLeaf) {
+                leaf = node;
+                node = pop();
+            }
+            if (++steps >= kMaxSteps) {
+                atomicOr(s.status, ST_TRAVERSAL);
+                return false;
+            }
+            if (!__any_sync(__activemask(), leaf == kNoLeaf)) break;
+        }
+        while (leaf != kNoLeaf) {
+            const uint32_t first = (leaf & 0x7FFFFFFFu) >> 3, cnt = (leaf & 7u) + 1u;
             for (uint32_t k = 0; k < cnt; ++k) {
                 float t;
                 uint32_t prim;
                 if (tri_test(s.tris, first + k, o, d, t, prim) && t > 0.0f && t < tmax) return true;
             }
+            leaf = kNoLeaf;
+            if (node != kDone && (node & kLeafBit)) {
+                leaf = node;
+                node = pop();
+            }
         }
-        if (steps >= kMaxSteps) {
-            atomicOr(s.status, ST_TRAVERSAL);
-            return false;
-        }
-        if (sp == 0) return false;
-        ref = stack_ref[--sp];
-        ++steps;
     }
+    return false;
 }
 
 }  // namespace pt
