@@ -205,6 +205,7 @@ def run_gpu(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     wf_opts = dict(mode="wavefront", rr_start=3, sort=args.sort, profile=True)
     mk_opts = dict(mode="megakernel", rr_start=3, profile=True)
+    mk_static_opts = dict(mode="megakernel", rr_start=3, mk_static=True)
 
     def step(seed, timing):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -281,6 +282,16 @@ def run_gpu(args):
 
     wf_frame = float(np.mean(wf_ms))
     mk_frame = float(np.mean(mk_ms))
+    # the paper's megakernel layout (one thread per path over all paths), timed apart from the step
+    st_ms = []
+    for s_ in range(max(3, args.steps // 2)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.render(cam, spp, depth, 500 + s_, **mk_static_opts)
+        e1.record(stream)
+        e1.synchronize()
+        st_ms.append(e0.elapsed_time(e1))
+        flush.fill_(s_ & 0xFF)
     out = None
     if rank == 0:
         e2e = measure_e2e(g, cam, spp, depth, grad, args, wf_opts, mk_opts) if world == 1 else None
@@ -295,6 +306,9 @@ def run_gpu(args):
                           "rays_per_frame": float(np.mean(wf_rays))},
             "megakernel": {"mrays_s": float(np.sum(mk_rays)) / (np.sum(mk_ms) * 1e-3) / 1e6,
                            "ms_per_frame": mk_frame, "rays_per_frame": float(np.mean(mk_rays))},
+            "megakernel_static": {"ms_per_frame": float(np.mean(st_ms)),
+                                  "mrays_s": float(np.mean(mk_rays)) / (float(np.mean(st_ms)) * 1e-3) / 1e6,
+                                  "note": "one thread per path over all paths (the paper's layout); not in the step"},
             "wf_over_mk_speedup": mk_frame / wf_frame,
             "bwd_over_fwd": float(np.mean(bw_ms)) / min(wf_frame, mk_frame),
             "stage_ms_per_step": {k: v / args.steps for k, v in stage.items()},

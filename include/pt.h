@@ -72,7 +72,9 @@ enum { PT_SORT_NONE = 0, PT_SORT_TYPE = 1, PT_SORT_MATERIAL = 2 };
 enum {
     PT_FLAG_PROFILE = 1u,       /* time each stage with CUDA events on the launch stream; read the
                                    times with pt_get_stats after the stream completes */
-    PT_FLAG_NO_GRAPH = 2u       /* wavefront: launch the bounce loop directly, not as a CUDA graph */
+    PT_FLAG_NO_GRAPH = 2u,      /* batched wavefront: launch the bounce loop directly, not as a CUDA graph */
+    PT_FLAG_MK_STATIC = 4u      /* megakernel: one thread per path, launched over all paths (the paper's
+                                   layout) instead of the persistent kernel with path regeneration */
 };
 
 typedef struct {

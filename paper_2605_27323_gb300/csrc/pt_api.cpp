@@ -201,7 +201,8 @@ struct pt_scene {
     unsigned long long* hist() const { return reinterpret_cast<unsigned long long*>(counters.as<char>() + 256); }
     unsigned long long* rays() const { return hist() + 128; }
 
-    pt_status ensure_counters() { return counters.ensure(256 + 8 * 130); }
+    pt_status ensure_counters() { return counters.ensure(256 + 8 * 132); }
+    unsigned long long* next_path() const { return hist() + 130; }
 
     // One allocation carved into the wavefront arrays for `cap` paths per wave.
     pt_status ensure_wf(uint64_t cap) {
@@ -854,10 +855,16 @@ pt_status pt_render(pt_scene* sc, const pt_camera* cam, uint32_t spp, uint32_t m
             PT_TRY(sc->pathL.ensure(n_paths * 12));
             outL = sc->pathL.as<float>();
         }
-        pt::Launch l = launch_for(sc, pt::K_MEGA, o.block_size, 128, st, n_paths);
         size_t ev = 0;
         PT_TRY(sc->ev_begin(ST_MEGA, st, ev));
-        PT_CUDA(pt::launch_megakernel(l, sc->view(), dc, p, n_paths, outL, img, o.d_path_sig, sc->rays()));
+        if (o.flags & PT_FLAG_MK_STATIC) {
+            pt::Launch l = launch_for(sc, pt::K_MEGA, o.block_size, 128, st, n_paths);
+            PT_CUDA(pt::launch_megakernel(l, sc->view(), dc, p, n_paths, outL, img, o.d_path_sig, sc->rays()));
+        } else {
+            pt::Launch l = launch_for(sc, pt::K_MEGA_REGEN, o.block_size, 128, st, n_paths);
+            PT_CUDA(pt::launch_megakernel_regen(l, sc->view(), dc, p, n_paths, outL, img, o.d_path_sig, sc->rays(),
+                                                sc->next_path()));
+        }
         PT_TRY(sc->ev_end(ev, st));
         sc->launches += 1;
         if (outL) {

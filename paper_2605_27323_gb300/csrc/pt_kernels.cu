@@ -76,7 +76,7 @@ __device__ __forceinline__ float3 mk_path(const DevScene& s, const DevCamera& c,
     bool prev_delta = true;
     for (uint32_t b = 0; b < p.max_depth; ++b) {
         ++n_ext;
-        Hit h = trace_closest(s, o, d);                        // step 2
+        Hit h = trace_closest<true>(s, o, d);                  // step 2
         if (h.tri == kMiss) {
             L = add_rn(L, mul_rn(tp, env));
             rec.ev(b, 0, kMiss, __int_as_float(0x7f800000), tp.x);
@@ -90,7 +90,7 @@ __device__ __forceinline__ float3 mk_path(const DevScene& s, const DevCamera& c,
             uint32_t vis = 0;
             if (V.cast) {
                 ++n_shd;
-                vis = trace_any(s, V.s_o, V.s_d, V.s_tmax) ? 0u : 1u;
+                vis = trace_any<true>(s, V.s_o, V.s_d, V.s_tmax) ? 0u : 1u;
                 if (vis) L = add_rn(L, V.contrib);
             }
             rec.ev(b, 1, (V.light_j << 2) | ((uint32_t)V.cast << 1) | vis, V.nee_cx, V.nee_cl);
@@ -132,6 +132,109 @@ __global__ void __launch_bounds__(256) k_megakernel(DevScene s, DevCamera c, Ren
             img[3 * (size_t)pixel] = L.x;
             img[3 * (size_t)pixel + 1] = L.y;
             img[3 * (size_t)pixel + 2] = L.z;
+        }
+    }
+    warp_add_u64(rays, n_ext);
+    warp_add_u64(rays + 1, n_shd);
+}
+
+// Persistent megakernel with path regeneration.  Each thread still traces one path at a time from
+// its camera ray to termination, one bounce per loop iteration; a lane whose path ended claims the
+// next path id (warp-aggregated atomic on a device counter) instead of idling until the longest
+// path of its warp finishes.  The per-path arithmetic is that of mk_path, so images are identical.
+template <bool SIG>
+__global__ void __launch_bounds__(256) k_megakernel_regen(DevScene s, DevCamera c, RenderParams p, uint64_t n_paths,
+                                                          float* __restrict__ out_L, float* __restrict__ img,
+                                                          uint32_t* __restrict__ sig,
+                                                          unsigned long long* __restrict__ rays,
+                                                          unsigned long long* __restrict__ next_path) {
+    unsigned long long n_ext = 0, n_shd = 0;
+    const float3 env = f3(s.env_r, s.env_g, s.env_b);
+    bool active = false, exhausted = false;
+    uint64_t i = 0;
+    uint32_t pixel = 0, key = 0, b = 0, sg = 0;
+    float3 o = f3(0.f, 0.f, 0.f), d = o, tp = o, L = o;
+    bool prev_delta = true;
+    while (true) {
+        const bool want = !active && !exhausted;
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, want);
+        if (m) {
+            const uint32_t leader = __ffs(m) - 1u;
+            unsigned long long first = 0;
+            if (lane_id() == leader) first = atomicAdd(next_path, (unsigned long long)__popc(m));
+            first = __shfl_sync(0xFFFFFFFFu, first, leader);
+            if (want) {
+                i = first + (uint64_t)__popc(m & ((1u << lane_id()) - 1u));
+                if (i < n_paths) {
+                    const uint64_t path = p.path_begin + i;
+                    pixel = (uint32_t)(path / p.spp);
+                    const uint32_t sample = (uint32_t)(path - (uint64_t)pixel * p.spp);
+                    key = path_key(p.seed, pixel, sample);
+                    camera_ray(c, pixel, key, o, d);
+                    tp = f3(1.f, 1.f, 1.f);
+                    L = f3(0.f, 0.f, 0.f);
+                    prev_delta = true;
+                    b = 0;
+                    sg = 0;
+                    active = true;
+                } else {
+                    exhausted = true;
+                }
+            }
+        }
+        if (!__any_sync(0xFFFFFFFFu, active)) break;
+        if (active) {
+            bool end = false;
+            ++n_ext;
+            Hit h = trace_closest<true>(s, o, d);
+            if (h.tri == kMiss) {
+                L = add_rn(L, mul_rn(tp, env));
+                if (SIG) sg ^= sig_event(b, 0, kMiss);
+                end = true;
+            } else {
+                Vertex V = shade_vertex(s, p, key, b, o, d, tp, prev_delta, h.t, h.tri);
+                if (SIG) sg ^= sig_event(b, 0, V.prim);
+                if (V.emit_counted) L = add_rn(L, V.emit);
+                if (V.last) {
+                    end = true;
+                } else {
+                    if (V.nee) {
+                        uint32_t vis = 0;
+                        if (V.cast) {
+                            ++n_shd;
+                            vis = trace_any<true>(s, V.s_o, V.s_d, V.s_tmax) ? 0u : 1u;
+                            if (vis) L = add_rn(L, V.contrib);
+                        }
+                        if (SIG) sg ^= sig_event(b, 1, (V.light_j << 2) | ((uint32_t)V.cast << 1) | vis);
+                    }
+                    if (SIG) {
+                        sg ^= sig_event(b, 2, V.bsdf_code);
+                        if (V.rr >= 0) sg ^= sig_event(b, 3, (uint32_t)V.rr);
+                    }
+                    if (V.cont) {
+                        o = V.no;
+                        d = V.nd;
+                        tp = V.ntp;
+                        prev_delta = V.delta;
+                        ++b;
+                    } else {
+                        end = true;
+                    }
+                }
+            }
+            if (end) {
+                if (out_L) {
+                    out_L[3 * i] = L.x;
+                    out_L[3 * i + 1] = L.y;
+                    out_L[3 * i + 2] = L.z;
+                } else {
+                    img[3 * (size_t)pixel] = L.x;
+                    img[3 * (size_t)pixel + 1] = L.y;
+                    img[3 * (size_t)pixel + 2] = L.z;
+                }
+                if (SIG) sig[p.path_begin + i] = sg;
+                active = false;
+            }
         }
     }
     warp_add_u64(rays, n_ext);
@@ -256,7 +359,7 @@ __global__ void __launch_bounds__(256) k_extend(Src src, WfBuffers w, int in) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         float4 o4 = qo[j], d4 = qd[j];
-        Hit h = trace_closest(src.scene(src.sid_of(base, __float_as_uint(o4.w))), xyz(o4), xyz(d4));
+        Hit h = trace_closest<false>(src.scene(src.sid_of(base, __float_as_uint(o4.w))), xyz(o4), xyz(d4));
         hit[j] = make_float2(h.t, __uint_as_float(h.tri));
     }
 }
@@ -425,7 +528,7 @@ __global__ void __launch_bounds__(256) k_shadow(Src src, WfBuffers w, uint32_t b
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         const float4 so = w.s_o[j], sd = w.s_d[j];
         const uint32_t pid = __float_as_uint(sd.w);
-        const bool occ = trace_any(src.scene(src.sid_of(base, pid)), xyz(so), xyz(sd), so.w);
+        const bool occ = trace_any<false>(src.scene(src.sid_of(base, pid)), xyz(so), xyz(sd), so.w);
         if (!occ) {
             const float4 sc = w.s_c[j];
             float3 L = add_rn(xyz(w.L[pid]), xyz(sc));
@@ -523,7 +626,7 @@ __global__ void __launch_bounds__(256) k_shadow_adj(SingleSrc src, WfBuffers w, 
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         const float4 so = w.s_o[j], sd = w.s_d[j];
-        if (!trace_any(src.s, xyz(so), xyz(sd), so.w)) {
+        if (!trace_any<false>(src.s, xyz(so), xyz(sd), so.w)) {
             const uint32_t pid = __float_as_uint(sd.w);
             float* fl = reinterpret_cast<float*>(a.rec + 4 * ((size_t)b * cap + pid) + 3) + 3;
             *fl = __uint_as_float(__float_as_uint(*fl) | 2u);
@@ -709,7 +812,7 @@ __global__ void __launch_bounds__(256) k_adjoint(DevScene s, DevCamera c, Render
             float3 tp = f3(1.f, 1.f, 1.f);
             bool prev_delta = true;
             for (uint32_t b = 0; b < p.max_depth && b < (uint32_t)MAXD; ++b) {
-                Hit h = trace_closest(s, o, d);
+                Hit h = trace_closest<true>(s, o, d);
                 if (h.tri == kMiss) {
                     end_miss = true;
                     break;
@@ -727,7 +830,7 @@ __global__ void __launch_bounds__(256) k_adjoint(DevScene s, DevCamera c, Render
                 r.dwa = r.nee_g;
                 r.Lj = 0.f;
                 if (V.last) break;
-                if (V.nee && V.cast && !trace_any(s, V.s_o, V.s_d, V.s_tmax)) {
+                if (V.nee && V.cast && !trace_any<true>(s, V.s_o, V.s_d, V.s_tmax)) {
                     r.flags |= 2u;
                     r.nee_g = V.nee_g;
                     r.nee_dfa = V.nee_dfa;
@@ -879,7 +982,7 @@ __global__ void __launch_bounds__(256) k_trace_closest(DevScene s, const float* 
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float* r = rays + 8 * (size_t)i;
-        Hit h = trace_closest(s, f3(r[0], r[1], r[2]), f3(r[4], r[5], r[6]));
+        Hit h = trace_closest<false>(s, f3(r[0], r[1], r[2]), f3(r[4], r[5], r[6]));
         t[i] = h.t;
         prim[i] = h.tri == kMiss ? -1 : (int32_t)__float_as_uint(__ldg(s.tris + 3 * (size_t)h.tri).w);
     }
@@ -892,6 +995,14 @@ __global__ void k_debug_rng(uint64_t seed, const uint32_t* px, const uint32_t* s
 }
 
 // ================================================================== launchers
+cudaError_t launch_megakernel_regen(const Launch& l, const DevScene& s, const DevCamera& c, const RenderParams& p,
+                                    uint64_t n_paths, float* out_L, float* img, uint32_t* sig, unsigned long long* rays,
+                                    unsigned long long* next_path) {
+    if (sig) k_megakernel_regen<true><<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays, next_path);
+    else k_megakernel_regen<false><<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays, next_path);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_megakernel(const Launch& l, const DevScene& s, const DevCamera& c, const RenderParams& p,
                               uint64_t n_paths, float* out_L, float* img, uint32_t* sig, unsigned long long* rays) {
     if (sig) k_megakernel<true><<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays);
@@ -1063,6 +1174,7 @@ int max_blocks_per_sm(int which, int block) {
     cudaError_t e = cudaErrorInvalidValue;
     switch (which) {
         case K_MEGA: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_megakernel<false>, block, 0); break;
+        case K_MEGA_REGEN: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_megakernel_regen<false>, block, 0); break;
         case K_EXTEND: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend<SingleSrc>, block, 0); break;
         case K_SHADE: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<SingleSrc, false>, block, 0); break;
         case K_SHADOW: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shadow<SingleSrc, false>, block, 0); break;

@@ -20,6 +20,11 @@ cudaError_t launch_megakernel(const Launch& l, const DevScene& s, const DevCamer
                               uint64_t n_paths, float* out_L, float* img, uint32_t* sig,
                               unsigned long long* rays);
 
+// Persistent megakernel with path regeneration (next_path: device counter zeroed by the caller).
+cudaError_t launch_megakernel_regen(const Launch& l, const DevScene& s, const DevCamera& c, const RenderParams& p,
+                                    uint64_t n_paths, float* out_L, float* img, uint32_t* sig, unsigned long long* rays,
+                                    unsigned long long* next_path);
+
 // Event logs of selected paths (testing aid).
 cudaError_t launch_debug_paths(cudaStream_t st, const DevScene& s, const DevCamera& c, const RenderParams& p,
                                const unsigned long long* ids, uint32_t n, uint32_t* ev_u, float* ev_f, uint32_t* n_ev,
@@ -80,6 +85,7 @@ cudaError_t launch_debug_rng(const Launch& l, uint64_t seed, const uint32_t* px,
 // Occupancy helpers.
 int max_blocks_per_sm(int which, int block);   // which: 0 megakernel, 1 extend, 2 shade, 3 shadow, 4 adjoint
 enum { K_MEGA = 0, K_EXTEND = 1, K_SHADE = 2, K_SHADOW = 3, K_ADJOINT = 4, K_EXTEND_BATCH = 5, K_SHADE_BATCH = 6,
-       K_SHADOW_BATCH = 7, K_SHADE_ADJ = 8, K_SHADOW_ADJ = 9 };
+       K_SHADOW_BATCH = 7, K_SHADE_ADJ = 8, K_SHADOW_ADJ = 9,
+       K_MEGA_REGEN = 10 };
 
 }  // namespace pt

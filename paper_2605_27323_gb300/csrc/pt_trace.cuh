@@ -79,16 +79,127 @@ __device__ __forceinline__ void load_node(const float4* __restrict__ nodes, uint
     refs = make_uint2(__float_as_uint(n3.x), __float_as_uint(n3.y));
 }
 
+// Closest hit, plain order: one loop that takes a node step or a leaf step per iteration.  The
+// wavefront's traversal kernels use it (measured faster there than the while-while order).
+__device__ __forceinline__ Hit trace_closest_plain(const DevScene& s, float3 o, float3 d) {
+    float3 id = ray_rcp(d);
+    float tbest = __int_as_float(0x7f800000);
+    uint32_t best = kMiss, bprim = kMiss;
+    uint32_t stack_ref[kStack];
+    float stack_t[kStack];
+    int sp = 0;
+    uint32_t ref = 0;          // the root is always an internal node
+    uint32_t steps = 0;
+    while (true) {
+        if (!(ref & kLeafBit)) {
+            float4 n0, n1, n2;
+            uint2 r;
+            load_node(s.nodes, ref, n0, n1, n2, r);
+            float t0, t1;
+            bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tbest, t0);
+            bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tbest, t1);
+            if (h0 && h1) {
+                bool first0 = t0 <= t1;
+                if (sp < kStack) {
+                    stack_ref[sp] = first0 ? r.y : r.x;
+                    stack_t[sp] = first0 ? t1 : t0;
+                    ++sp;
+                } else {
+                    atomicOr(s.status, ST_TRAVERSAL);
+                }
+                ref = first0 ? r.x : r.y;
+                if (++steps < kMaxSteps) continue;
+            } else if (h0 || h1) {
+                ref = h0 ? r.x : r.y;
+                if (++steps < kMaxSteps) continue;
+            }
+        } else {
+            uint32_t first = (ref & 0x7FFFFFFFu) >> 3, cnt = (ref & 7u) + 1u;
+            for (uint32_t k = 0; k < cnt; ++k) {
+                float t;
+                uint32_t prim;
+                if (tri_test(s.tris, first + k, o, d, t, prim) && t > 0.0f &&
+                    (t < tbest || (t == tbest && prim < bprim))) {
+                    tbest = t;
+                    best = first + k;
+                    bprim = prim;
+                }
+            }
+        }
+        if (steps >= kMaxSteps) {
+            atomicOr(s.status, ST_TRAVERSAL);
+            break;
+        }
+        bool found = false;        // pop the next subtree whose entry is not beyond the best hit
+        while (sp > 0) {
+            --sp;
+            if (stack_t[sp] <= tbest * 1.0000005f) {
+                ref = stack_ref[sp];
+                found = true;
+                break;
+            }
+        }
+        if (!found) break;
+        ++steps;
+    }
+    Hit h;
+    h.t = tbest;
+    h.tri = best;
+    return h;
+}
+
+// Any hit with 0 < t < tmax, plain order.
+__device__ __forceinline__ bool trace_any_plain(const DevScene& s, float3 o, float3 d, float tmax) {
+    float3 id = ray_rcp(d);
+    uint32_t stack_ref[kStack];
+    int sp = 0;
+    uint32_t ref = 0;
+    uint32_t steps = 0;
+    while (true) {
+        if (!(ref & kLeafBit)) {
+            float4 n0, n1, n2;
+            uint2 r;
+            load_node(s.nodes, ref, n0, n1, n2, r);
+            float t0, t1;
+            bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tmax, t0);
+            bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tmax, t1);
+            if (h0 && h1) {
+                if (sp < kStack) stack_ref[sp++] = r.y;
+                else atomicOr(s.status, ST_TRAVERSAL);
+                ref = r.x;
+                if (++steps < kMaxSteps) continue;
+            } else if (h0 || h1) {
+                ref = h0 ? r.x : r.y;
+                if (++steps < kMaxSteps) continue;
+            }
+        } else {
+            uint32_t first = (ref & 0x7FFFFFFFu) >> 3, cnt = (ref & 7u) + 1u;
+            for (uint32_t k = 0; k < cnt; ++k) {
+                float t;
+                uint32_t prim;
+                if (tri_test(s.tris, first + k, o, d, t, prim) && t > 0.0f && t < tmax) return true;
+            }
+        }
+        if (steps >= kMaxSteps) {
+            atomicOr(s.status, ST_TRAVERSAL);
+            return false;
+        }
+        if (sp == 0) return false;
+        ref = stack_ref[--sp];
+        ++steps;
+    }
+}
+
 constexpr uint32_t kDone = 0x7FFFFFFFu;     // "traversal finished" (no internal node has this index)
 constexpr uint32_t kNoLeaf = 0u;            // no postponed leaf (0 is the root, never a leaf ref)
 
-// Closest hit along o + t d, t > 0 (the extend query).  "While-while" order (after Aila & Laine,
+// Closest hit along o + t d, t > 0.  "While-while" order (after Aila & Laine,
 // "Understanding the Efficiency of Ray Traversal on GPUs", 2009): each lane walks internal nodes,
 // setting aside the first leaf it reaches, until every lane of the warp holds a leaf; then the
 // lanes test their leaves together.  Keeping node steps and triangle steps in separate loops keeps
 // the warp on one code path; the hit found does not depend on the visiting order (ties on t go to
 // the lower triangle id).
-__device__ __forceinline__ Hit trace_closest(const DevScene& s, float3 o, float3 d) {
+__device__ __forceinline__ Hit trace_closest_ww(const DevScene& s, float3 o, float3 d) {
     const float3 id = ray_rcp(d);
     float tbest = __int_as_float(0x7f800000);
     uint32_t best = kMiss, bprim = kMiss;
@@ -165,9 +276,8 @@ __device__ __forceinline__ Hit trace_closest(const DevScene& s, float3 o, float3
     return h;
 }
 
-// Any hit with 0 < t < tmax (the shadow query), in the same while-while order; returns at the
-// first hit.
-__device__ __forceinline__ bool trace_any(const DevScene& s, float3 o, float3 d, float tmax) {
+// Any hit with 0 < t < tmax, in the same while-while order; returns at the first hit.
+__device__ __forceinline__ bool trace_any_ww(const DevScene& s, float3 o, float3 d, float tmax) {
     const float3 id = ray_rcp(d);
     uint32_t stack_ref[kStack];
     int sp = 0;
@@ -216,6 +326,17 @@ __device__ __forceinline__ bool trace_any(const DevScene& s, float3 o, float3 d,
         }
     }
     return false;
+}
+
+// The extend and shadow queries.  WW selects the while-while order (used by the one-thread-per-path
+// kernels, where it also lowers register pressure) or the plain loop (used by the wavefront stages).
+template <bool WW>
+__device__ __forceinline__ Hit trace_closest(const DevScene& s, float3 o, float3 d) {
+    return WW ? trace_closest_ww(s, o, d) : trace_closest_plain(s, o, d);
+}
+template <bool WW>
+__device__ __forceinline__ bool trace_any(const DevScene& s, float3 o, float3 d, float tmax) {
+    return WW ? trace_any_ww(s, o, d, tmax) : trace_any_plain(s, o, d, tmax);
 }
 
 }  // namespace pt

@@ -38,14 +38,15 @@ def make_camera(cam: dict) -> capi.Camera:
 
 
 def make_opts(mode="wavefront", rr_start=3, rr_fixed=0.0, sort="none", block_size=0, queue_capacity=0,
-              profile=False, sig=None, graph=True) -> capi.RenderOpts:
+              profile=False, sig=None, graph=True, mk_static=False) -> capi.RenderOpts:
     o = capi.RenderOpts()
     o.mode = capi.MODE[mode] if isinstance(mode, str) else int(mode)
     o.rr_start = int(rr_start)
     o.rr_fixed = float(rr_fixed)
     o.sort_mode = capi.SORT[sort] if isinstance(sort, str) else int(sort)
     o.block_size = int(block_size)
-    o.flags = (capi.FLAG_PROFILE if profile else 0) | (0 if graph else capi.FLAG_NO_GRAPH)
+    o.flags = ((capi.FLAG_PROFILE if profile else 0) | (0 if graph else capi.FLAG_NO_GRAPH)
+               | (capi.FLAG_MK_STATIC if mk_static else 0))
     o.queue_capacity = int(queue_capacity)
     o.d_path_sig = sig.data_ptr() if sig is not None else None
     return o

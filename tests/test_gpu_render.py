@@ -97,11 +97,14 @@ def test_closest_hit_matches_brute_force(pt, torch, which):
 
 
 def _render_both_modes(pt, g, cam, spp, depth, seed, **kw):
+    """Megakernel (persistent, path regeneration), megakernel (one thread per path) and wavefront."""
     out = {}
-    for mode in ("megakernel", "wavefront"):
-        r = g.render(cam, spp, depth, seed, path_L=True, sig=True, mode=mode, **kw)
+    for mode, extra in (("megakernel", {}), ("wavefront", {}), ("megakernel_static", {"mk_static": True})):
+        r = g.render(cam, spp, depth, seed, path_L=True, sig=True, mode=mode.split("_")[0], **extra, **kw)
         out[mode] = {k: v.cpu().numpy() for k, v in r.items()}
         out[mode]["stats"] = g.stats()
+    for k in ("img", "path_L", "sig"):
+        assert np.array_equal(out["megakernel_static"][k], out["megakernel"][k])
     return out
 
 
@@ -174,7 +177,8 @@ def test_wavefront_sort_and_waves_are_bitwise_identical(pt, torch):
     ref = g.render(cam, 4, 8, 3, mode="wavefront").cpu().numpy()
     for kw in ({"sort": "type"}, {"sort": "material"}, {"queue_capacity": 4 * 1000},
                {"queue_capacity": 4 * 777, "sort": "material", "block_size": 128}, {"mode": "megakernel"},
-               {"mode": "megakernel", "block_size": 64}):
+               {"mode": "megakernel", "block_size": 64}, {"mode": "megakernel", "mk_static": True},
+               {"mode": "megakernel", "mk_static": True, "block_size": 96}):
         kw.setdefault("mode", "wavefront")
         img = g.render(cam, 4, 8, 3, **kw).cpu().numpy()
         assert np.array_equal(img, ref), kw
