@@ -502,8 +502,30 @@ pt_status batch_render(pt_scene* const* scenes, const pt_camera* cams, const uin
         uint32_t seg0, nseg;
     };
     std::vector<Wave> waves;
-    for (uint64_t w0 = 0; w0 < total; w0 += cap) {
-        const uint64_t w1 = std::min(total, w0 + cap);
+    // waves: a scene larger than half a wave gets waves of its own (one large BVH in L2 at a time);
+    // smaller scenes are packed together up to the capacity
+    std::vector<std::pair<uint64_t, uint64_t>> ranges;
+    {
+        uint64_t cur0 = 0, cur1 = 0;
+        for (uint32_t s = 0; s < n; ++s) {
+            const uint64_t a0 = off[s], a1 = off[s + 1];
+            if (a1 - a0 > cap / 2) {
+                if (cur1 > cur0) ranges.push_back({cur0, cur1});
+                const uint64_t k = (a1 - a0 + cap - 1) / cap, per = (a1 - a0 + k - 1) / k;
+                for (uint64_t x = a0; x < a1; x += per) ranges.push_back({x, std::min(a1, x + per)});
+                cur0 = cur1 = a1;
+            } else {
+                if (a1 - cur0 > cap) {
+                    ranges.push_back({cur0, cur1});
+                    cur0 = cur1;
+                }
+                cur1 = a1;
+            }
+        }
+        if (cur1 > cur0) ranges.push_back({cur0, cur1});
+    }
+    for (const auto& rg : ranges) {
+        const uint64_t w0 = rg.first, w1 = rg.second;
         Wave wv{w0, w1, 0, (uint32_t)segs.size(), 0};
         for (uint32_t s = 0; s < n; ++s) {
             if (off[s + 1] <= w0 || off[s] >= w1 || off[s + 1] == off[s]) continue;

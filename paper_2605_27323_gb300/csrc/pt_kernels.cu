@@ -285,6 +285,12 @@ struct SingleSrc {
     __device__ __forceinline__ DevScene scene(uint32_t) const { return s; }
     __device__ __forceinline__ DevCamera camera(uint32_t) const { return c; }
     __device__ __forceinline__ RenderParams params(uint32_t) const { return p; }
+    // scene id carried in the queue records: none needed for one scene
+    __device__ __forceinline__ uint32_t ray_tag(uint32_t, uint32_t flags) const { return flags; }
+    __device__ __forceinline__ uint32_t sid_from_ray(float, uint64_t, uint32_t) const { return 0; }
+    __device__ __forceinline__ uint32_t shadow_tag(uint32_t light_j, uint32_t) const { return light_j; }
+    __device__ __forceinline__ uint32_t sid_from_shadow(float, uint64_t, uint32_t) const { return 0; }
+    __device__ __forceinline__ PathLoc locate_in(uint64_t base, uint32_t pid, uint32_t) const { return locate(base, pid); }
 };
 
 struct TableSrc {
@@ -319,6 +325,25 @@ struct TableSrc {
         q.seed = __ldg(t.seed);
         return q;
     }
+    // the scene id rides in the records' spare bits: ray d.w = flags | sid << 8; shadow c.w = sid
+    __device__ __forceinline__ uint32_t ray_tag(uint32_t sid, uint32_t flags) const { return flags | (sid << 8); }
+    __device__ __forceinline__ uint32_t sid_from_ray(float dw, uint64_t, uint32_t) const {
+        return __float_as_uint(dw) >> 8;
+    }
+    __device__ __forceinline__ uint32_t shadow_tag(uint32_t, uint32_t sid) const { return sid; }
+    __device__ __forceinline__ uint32_t sid_from_shadow(float cw, uint64_t, uint32_t) const {
+        return __float_as_uint(cw);
+    }
+    __device__ __forceinline__ PathLoc locate_in(uint64_t base, uint32_t pid, uint32_t sid) const {
+        PathLoc l;
+        l.sid = sid;
+        l.path = base + pid;
+        const uint64_t local = l.path - __ldg(t.off + sid);
+        const uint32_t spp = __ldg(t.spp + sid);
+        l.pixel = (uint32_t)(local / spp);
+        l.sample = (uint32_t)(local - (uint64_t)l.pixel * spp);
+        return l;
+    }
 };
 
 // Ray generation: one queue record per path of the wave, radiance zeroed, active count = n.  The
@@ -335,7 +360,7 @@ __global__ void __launch_bounds__(256) k_raygen(Src src, uint64_t base, uint32_t
         float3 o, d;
         camera_ray(src.camera(l.sid), l.pixel, key, o, d);
         w.q_o[0][i] = f4(o, __uint_as_float(i));
-        w.q_d[0][i] = f4(d, __uint_as_float(1u));            // previous vertex "delta": the camera
+        w.q_d[0][i] = f4(d, __uint_as_float(src.ray_tag(l.sid, 1u)));   // previous vertex "delta": the camera
         w.q_tp[0][i] = make_float4(1.f, 1.f, 1.f, 0.f);
         w.L[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (w.sig) w.sig[l.path] = 0u;
@@ -359,7 +384,7 @@ __global__ void __launch_bounds__(256) k_extend(Src src, WfBuffers w, int in) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         float4 o4 = qo[j], d4 = qd[j];
-        Hit h = trace_closest<false>(src.scene(src.sid_of(base, __float_as_uint(o4.w))), xyz(o4), xyz(d4));
+        Hit h = trace_closest<false>(src.scene(src.sid_from_ray(d4.w, base, __float_as_uint(o4.w))), xyz(o4), xyz(d4));
         hit[j] = make_float2(h.t, __uint_as_float(h.tri));
     }
 }
@@ -377,7 +402,7 @@ __global__ void __launch_bounds__(256) k_sort_keys(Src src, WfBuffers w, int in,
         uint32_t tri = __float_as_uint(w.hit[j].y);
         uint32_t key = n_keys - 1u;                          // misses last
         if (tri != kMiss) {
-            const DevScene s = src.scene(src.sid_of(base, __float_as_uint(w.q_o[in][j].w)));
+            const DevScene s = src.scene(src.sid_from_ray(w.q_d[in][j].w, base, __float_as_uint(w.q_o[in][j].w)));
             uint32_t m = __float_as_uint(__ldg(s.tris + 3 * (size_t)tri + 1).w);
             key = mode == 1u ? __float_as_uint(__ldg(reinterpret_cast<const float*>(s.mats + m))) : m;
             key = min(key, n_keys - 2u);
@@ -451,7 +476,7 @@ __global__ void __launch_bounds__(256) k_shade(Src src, WfBuffers w, int in, uin
             const float4 o4 = w.q_o[in][slot], d4 = w.q_d[in][slot], tp4 = w.q_tp[in][slot];
             const float2 hh = w.hit[slot];
             const uint32_t pid = __float_as_uint(o4.w);
-            const PathLoc l = src.locate(base, pid);
+            const PathLoc l = src.locate_in(base, pid, src.sid_from_ray(d4.w, base, pid));
             const DevScene s = src.scene(l.sid);
             const float3 tp = xyz(tp4);
             const uint32_t tri = __float_as_uint(hh.y);
@@ -476,7 +501,7 @@ __global__ void __launch_bounds__(256) k_shade(Src src, WfBuffers w, int in, uin
                             want_shadow = true;
                             so = f4(V.s_o, V.s_tmax);
                             sd = f4(V.s_d, __uint_as_float(pid));
-                            sc = f4(V.contrib, __uint_as_float(V.light_j));
+                            sc = f4(V.contrib, __uint_as_float(src.shadow_tag(V.light_j, l.sid)));
                         } else if (SIG) {
                             sg ^= sig_event(b, 1, V.light_j << 2);
                         }
@@ -488,7 +513,7 @@ __global__ void __launch_bounds__(256) k_shade(Src src, WfBuffers w, int in, uin
                     if (V.cont) {
                         want_ray = true;
                         ro = f4(V.no, __uint_as_float(pid));
-                        rd = f4(V.nd, __uint_as_float(V.delta ? 1u : 0u));
+                        rd = f4(V.nd, __uint_as_float(src.ray_tag(l.sid, V.delta ? 1u : 0u)));
                         rtp = f4(V.ntp, 0.f);
                     }
                 }
@@ -526,16 +551,15 @@ __global__ void __launch_bounds__(256) k_shadow(Src src, WfBuffers w, uint32_t b
     const uint64_t base = src.base();
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-        const float4 so = w.s_o[j], sd = w.s_d[j];
+        const float4 so = w.s_o[j], sd = w.s_d[j], sc = w.s_c[j];
         const uint32_t pid = __float_as_uint(sd.w);
-        const bool occ = trace_any<false>(src.scene(src.sid_of(base, pid)), xyz(so), xyz(sd), so.w);
+        const bool occ = trace_any<false>(src.scene(src.sid_from_shadow(sc.w, base, pid)), xyz(so), xyz(sd), so.w);
         if (!occ) {
-            const float4 sc = w.s_c[j];
             float3 L = add_rn(xyz(w.L[pid]), xyz(sc));
             w.L[pid] = f4(L, 0.f);
         }
         if (SIG) {
-            const uint32_t lj = __float_as_uint(w.s_c[j].w);
+            const uint32_t lj = __float_as_uint(sc.w);
             w.sig[base + pid] ^= sig_event(b, 1, (lj << 2) | 2u | (occ ? 0u : 1u));
         }
     }
