@@ -250,6 +250,28 @@ def test_spheres_1080p_sampled_paths(pt, torch):
     assert float(wf["img"].mean()) > 0
 
 
+def test_large_terrain_scene_4k_sampled_paths(pt, torch):
+    """~10M triangles (2048^2 fBm heightfield + 5000 icospheres), 3840x2160, 4 spp, depth 8, the
+    wavefront queues sized to all 33.2M paths: megakernel == wavefront bitwise on the whole image,
+    3000 sampled paths against the oracle."""
+    sc = scenes.terrain_scene(seed=0)
+    cam, spp, depth = sc["camera"], sc["spp"], sc["max_depth"]
+    g, osc = _both(pt, sc)
+    assert g.info()["n_tris"] > 9_900_000
+    n = cam["width"] * cam["height"] * spp
+    wf = g.render(cam, spp, depth, 0, path_L=True, sig=True, mode="wavefront", rr_start=3)
+    st = g.stats()
+    assert st["status"] == 0 and st["active"][0] == n
+    mk = g.render(cam, spp, depth, 0, sig=True, path_L=True, mode="megakernel", rr_start=3)
+    assert torch.equal(wf["img"], mk["img"]) and torch.equal(wf["sig"], mk["sig"])
+    rng = np.random.default_rng(1)
+    ids = np.sort(rng.choice(n, 3000, replace=False))
+    o = osc.render_paths(cam, spp, depth, 0, ids, rr_start=3)
+    compare_with_oracle(wf["path_L"][torch.from_numpy(ids).cuda()].cpu().numpy(),
+                        wf["sig"][torch.from_numpy(ids).cuda()].cpu().numpy(), o["L"], o["sig"], 1, label="terrain-4k")
+    del wf, mk
+
+
 def test_1024spp_image_within_monte_carlo_error(pt, torch):
     sc = _mixed_box(24, 24)
     cam = sc["camera"]
