@@ -883,7 +883,8 @@ pt_status pt_render(pt_scene* sc, const pt_camera* cam, uint32_t spp, uint32_t m
             pt::Launch l = launch_for(sc, pt::K_MEGA, o.block_size, 128, st, n_paths);
             PT_CUDA(pt::launch_megakernel(l, sc->view(), dc, p, n_paths, outL, img, o.d_path_sig, sc->rays()));
         } else {
-            pt::Launch l = launch_for(sc, pt::K_MEGA_REGEN, o.block_size, 128, st, n_paths);
+            pt::Launch l = launch_for(sc, pt::K_MEGA_REGEN, o.block_size ? std::min<uint32_t>(o.block_size, 128) : 128, 128,
+                                      st, n_paths);
             PT_CUDA(pt::launch_megakernel_regen(l, sc->view(), dc, p, n_paths, outL, img, o.d_path_sig, sc->rays(),
                                                 sc->next_path()));
         }

@@ -79,8 +79,7 @@ __device__ __forceinline__ void load_node(const float4* __restrict__ nodes, uint
     refs = make_uint2(__float_as_uint(n3.x), __float_as_uint(n3.y));
 }
 
-// Closest hit, plain order: one loop that takes a node step or a leaf step per iteration.  The
-// wavefront's traversal kernels use it (measured faster there than the while-while order).
+// Closest hit: one loop that takes a node step or a leaf step per iteration.
 __device__ __forceinline__ Hit trace_closest_plain(const DevScene& s, float3 o, float3 d) {
     float3 id = ray_rcp(d);
     float tbest = __int_as_float(0x7f800000);
@@ -148,7 +147,7 @@ __device__ __forceinline__ Hit trace_closest_plain(const DevScene& s, float3 o, 
     return h;
 }
 
-// Any hit with 0 < t < tmax, plain order.
+// Any hit with 0 < t < tmax.
 __device__ __forceinline__ bool trace_any_plain(const DevScene& s, float3 o, float3 d, float tmax) {
     float3 id = ray_rcp(d);
     uint32_t stack_ref[kStack];
@@ -190,153 +189,13 @@ __device__ __forceinline__ bool trace_any_plain(const DevScene& s, float3 o, flo
     }
 }
 
-constexpr uint32_t kDone = 0x7FFFFFFFu;     // "traversal finished" (no internal node has this index)
-constexpr uint32_t kNoLeaf = 0u;            // no postponed leaf (0 is the root, never a leaf ref)
-
-// Closest hit along o + t d, t > 0.  "While-while" order (after Aila & Laine,
-// "Understanding the Efficiency of Ray Traversal on GPUs", 2009): each lane walks internal nodes,
-// setting aside the first leaf it reaches, until every lane of the warp holds a leaf; then the
-// lanes test their leaves together.  Keeping node steps and triangle steps in separate loops keeps
-// the warp on one code path; the hit found does not depend on the visiting order (ties on t go to
-// the lower triangle id).
-__device__ __forceinline__ Hit trace_closest_ww(const DevScene& s, float3 o, float3 d) {
-    const float3 id = ray_rcp(d);
-    float tbest = __int_as_float(0x7f800000);
-    uint32_t best = kMiss, bprim = kMiss;
-    uint32_t stack_ref[kStack];
-    float stack_t[kStack];
-    int sp = 0;
-    uint32_t node = 0, leaf = kNoLeaf;
-    uint32_t steps = 0;
-    auto pop = [&]() -> uint32_t {
-        while (sp > 0) {
-            --sp;
-            if (stack_t[sp] <= tbest * 1.0000005f) return stack_ref[sp];
-        }
-        return kDone;
-    };
-    while (node != kDone || leaf != kNoLeaf) {
-        // walk internal nodes; set aside the first leaf reached
-        while (node != kDone && !(node & kLeafBit)) {
-            float4 n0, n1, n2;
-            uint2 r;
-            load_node(s.nodes, node, n0, n1, n2, r);
-            float t0, t1;
-            const bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tbest, t0);
-            const bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tbest, t1);
-            if (h0 && h1) {
-                const bool first0 = t0 <= t1;
-                if (sp < kStack) {
-                    stack_ref[sp] = first0 ? r.y : r.x;
-                    stack_t[sp] = first0 ? t1 : t0;
-                    ++sp;
-                } else {
-                    atomicOr(s.status, ST_TRAVERSAL);
-                }
-                node = first0 ? r.x : r.y;
-            } else if (h0 || h1) {
-                node = h0 ? r.x : r.y;
-            } else {
-                node = pop();
-            }
-            if (node != kDone && (node & kLeafBit) && leaf == kNoLeaf) {
-                leaf = node;
-                node = pop();
-            }
-            if (++steps >= kMaxSteps) {
-                atomicOr(s.status, ST_TRAVERSAL);
-                node = kDone;
-                leaf = kNoLeaf;
-            }
-            if (!__any_sync(__activemask(), leaf == kNoLeaf)) break;
-        }
-        // test the set-aside leaf, then any leaves that follow directly
-        while (leaf != kNoLeaf) {
-            const uint32_t first = (leaf & 0x7FFFFFFFu) >> 3, cnt = (leaf & 7u) + 1u;
-            for (uint32_t k = 0; k < cnt; ++k) {
-                float t;
-                uint32_t prim;
-                if (tri_test(s.tris, first + k, o, d, t, prim) && t > 0.0f &&
-                    (t < tbest || (t == tbest && prim < bprim))) {
-                    tbest = t;
-                    best = first + k;
-                    bprim = prim;
-                }
-            }
-            leaf = kNoLeaf;
-            if (node != kDone && (node & kLeafBit)) {
-                leaf = node;
-                node = pop();
-            }
-        }
-    }
-    Hit h;
-    h.t = tbest;
-    h.tri = best;
-    return h;
-}
-
-// Any hit with 0 < t < tmax, in the same while-while order; returns at the first hit.
-__device__ __forceinline__ bool trace_any_ww(const DevScene& s, float3 o, float3 d, float tmax) {
-    const float3 id = ray_rcp(d);
-    uint32_t stack_ref[kStack];
-    int sp = 0;
-    uint32_t node = 0, leaf = kNoLeaf;
-    uint32_t steps = 0;
-    auto pop = [&]() -> uint32_t { return sp > 0 ? stack_ref[--sp] : kDone; };
-    while (node != kDone || leaf != kNoLeaf) {
-        while (node != kDone && !(node & kLeafBit)) {
-            float4 n0, n1, n2;
-            uint2 r;
-            load_node(s.nodes, node, n0, n1, n2, r);
-            float t0, t1;
-            const bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tmax, t0);
-            const bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tmax, t1);
-            if (h0 && h1) {
-                if (sp < kStack) stack_ref[sp++] = r.y;
-                else atomicOr(s.status, ST_TRAVERSAL);
-                node = r.x;
-            } else if (h0 || h1) {
-                node = h0 ? r.x : r.y;
-            } else {
-                node = pop();
-            }
-            if (node != kDone && (node & kLeafBit) && leaf == kNoLeaf) {
-                leaf = node;
-                node = pop();
-            }
-            if (++steps >= kMaxSteps) {
-                atomicOr(s.status, ST_TRAVERSAL);
-                return false;
-            }
-            if (!__any_sync(__activemask(), leaf == kNoLeaf)) break;
-        }
-        while (leaf != kNoLeaf) {
-            const uint32_t first = (leaf & 0x7FFFFFFFu) >> 3, cnt = (leaf & 7u) + 1u;
-            for (uint32_t k = 0; k < cnt; ++k) {
-                float t;
-                uint32_t prim;
-                if (tri_test(s.tris, first + k, o, d, t, prim) && t > 0.0f && t < tmax) return true;
-            }
-            leaf = kNoLeaf;
-            if (node != kDone && (node & kLeafBit)) {
-                leaf = node;
-                node = pop();
-            }
-        }
-    }
-    return false;
-}
-
-// The extend and shadow queries.  WW selects the while-while order (used by the one-thread-per-path
-// kernels, where it also lowers register pressure) or the plain loop (used by the wavefront stages).
-template <bool WW>
-__device__ __forceinline__ Hit trace_closest(const DevScene& s, float3 o, float3 d) {
-    return WW ? trace_closest_ww(s, o, d) : trace_closest_plain(s, o, d);
-}
-template <bool WW>
+// The extend and shadow queries.  (A "while-while" variant that voted across the warp with
+// __any_sync(__activemask(), ...) was tried and removed: its result depended on which paths shared a
+// warp -- lanes that are not converged may pass different masks to the vote -- so one path in 33M
+// differed between the megakernel and the wavefront.)
+__device__ __forceinline__ Hit trace_closest(const DevScene& s, float3 o, float3 d) { return trace_closest_plain(s, o, d); }
 __device__ __forceinline__ bool trace_any(const DevScene& s, float3 o, float3 d, float tmax) {
-    return WW ? trace_any_ww(s, o, d, tmax) : trace_any_plain(s, o, d, tmax);
+    return trace_any_plain(s, o, d, tmax);
 }
 
 }  // namespace pt
