@@ -56,8 +56,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
             obj = os.path.join(BUILD, os.path.basename(src) + ".o")
             objs.append(obj)
-            jobs.append([nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas",
-                         "-warn-spills", *inc, "-c", src, "-o", obj])
+            # -fmad=false: every product and sum is rounded on its own, so the megakernel, the
+            # wavefront stages and the adjoint compute bit-identical values (ptxas may otherwise fuse
+            # a mul and an add into an FMA differently in each kernel, depending on register pressure)
+            jobs.append([nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
+                         "-Xptxas", "-warn-spills", *inc, "-c", src, "-o", obj])
         for src in sorted(glob.glob(os.path.join(CSRC, "*.cpp"))):
             obj = os.path.join(BUILD, os.path.basename(src) + ".o")
             objs.append(obj)
