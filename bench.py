@@ -39,7 +39,6 @@ BYTES_PER_UNIT = {
     "shadow": 80,      # per shadow ray: o|tmax + d|id (32 B) + contribution (16 B) read, L rw (32 B)
     "shade": 184,      # per active path: ray+tp (48) + hit (8) + L rw (32) + next ray (48) + shadow (48)
     "megakernel": 12,  # per path: radiance written (scene reads amortise to ~0 per path)
-    "adjoint": 12,     # per path: gradient image read
 }
 
 
@@ -255,20 +254,21 @@ def run_gpu(args):
         total_ms, total_rays = float(t.item()), float(r_.item())
     value = total_rays / (total_ms * 1e-3) / 1e6
 
-    # stage times from the library's events on the launch stream (timed region)
-    stage = {"extend": sum(r[3]["ms_extend"] for r in recs), "shade": sum(r[3]["ms_shade"] for r in recs),
-             "shadow": sum(r[3]["ms_shadow"] for r in recs), "sort": sum(r[3]["ms_sort"] for r in recs),
-             "raygen": sum(r[3]["ms_raygen"] for r in recs), "reduce": sum(r[3]["ms_reduce"] for r in recs),
+    # stage times from the library's events on the launch stream (timed region); the adjoint's
+    # wavefront replay launches the same extend/shadow kernels (and a record-writing shade), so
+    # its stages are added to the forward ones
+    def tot(key, idx=(3, 5)):
+        return sum(r[i][key] for r in recs for i in idx)
+    stage = {"extend": tot("ms_extend"), "shade": tot("ms_shade"), "shadow": tot("ms_shadow"),
+             "sort": tot("ms_sort"), "raygen": tot("ms_raygen"), "reduce": tot("ms_reduce"),
              "megakernel": sum(r[4]["ms_megakernel"] for r in recs),
-             "adjoint": sum(r[5]["ms_adjoint"] for r in recs)}
-    launches = {"extend": sum(r[3]["launches_extend"] for r in recs),
-                "shadow": sum(r[3]["launches_shadow"] for r in recs),
-                "megakernel": args.steps, "adjoint": args.steps,
-                "shade": sum(r[3]["launches_extend"] for r in recs)}
-    units = {"extend": sum(r[3]["extension_rays"] for r in recs), "shadow": sum(r[3]["shadow_rays"] for r in recs),
-             "shade": sum(r[3]["extension_rays"] for r in recs), "megakernel": n_paths * args.steps,
-             "adjoint": n_paths * args.steps}
-    dom = max(("extend", "shadow", "shade", "megakernel", "adjoint"), key=lambda k: stage[k])
+             "adjoint_total": sum(r[5]["ms_adjoint"] for r in recs)}
+    launches = {"extend": tot("launches_extend"), "shadow": tot("launches_shadow"),
+                "megakernel": args.steps, "shade": tot("launches_extend")}
+    units = {"extend": 2 * sum(r[3]["extension_rays"] for r in recs),
+             "shadow": 2 * sum(r[3]["shadow_rays"] for r in recs),
+             "shade": 2 * sum(r[3]["extension_rays"] for r in recs), "megakernel": n_paths * args.steps}
+    dom = max(("extend", "shadow", "shade", "megakernel"), key=lambda k: stage[k])
     peak, peak_src = load_peaks()
     alg_bytes = BYTES_PER_UNIT[dom] * units[dom]
     achieved = alg_bytes / (stage[dom] * 1e-3) / 1e9
@@ -311,6 +311,7 @@ def run_gpu(args):
                                   "note": "one thread per path over all paths (the paper's layout); not in the step"},
             "wf_over_mk_speedup": mk_frame / wf_frame,
             "bwd_over_fwd": float(np.mean(bw_ms)) / min(wf_frame, mk_frame),
+            "adjoint": {"ms_per_pass": float(np.mean(bw_ms)), "replay": "wavefront stages + per-vertex records"},
             "stage_ms_per_step": {k: v / args.steps for k, v in stage.items()},
             "roofline": roofline,
             "gpu_launches": int(gpu_launches),

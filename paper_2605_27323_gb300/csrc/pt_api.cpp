@@ -975,16 +975,27 @@ pt_status pt_render_backward(pt_scene* sc, const pt_camera* cam, uint32_t spp, u
             const uint32_t n = (uint32_t)std::min<uint64_t>(cap, n_paths - w0);
             pt::RenderParams pw = p;
             pw.path_begin = w0;
+            size_t e2 = 0;
+            PT_TRY(sc->ev_begin(ST_RAYGEN, st, e2));
             PT_CUDA(pt::launch_raygen(simple_launch(sc, st, n), dc, pw, n, w));
+            PT_TRY(sc->ev_end(e2, st));
             for (uint32_t b = 0; b < max_depth; ++b) {
                 const int in = (int)(b & 1u);
+                PT_TRY(sc->ev_begin(ST_EXTEND, st, e2));
                 PT_CUDA(pt::launch_extend(launch_for(sc, pt::K_EXTEND, o.block_size, 256, st, n), ds, w, in, pw));
+                PT_TRY(sc->ev_end(e2, st));
+                PT_TRY(sc->ev_begin(ST_SHADE, st, e2));
                 PT_CUDA(pt::launch_shade_adj(launch_for(sc, pt::K_SHADE_ADJ, o.block_size, 256, st, n), ds, pw, w, ab, in, b));
+                PT_TRY(sc->ev_end(e2, st));
+                PT_TRY(sc->ev_begin(ST_SHADOW, st, e2));
                 PT_CUDA(pt::launch_shadow_adj(launch_for(sc, pt::K_SHADOW_ADJ, o.block_size, 256, st, n), ds, pw, w, ab, b));
+                PT_TRY(sc->ev_end(e2, st));
                 PT_CUDA(pt::launch_prepare(st, w, b));
             }
+            PT_TRY(sc->ev_begin(ST_REDUCE, st, e2));
             PT_CUDA(pt::launch_adjoint_reverse(simple_launch(sc, st, n), ds, pw, w, ab, n, grad, d_grad_albedo,
                                                d_grad_emission));
+            PT_TRY(sc->ev_end(e2, st));
             sc->launches += 2 + 4 * max_depth;
         }
     }
