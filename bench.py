@@ -9,6 +9,8 @@ the device.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   python bench.py --workload batch      # 64 scenes in one persistent launch vs 64 renders
+  python bench.py --workload large      # ~10M-triangle scene, 3840x2160, 4 spp, depth 8
+  python bench.py --workload diff       # inverse rendering, 512x512, 64 spp, 256 materials
 Under torchrun (N > 1) each rank renders its own frames (seed offset by rank, no collective on the
 data path: weak scaling); the barrier and max-over-ranks timing are the only communication.
 """
@@ -28,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Mrays/s and ms/frame (1080p, 1 spp) wavefront vs megakernel; bwd/fwd time ratio"
-WORKLOAD = ("procedural spheres scene: 200 level-4 icospheres + 256x256-quad ground (1,155,072 tris), "
+WORKLOAD = ("procedural spheres scene: 200 level-4 icospheres + 256x256-quad ground (1,155,088 tris), "
             "8 emissive quads + constant environment, 1920x1080, 1 spp, max depth 5, roulette from bounce 3; "
             "step = wavefront frame + megakernel frame + adjoint pass")
 KERNEL_SOURCES = ["paper_2605_27323_gb300/csrc/pt_kernels.cu", "paper_2605_27323_gb300/csrc/pt_device.cuh",
@@ -183,6 +185,27 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def hybrid_sweep(g, cam, spp, depth, thresholds, reps, flush, base_kw):
+    """Wavefront frames with the hybrid continuation kernel at each threshold (device-timed, L2
+    flushed between frames): {threshold: mean ms per frame}."""
+    import torch
+    stream = torch.cuda.current_stream()
+    res = {}
+    for thr in thresholds:
+        g.render(cam, spp, depth, 700, hybrid=thr, **base_kw)
+        ms = []
+        for k in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.render(cam, spp, depth, 800 + k, hybrid=thr, **base_kw)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            flush.fill_(k & 0xFF)
+        res[int(thr)] = float(np.mean(ms))
+    return res
+
+
 def run_gpu(args):
     import torch
 
@@ -268,7 +291,16 @@ def run_gpu(args):
     units = {"extend": 2 * sum(r[3]["extension_rays"] for r in recs),
              "shadow": 2 * sum(r[3]["shadow_rays"] for r in recs),
              "shade": 2 * sum(r[3]["extension_rays"] for r in recs), "megakernel": n_paths * args.steps}
-    dom = max(("extend", "shadow", "shade", "megakernel"), key=lambda k: stage[k])
+    # The roofline is reported for k_extend, the wavefront's top kernel (forward + adjoint replay):
+    # its algorithmic bytes are the queue records it moves.  The megakernel, whose total time is
+    # similar, keeps each path's state in registers (12 B of radiance written per path), so an HBM
+    # roofline does not bound it; every kernel's share of the step is listed beside the roofline.
+    dom = "extend"
+    kernel_ms = {k: stage[k] for k in ("extend", "shadow", "shade", "megakernel", "sort", "raygen", "reduce")}
+    kernel_ms["adjoint_other"] = max(0.0, stage["adjoint_total"] - sum(r[5][k] for r in recs for k in
+                                                                     ("ms_extend", "ms_shade", "ms_shadow",
+                                                                      "ms_raygen", "ms_reduce")))
+    shares = {k: v / max(1e-9, sum(kernel_ms.values())) for k, v in kernel_ms.items()}
     peak, peak_src = load_peaks()
     alg_bytes = BYTES_PER_UNIT[dom] * units[dom]
     achieved = alg_bytes / (stage[dom] * 1e-3) / 1e9
@@ -277,7 +309,8 @@ def run_gpu(args):
                 "frac": achieved / peak, "peak_source": peak_src,
                 "traffic": (tr * units[dom] / launches[dom]) if tr is not None else None,
                 "algorithmic_bytes_per_launch": alg_bytes / launches[dom],
-                "avg_launch_ms": stage[dom] / launches[dom]}
+                "avg_launch_ms": stage[dom] / launches[dom],
+                "share_of_step_kernel_time": {k: round(v, 4) for k, v in shares.items()}}
     gpu_launches = sum(r[3]["launches_total"] + r[4]["launches_total"] + r[5]["launches_total"] for r in recs)
 
     wf_frame = float(np.mean(wf_ms))
@@ -292,6 +325,10 @@ def run_gpu(args):
         e1.synchronize()
         st_ms.append(e0.elapsed_time(e1))
         flush.fill_(s_ & 0xFF)
+    # the hybrid of the paper's future work: the last sparse bounces finished in one kernel
+    hyb = hybrid_sweep(g, cam, spp, depth, (1 << 16, 1 << 18, 1 << 20), max(3, args.steps // 2), flush,
+                       dict(mode="wavefront", rr_start=3, sort=args.sort))
+    hyb_thr = min(hyb, key=hyb.get)
     out = None
     if rank == 0:
         e2e = measure_e2e(g, cam, spp, depth, grad, args, wf_opts, mk_opts) if world == 1 else None
@@ -306,6 +343,10 @@ def run_gpu(args):
                           "rays_per_frame": float(np.mean(wf_rays))},
             "megakernel": {"mrays_s": float(np.sum(mk_rays)) / (np.sum(mk_ms) * 1e-3) / 1e6,
                            "ms_per_frame": mk_frame, "rays_per_frame": float(np.mean(mk_rays))},
+            "hybrid": {"ms_per_frame": hyb[hyb_thr], "threshold": hyb_thr, "sweep_ms": hyb,
+                       "wavefront_over_hybrid": wf_frame / hyb[hyb_thr],
+                       "note": "wavefront frame whose remaining bounces run in one persistent kernel once at "
+                               "most `threshold` paths are active; same image; not in the step"},
             "megakernel_static": {"ms_per_frame": float(np.mean(st_ms)),
                                   "mrays_s": float(np.mean(mk_rays)) / (float(np.mean(st_ms)) * 1e-3) / 1e6,
                                   "note": "one thread per path over all paths (the paper's layout); not in the step"},
@@ -394,6 +435,11 @@ def run_large(args):
             rays.append(st["extension_rays"] + st["shadow_rays"])
         res[mode] = {"ms_per_frame": float(np.mean(ms)), "mrays_s": float(np.sum(rays) / (np.sum(ms) * 1e-3) / 1e6),
                      "rays_per_frame": float(np.mean(rays))}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    hyb = hybrid_sweep(g, cam, spp, depth, (1 << 18, 1 << 20, 1 << 22), 3, flush, dict(mode="wavefront"))
+    hyb_thr = min(hyb, key=hyb.get)
+    res["hybrid"] = {"ms_per_frame": hyb[hyb_thr], "threshold": hyb_thr, "sweep_ms": hyb,
+                     "wavefront_over_hybrid": res["wavefront"]["ms_per_frame"] / hyb[hyb_thr]}
     info = g.info()
     line = {"metric": "Mrays/s and ms/frame, large scene (3840x2160, 4 spp, depth 8)", "value": res["wavefront"]["mrays_s"],
             "unit": "Mrays/s", "n_gpus": 1, "steps": max(3, min(args.steps, 10)), "warmup": args.warmup,
@@ -402,8 +448,84 @@ def run_large(args):
             "config": {"workload": "2048^2 fBm heightfield + 5000 level-2 icospheres, 64 emissive quads",
                        "triangles": int(info["n_tris"]), "bvh_nodes": int(info["n_nodes"]),
                        "device_bytes": int(info["device_bytes"]), "scene_setup_s": setup_s},
-            "wavefront": res["wavefront"], "megakernel": res["megakernel"],
+            "wavefront": res["wavefront"], "megakernel": res["megakernel"], "hybrid": res["hybrid"],
             "wf_over_mk_speedup": res["megakernel"]["ms_per_frame"] / res["wavefront"]["ms_per_frame"]}
+    print(json.dumps(line), flush=True)
+
+
+def run_diff(args):
+    """Inverse rendering on the 256-material spheres scene (512x512, 64 spp, depth 6, fixed roulette
+    0.9): each step renders the image with the current albedos and emissions, takes the L2 loss
+    against a target rendered with hidden parameters (another seed), back-propagates through the
+    path-replay adjoint and applies an Adam update.  Reports forward and backward device times,
+    their ratio, and the loss and parameter error along the way."""
+    import torch
+
+    import paper_2605_27323_gb300 as pt
+    from paper_2605_27323_gb300 import scenes
+    sc = scenes.diff_scene(seed=0)
+    g = pt.Scene.from_dict(sc)
+    cam, spp, depth = sc["camera"], sc["spp"], sc["max_depth"]
+    W, H = cam["width"], cam["height"]
+    kw = dict(rr_start=sc["rr_start"], rr_fixed=sc["rr_fixed"])
+    alb_t, em_t = (torch.from_numpy(x).cuda() for x in scenes.diff_target(sc, seed=7))
+    g.set_materials(alb_t, em_t)
+    target = g.render(cam, spp, depth, 999_999, **kw).clone()
+    alb = torch.tensor(np.asarray(sc["mat_albedo"], np.float32), device="cuda").reshape(-1, 3).requires_grad_()
+    em = torch.tensor(np.asarray(sc["mat_emission"], np.float32), device="cuda").requires_grad_()
+    opt = torch.optim.Adam([{"params": [alb], "lr": 0.02}, {"params": [em], "lr": 0.2}])
+    stream = torch.cuda.current_stream()
+    n_paths = W * H * spp
+
+    def step(seed):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        opt.zero_grad(set_to_none=True)
+        ev[0].record(stream)
+        g.set_materials(alb, em)
+        img = g.render(cam, spp, depth, seed, **kw)
+        ev[1].record(stream)
+        diff = img - target
+        loss = (diff * diff).mean()
+        grad_img = (2.0 / diff.numel()) * diff
+        ev[2].record(stream)
+        ga, ge = g.backward(cam, spp, depth, seed, grad_img, **kw)
+        ev[3].record(stream)
+        alb.grad, em.grad = ga, ge
+        opt.step()
+        with torch.no_grad():
+            alb.clamp_(0.0, 1.0)
+            em.clamp_(min=0.0)
+        ev[4].record(stream)
+        return ev, loss.detach()
+
+    lam = torch.from_numpy(np.asarray(sc["mat_type"]) == scenes.LAMBERT).cuda()
+    alb_err0 = float((alb.detach() - alb_t)[lam].abs().mean())
+    for w in range(args.warmup):
+        step(50_000 + w)
+    torch.cuda.synchronize()
+    recs = [step(s) for s in range(args.steps)]
+    torch.cuda.synchronize()
+    fwd = [r[0][0].elapsed_time(r[0][1]) for r in recs]
+    bwd = [r[0][2].elapsed_time(r[0][3]) for r in recs]
+    tot = [r[0][0].elapsed_time(r[0][4]) for r in recs]
+    losses = [float(r[1]) for r in recs]
+    g.render(cam, spp, depth, 0, **kw)
+    st = g.stats()
+    rays_fwd = st["extension_rays"] + st["shadow_rays"]
+    alb_err = float((alb.detach() - alb_t)[lam].abs().mean())
+    line = {"metric": "inverse-rendering step: backward/forward time ratio (512x512, 64 spp, depth 6, 256 materials)",
+            "value": float(np.median(bwd) / np.median(fwd)), "unit": "ratio", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(np.mean(tot)), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "procedural spheres geometry, 256 shared materials, 512x512, 64 spp, depth 6, "
+                                   "roulette from bounce 3 with q = 0.9; L2 loss to a target from hidden parameters "
+                                   "(seed 7); Adam on albedo and emission",
+                       "paths": n_paths, "l2": "inputs (scene, queues, records) exceed L2; no flush"},
+            "forward_ms": float(np.median(fwd)), "backward_ms": float(np.median(bwd)),
+            "forward_mrays_s": rays_fwd / (np.median(fwd) * 1e-3) / 1e6,
+            "loss_first": losses[0], "loss_last": losses[-1],
+            "lambert_albedo_mean_abs_error": {"start": alb_err0, "end": alb_err,
+                                              "steps": args.warmup + args.steps}}
     print(json.dumps(line), flush=True)
 
 
@@ -499,7 +621,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="frame", choices=["frame", "batch", "large"])
+    ap.add_argument("--workload", default="frame", choices=["frame", "batch", "large", "diff"])
     ap.add_argument("--sort", default="none", choices=["none", "type", "material"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -513,6 +635,9 @@ def main():
         return
     if args.workload == "large":
         run_large(args)
+        return
+    if args.workload == "diff":
+        run_diff(args)
         return
     run_gpu(args)
 

@@ -73,8 +73,11 @@ enum {
     PT_FLAG_PROFILE = 1u,       /* time each stage with CUDA events on the launch stream; read the
                                    times with pt_get_stats after the stream completes */
     PT_FLAG_NO_GRAPH = 2u,      /* batched wavefront: launch the bounce loop directly, not as a CUDA graph */
-    PT_FLAG_MK_STATIC = 4u      /* megakernel: one thread per path, launched over all paths (the paper's
+    PT_FLAG_MK_STATIC = 4u,     /* megakernel: one thread per path, launched over all paths (the paper's
                                    layout) instead of the persistent kernel with path regeneration */
+    PT_FLAG_HALTON = 8u         /* pixel jitter from the Halton sequence in bases 2 and 3 over the pixel's
+                                   sample index with a per-pixel Cranley-Patterson rotation (Sec. 2.3),
+                                   in 24-bit fixed point; default: the path's PCG uniforms */
 };
 
 typedef struct {
@@ -86,7 +89,12 @@ typedef struct {
     uint32_t flags;             /* PT_FLAG_* */
     uint64_t queue_capacity;    /* wavefront: paths per wave; 0 = all paths in one wave */
     uint32_t* d_path_sig;       /* optional device N_p u32: per-path branch signature (testing) */
-    uint64_t reserved;
+    uint64_t hybrid_threshold;  /* wavefront (pt_render, pt_render_progressive): when at most this many
+                                   paths of a wave are active entering a bounce, one persistent kernel
+                                   finishes them all in registers (the megakernel's loop body) instead
+                                   of running the remaining bounces as wavefront stages -- the hybrid of
+                                   the paper's future work (Sec. 5).  Decided on the device, so the
+                                   image is unchanged.  0 = off.  Ignored by the other entry points. */
 } pt_render_opts;
 
 typedef struct {
@@ -96,7 +104,8 @@ typedef struct {
     uint32_t bounces;           /* entries valid in active[] */
     uint32_t status;            /* device status word: 0 or a pt_status */
     uint64_t active[64];        /* wavefront: active paths entering each bounce (all waves) */
-    /* PT_FLAG_PROFILE: total milliseconds per stage of the last profiled call, and launches */
+    /* PT_FLAG_PROFILE: total milliseconds per stage of the last profiled call, and launches
+       (ms_megakernel includes the hybrid continuation kernel of a wavefront render) */
     float ms_raygen, ms_extend, ms_sort, ms_shade, ms_shadow, ms_reduce, ms_megakernel, ms_adjoint;
     uint32_t launches_extend, launches_shadow, launches_total;
     float ms_total;
@@ -131,6 +140,19 @@ pt_status pt_scene_set_materials(pt_scene* scene, const float* d_albedo, const f
  * megakernel and wavefront produce the same image. */
 pt_status pt_render(pt_scene* scene, const pt_camera* cam, uint32_t spp, uint32_t max_depth, uint64_t seed,
                     const pt_render_opts* opts, float* d_out_rgb, float* d_path_L_or_null, void* stream);
+
+/* Progressive rendering (the running average of the accumulation stage, Sec. 2.3): render pixel
+ * samples sample_offset .. sample_offset + spp - 1 (the random numbers of sample s are those of
+ * sample s of a one-call render), add each pixel's samples in sample order to its running FP32 sum
+ * in d_accum_rgb (device H x W x 3; zeroed first when sample_offset == 0, otherwise the caller's sums
+ * of samples 0 .. sample_offset - 1, e.g. from an earlier call or a saved state), and write
+ * sum / (sample_offset + spp) to d_out_rgb_or_null (device H x W x 3, or NULL).  Frames of k1, k2, ...
+ * samples therefore give exactly the image of one pt_render call with k1 + k2 + ... samples, and a
+ * render resumes from (sums, sample count).  Errors as pt_render, plus PT_ERR_INVALID_ARG for a NULL
+ * or host d_accum_rgb, a host d_out_rgb_or_null, or sample_offset + spp >= 2^32. */
+pt_status pt_render_progressive(pt_scene* scene, const pt_camera* cam, uint32_t spp, uint32_t max_depth, uint64_t seed,
+                                uint32_t sample_offset, const pt_render_opts* opts, float* d_accum_rgb,
+                                float* d_out_rgb_or_null, void* stream);
 
 /* Path-replay adjoint: accumulate d(loss)/d(albedo) and d(loss)/d(emission) for the image that
  * pt_render produces with the same arguments, given d_grad_rgb = d(loss)/d(image) (H x W x 3,

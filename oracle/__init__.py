@@ -66,6 +66,9 @@ def lib():
             L.or_u01.restype = f64
             L.or_u01.argtypes = [u32, u32, u32]
             L.or_u01_batch.argtypes = [u64, vp, vp, vp, vp, i64, vp]
+            L.or_radical_inverse24.restype = u32
+            L.or_radical_inverse24.argtypes = [u32, u32]
+            L.or_pixel_jitter_batch.argtypes = [u32, u64, vp, vp, i64, vp]
             L.or_scene_create.restype = vp
             L.or_scene_create.argtypes = [vp, i64, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp]
             L.or_scene_destroy.argtypes = [vp]
@@ -80,18 +83,20 @@ def lib():
             L.or_bsdf_sample.restype = i32
             L.or_bsdf_sample.argtypes = [u32, vp, f64, f64, vp, vp, vp, f64, f64, f64, vp, vp, vp]
             L.or_onb.argtypes = [vp, vp, vp]
+            L.or_bsdf_pdf.restype = f64
+            L.or_bsdf_pdf.argtypes = [u32, f64, vp, vp, vp]
             L.or_fresnel_dielectric.restype = f64
             L.or_fresnel_dielectric.argtypes = [f64, f64, f64]
             L.or_ggx_D.restype = f64
             L.or_ggx_D.argtypes = [f64, f64]
             L.or_ggx_G1.restype = f64
             L.or_ggx_G1.argtypes = [f64, f64]
-            L.or_render_paths.argtypes = [vp, vp, vp, vp, f32, u32, u32, u32, u32, u64, u32, f64, i32,
+            L.or_render_paths.argtypes = [vp, vp, vp, vp, f32, u32, u32, u32, u32, u64, u32, f64, u32, i32,
                                           vp, i64, i32, vp, vp, i32, vp, vp, vp, vp]
-            L.or_render_pixels.argtypes = [vp, vp, vp, vp, f32, u32, u32, u32, u32, u64, u32, f64, i32,
+            L.or_render_pixels.argtypes = [vp, vp, vp, vp, f32, u32, u32, u32, u32, u64, u32, f64, u32, i32,
                                            vp, i64, i32, vp, vp]
-            L.or_trace_rays.argtypes = [vp, vp, vp, vp, i64, u32, u32, f64, i32, i32, vp, vp, i32, vp, vp]
-            L.or_trace_path_events.argtypes = [vp, vp, vp, vp, f32, u32, u32, u32, u32, u64, u32, f64, vp, i64, vp,
+            L.or_trace_rays.argtypes = [vp, vp, vp, vp, i64, u32, u32, f64, u32, i32, i32, vp, vp, i32, vp, vp]
+            L.or_trace_path_events.argtypes = [vp, vp, vp, vp, f32, u32, u32, u32, u32, u64, u32, f64, u32, vp, i64, vp,
                                                vp, vp, vp]
             L.or_max_tangents.restype = i32
             _lib = L
@@ -105,6 +110,28 @@ def pcg_hash(v: int) -> int:
 
 def path_key(seed: int, pixel: int, sample: int) -> int:
     return int(lib().or_path_key(seed, pixel, sample))
+
+
+SAMPLERS = {"pcg": 0, "halton": 1}
+
+
+def _opts(sampler: str, mis: bool) -> int:
+    """Option bits of the render calls: 1 = Halton pixel jitter, 2 = multiple importance sampling."""
+    return SAMPLERS[sampler] | (2 if mis else 0)
+
+
+def radical_inverse24(base: int, s: int) -> int:
+    """floor(2^24 * phi_base(s)): the radical inverse of s in 24-bit fixed point."""
+    return int(lib().or_radical_inverse24(int(base), int(s)))
+
+
+def pixel_jitter(sampler: str, seed: int, pixel, sample) -> np.ndarray:
+    """Sub-pixel jitter (u0, u1) of camera rays, (n, 2)."""
+    px = _f(pixel, np.uint32).reshape(-1)
+    sm = _f(sample, np.uint32).reshape(-1)
+    out = np.empty((px.size, 2))
+    lib().or_pixel_jitter_batch(SAMPLERS[sampler], seed, _p(px), _p(sm), px.size, _p(out))
+    return out
 
 
 def u01(seed, pixel, sample, bounce, dim) -> np.ndarray:
@@ -132,6 +159,12 @@ def bsdf_sample(mtype, albedo, roughness, ior, n, ng, wo, u5, u6, u7):
                               _p(_f(ng, np.float64)), _p(_f(wo, np.float64)), u5, u6, u7, _p(wi), _p(w),
                               _p(code))
     return bool(ok), wi, w, int(code[0])
+
+
+def bsdf_pdf(mtype, roughness, n, wo, wi) -> float:
+    """Solid-angle density with which bsdf_sample draws wi (0 for the smooth dielectric)."""
+    return float(lib().or_bsdf_pdf(mtype, roughness, _p(_f(n, np.float64)), _p(_f(wo, np.float64)),
+                                   _p(_f(wi, np.float64))))
 
 
 def onb(n):
@@ -221,7 +254,7 @@ class Scene:
                 float(cam["vfov_deg"]), int(cam["width"]), int(cam["height"]))
 
     def render_paths(self, cam, spp, max_depth, seed, path_ids, rr_start=3, rr_fixed=0.0,
-                     use_bvh=True, dir_albedo=None, dir_emission=None, n_threads=0):
+                     use_bvh=True, dir_albedo=None, dir_emission=None, n_threads=0, sampler="pcg", mis=False):
         """Per-path radiance, optional directional derivatives, branch signatures, ray counts."""
         eye, tgt, up, fov, W, H = self._cam(cam)
         ids = _f(path_ids, np.uint64).reshape(-1)
@@ -239,12 +272,12 @@ class Scene:
             dL = None
             args = (0, None, None)
         lib().or_render_paths(self.h, _p(eye), _p(tgt), _p(up), fov, W, H, spp, max_depth, seed,
-                              rr_start, float(rr_fixed), int(use_bvh), _p(ids), n, *args, n_threads,
+                              rr_start, float(rr_fixed), _opts(sampler, mis), int(use_bvh), _p(ids), n, *args, n_threads,
                               _p(L), _p(dL) if dL is not None else None, _p(sig), _p(rays))
         return {"L": L, "dL": dL, "sig": sig, "rays": rays}
 
     def render_pixels(self, cam, spp, max_depth, seed, pixels=None, rr_start=3, rr_fixed=0.0,
-                      use_bvh=True, n_threads=0):
+                      use_bvh=True, n_threads=0, sampler="pcg", mis=False):
         """Mean radiance of the listed pixels (all pixels when None); returns (img (n,3), rays)."""
         eye, tgt, up, fov, W, H = self._cam(cam)
         if pixels is None:
@@ -253,11 +286,11 @@ class Scene:
         img = np.empty((px.size, 3))
         rays = np.zeros(2, np.uint64)
         lib().or_render_pixels(self.h, _p(eye), _p(tgt), _p(up), fov, W, H, spp, max_depth, seed,
-                               rr_start, float(rr_fixed), int(use_bvh), _p(px), px.size, n_threads,
+                               rr_start, float(rr_fixed), _opts(sampler, mis), int(use_bvh), _p(px), px.size, n_threads,
                                _p(img), _p(rays))
         return img, rays
 
-    def path_events(self, cam, spp, max_depth, seed, path_ids, rr_start=3, rr_fixed=0.0):
+    def path_events(self, cam, spp, max_depth, seed, path_ids, rr_start=3, rr_fixed=0.0, sampler="pcg", mis=False):
         """Event logs of the listed camera paths: list of [(bounce, kind, value, f0, f1), ...]."""
         eye, tgt, up, fov, W, H = self._cam(cam)
         ids = _f(path_ids, np.uint64).reshape(-1)
@@ -267,12 +300,12 @@ class Scene:
         n_ev = np.zeros(n, np.uint32)
         L = np.zeros((n, 3))
         lib().or_trace_path_events(self.h, _p(eye), _p(tgt), _p(up), fov, W, H, spp, max_depth, seed, rr_start,
-                                   float(rr_fixed), _p(ids), n, _p(ev), _p(pay), _p(n_ev), _p(L))
+                                   float(rr_fixed), _opts(sampler, mis), _p(ids), n, _p(ev), _p(pay), _p(n_ev), _p(L))
         return [[(int(ev[i, k, 0] >> 4), int(ev[i, k, 0] & 15), int(ev[i, k, 1]), float(pay[i, k, 0]),
                   float(pay[i, k, 1])) for k in range(n_ev[i])] for i in range(n)], L
 
     def trace_rays(self, o, d, keys, max_depth, rr_start=1 << 30, rr_fixed=0.0, use_bvh=True,
-                   dir_albedo=None, dir_emission=None, n_threads=0):
+                   dir_albedo=None, dir_emission=None, n_threads=0, mis=False):
         o = _f(o, np.float64).reshape(-1, 3)
         d = _f(d, np.float64).reshape(-1, 3)
         k = _f(keys, np.uint32).reshape(-1)
@@ -284,8 +317,8 @@ class Scene:
             de = _f(dir_emission, np.float64).reshape(nd, self.n_mats)
             dL = np.empty((n, nd, 3))
             lib().or_trace_rays(self.h, _p(o), _p(d), _p(k), n, max_depth, rr_start, float(rr_fixed),
-                                int(use_bvh), nd, _p(da), _p(de), n_threads, _p(L), _p(dL))
+                                _opts("pcg", mis), int(use_bvh), nd, _p(da), _p(de), n_threads, _p(L), _p(dL))
             return L, dL
         lib().or_trace_rays(self.h, _p(o), _p(d), _p(k), n, max_depth, rr_start, float(rr_fixed),
-                            int(use_bvh), 0, None, None, n_threads, _p(L), None)
+                            _opts("pcg", mis), int(use_bvh), 0, None, None, n_threads, _p(L), None)
         return L, None

@@ -20,7 +20,9 @@
  *
  * Readings where the paper is silent (each is listed with its reason in the design notes):
  *   - random numbers: counter-based PCG hash (Jarzynski & Olano, JCGT 2020) keyed by
- *     (seed, pixel, sample, bounce, dim); u = (h >> 8) * 2^-24, exact in FP32 and FP64;
+ *     (seed, pixel, sample, bounce, dim); u = (h >> 8) * 2^-24, exact in FP32 and FP64; the pixel
+ *     jitter optionally follows the paper's Halton (2,3) sequence with a per-pixel Cranley-Patterson
+ *     rotation, in 24-bit fixed point;
  *   - NEE only, no MIS: a BSDF-sampled hit on a listed light adds its emission only at bounce 0
  *     or after a delta bounce; emitters not in the light list always add; the light pmf is
  *     proportional to area; lights and all emission are one-sided (front face by winding);
@@ -96,6 +98,62 @@ enum { D_JX = 0, D_JY = 1, D_LIGHT = 2, D_LU = 3, D_LV = 4, D_LOBE = 5, D_DIR0 =
 void or_u01_batch(uint64_t seed, const uint32_t* pixel, const uint32_t* sample, const uint32_t* bounce,
                   const uint32_t* dim, int64_t n, double* out) {
     for (int64_t i = 0; i < n; ++i) out[i] = or_u01(or_path_key(seed, pixel[i], sample[i]), bounce[i], dim[i]);
+}
+
+/* ------------------------------------------------------------------ pixel jitter (Sec. 2.3)
+ * The ray-generation stage jitters each camera ray inside its pixel.  Two samplers:
+ *   OR_SAMPLER_PCG: u0, u1 = the path's uniforms of bounce 0, dims D_JX and D_JY;
+ *   OR_SAMPLER_HALTON: the paper's Halton sequence in bases 2 and 3 over the pixel's sample index,
+ *     shifted per pixel by a Cranley-Patterson rotation (Cranley & Patterson 1976) modulo 1.
+ * Everything is a 24-bit fixed-point fraction, so FP32 and FP64 see the same numbers:
+ *   radical inverse (van der Corput / Halton 1960): s = sum_k d_k b^k has phi_b(s) = sum_k d_k b^-(k+1);
+ *   with K digits (b^K >= 2^32 > s) that is R / b^K with R = sum_k d_k b^(K-1-k), kept as
+ *   floor(2^24 R / b^K);
+ *   rotation of dim d: the top 24 bits of the hash of (seed, pixel, sample 2^32 - 1) for (bounce 0, d)
+ *   (that sample index is never rendered: sample_offset + spp < 2^32);
+ *   u_d = ((phi(s) + rotation_d) mod 2^24) * 2^-24. */
+#define OR_SAMPLER_PCG 0u
+#define OR_SAMPLER_HALTON 1u
+
+uint32_t or_radical_inverse24(uint32_t base, uint32_t s) {
+    uint64_t bk = 1;
+    int K = 0;
+    while (bk < (1ull << 32)) {
+        bk *= base;
+        ++K;
+    }
+    uint64_t R = 0;
+    uint32_t t = s;
+    for (int k = 0; k < K; ++k) {   /* reverse the K base-b digits of s */
+        R = R * base + t % base;
+        t /= base;
+    }
+    return (uint32_t)((R << 24) / bk);
+}
+
+static uint32_t hash24(uint32_t key, uint32_t bounce, uint32_t dim) {
+    return or_pcg_hash(key ^ or_pcg_hash((bounce << 4) | dim)) >> 8;
+}
+
+static void pixel_jitter(uint32_t sampler, uint64_t seed, uint32_t pixel, uint32_t sample, uint32_t key, double* u0,
+                         double* u1) {
+    if (sampler == OR_SAMPLER_HALTON) {
+        uint32_t kp = or_path_key(seed, pixel, 0xFFFFFFFFu);
+        uint32_t j0 = (or_radical_inverse24(2, sample) + hash24(kp, 0, D_JX)) & 0xFFFFFFu;
+        uint32_t j1 = (or_radical_inverse24(3, sample) + hash24(kp, 0, D_JY)) & 0xFFFFFFu;
+        *u0 = (double)j0 / 16777216.0;
+        *u1 = (double)j1 / 16777216.0;
+    } else {
+        *u0 = or_u01(key, 0, D_JX);
+        *u1 = or_u01(key, 0, D_JY);
+    }
+}
+
+void or_pixel_jitter_batch(uint32_t sampler, uint64_t seed, const uint32_t* pixel, const uint32_t* sample, int64_t n,
+                           double* out) {
+    for (int64_t i = 0; i < n; ++i)
+        pixel_jitter(sampler, seed, pixel[i], sample[i], or_path_key(seed, pixel[i], sample[i]), out + 2 * i,
+                     out + 2 * i + 1);
 }
 
 /* ------------------------------------------------------------------ scene */
@@ -531,6 +589,28 @@ static dc bsdf_eval(const omat* m, dc a, v3 n, v3 wo, v3 wi, int nd) {
     return dc_scale(F, D * G2 / (4.0 * co * ci), nd);
 }
 
+/* Solid-angle density with which bsdf_sample draws wi (non-delta materials; n faces wo), for the
+ * multiple-importance weights:
+ *   Lambert: cos(n, wi) / pi (cosine-weighted hemisphere);
+ *   GGX: the visible-normal density D_wo(h) = G1(wo) max(0, wo.h) D(h) / (n.wo) (Heitz 2018) times
+ *   the Jacobian 1 / (4 wo.h) of wi = reflect(wo, h):  G1(wo) D(h) / (4 n.wo). */
+static double bsdf_pdf(const omat* m, v3 n, v3 wo, v3 wi) {
+    double co = dot(n, wo), ci = dot(n, wi);
+    if (co <= 0.0 || ci <= 0.0 || m->type == OR_MAT_DIELECTRIC) return 0.0;
+    if (m->type == OR_MAT_LAMBERT) return ci / OR_PI;
+    double alpha = ggx_alpha(m->roughness);
+    v3 h = nrm(add(wo, wi));
+    double g1 = 1.0 / (1.0 + ggx_lambda(alpha, co));
+    return g1 * ggx_D(alpha, dot(n, h)) / (4.0 * co);
+}
+
+/* Power heuristic with exponent 2 (Veach, "Robust Monte Carlo Methods for Light Transport
+ * Simulation", 1997): weight of the strategy with density pa against pb. */
+static double power_heuristic(double pa, double pb) {
+    double a2 = pa * pa, b2 = pb * pb;
+    return a2 + b2 > 0.0 ? a2 / (a2 + b2) : 0.0;
+}
+
 /* Visible-normal sample of GGX in the local frame (n = +z), from the construction of Heitz,
  * "Sampling the GGX Distribution of Visible Normals", JCGT 2018: stretch the view vector to the
  * hemisphere configuration, sample a point on the projected disk (warped toward the visible
@@ -648,6 +728,12 @@ int or_bsdf_sample(uint32_t type, const double* albedo, double roughness, double
     return s.valid;
 }
 
+double or_bsdf_pdf(uint32_t type, double roughness, const double* n, const double* wo, const double* wi) {
+    omat m; memset(&m, 0, sizeof(m));
+    m.type = type; m.roughness = roughness; m.ior = 1.5;
+    return bsdf_pdf(&m, mk(n[0], n[1], n[2]), mk(wo[0], wo[1], wo[2]), mk(wi[0], wi[1], wi[2]));
+}
+
 void or_onb(const double* n, double* t, double* b) {
     v3 tt, bb;
     onb(mk(n[0], n[1], n[2]), &tt, &bb);
@@ -669,7 +755,12 @@ typedef struct {
     uint32_t rr_start;
     double rr_fixed;     /* > 0: fixed survival probability; else clamp(max(tp), 0.05, 0.95) */
     int use_bvh;
+    int mis;             /* combine NEE and BSDF-sampled light hits with the power heuristic */
 } ropts;
+
+/* Option bits of the exported render calls. */
+#define OR_OPT_HALTON 1u
+#define OR_OPT_MIS 2u
 
 /* Optional per-path event log (testing aid): up to OR_MAX_EVENTS events of (bounce << 4 | kind,
  * value) with two diagnostic numbers each. */
@@ -715,6 +806,7 @@ static void trace(const or_scene* s, v3 o, v3 d, uint32_t key, const ropts* op, 
     int nd = dr->nd;
     dc tp = dc_const(1, 1, 1), L = dc_const(0, 0, 0);
     int prev_delta = 1;
+    double prev_pdf = 0.0;   /* solid-angle density of the BSDF sample that produced the ray */
     uint32_t sig = 0u;
     for (uint32_t b = 0; b < op->max_depth; ++b) {
         /* step 2: extend the path to the next scattering point */
@@ -734,9 +826,16 @@ static void trace(const or_scene* s, v3 o, v3 d, uint32_t key, const ropts* op, 
         int64_t mi = s->mat[tri];
         const omat* m = &s->mats[mi];
         int front = dot(d, ng) < 0.0;
-        /* step 3: accumulate emitted radiance */
+        /* step 3: accumulate emitted radiance.  A listed light hit by a BSDF sample after a
+         * non-delta vertex is left to NEE, or with MIS weighted against the density with which NEE
+         * would have drawn this point: (1 / total light area) * t^2 / cos at the light. */
         if (front && (!s->is_light[tri] || b == 0 || prev_delta))
             L = dc_add(L, dc_mul(tp, mat_emission(s, mi, dr), nd), nd);
+        else if (front && op->mis) {
+            double p_light = t * t / (-dot(d, ng) * s->light_area);
+            double w = power_heuristic(prev_pdf, p_light);
+            L = dc_add(L, dc_scale(dc_mul(tp, mat_emission(s, mi, dr), nd), w, nd), nd);
+        }
         if (b + 1 == op->max_depth) break;
         v3 wo = scl(d, -1.0);
         v3 n = front ? ng : scl(ng, -1.0);
@@ -774,6 +873,7 @@ static void trace(const or_scene* s, v3 o, v3 d, uint32_t key, const ropts* op, 
                 if (vis) {
                     dc f = bsdf_eval(m, a, n, wo, wi, nd);
                     double g = cx * cl * s->light_area / dist2;
+                    if (op->mis) g *= power_heuristic(dist2 / (cl * s->light_area), bsdf_pdf(m, n, wo, wi));
                     L = dc_add(L, dc_scale(dc_mul(dc_mul(tp, f, nd), mat_emission(s, s->mat[lt], dr), nd), g, nd), nd);
                 }
             }
@@ -788,6 +888,7 @@ static void trace(const or_scene* s, v3 o, v3 d, uint32_t key, const ropts* op, 
         if (!bs.valid) break;
         tp = dc_mul(tp, bs.weight, nd);
         prev_delta = bs.delta;
+        prev_pdf = bs.delta ? 0.0 : bsdf_pdf(m, n, wo, bs.wi);
         if (b >= op->rr_start) {
             double q;
             if (op->rr_fixed > 0.0) q = op->rr_fixed;
@@ -829,10 +930,10 @@ static ocam make_cam(const float* eye, const float* target, const float* up, flo
 }
 
 /* Step 1: camera ray through (x + u0, y + u1) of a pinhole camera; y = 0 is the top row. */
-static void camera_ray(const ocam* c, uint32_t pixel, uint32_t key, v3* o, v3* d) {
+static void camera_ray(const ocam* c, uint32_t pixel, double u0, double u1, v3* o, v3* d) {
     uint32_t x = pixel % c->W, y = pixel / c->W;
-    double sx = ((double)x + or_u01(key, 0, D_JX)) / (double)c->W;
-    double sy = ((double)y + or_u01(key, 0, D_JY)) / (double)c->H;
+    double sx = ((double)x + u0) / (double)c->W;
+    double sy = ((double)y + u1) / (double)c->H;
     *o = c->eye;
     *d = nrm(sub(add(scl(c->u, (2.0 * sx - 1.0) * c->tw), scl(c->v, (1.0 - 2.0 * sy) * c->th)), c->w));
 }
@@ -849,19 +950,21 @@ static int nthreads(int want) {
 /* Per-path radiance (and tangents) for the listed path ids (path = pixel * spp + sample). */
 void or_render_paths(const or_scene* s, const float* eye, const float* target, const float* up, float vfov_deg,
                      uint32_t W, uint32_t H, uint32_t spp, uint32_t max_depth, uint64_t seed, uint32_t rr_start,
-                     double rr_fixed, int use_bvh, const uint64_t* path_ids, int64_t n, int nd,
+                     double rr_fixed, uint32_t opts, int use_bvh, const uint64_t* path_ids, int64_t n, int nd,
                      const double* dir_a, const double* dir_e, int n_threads, double* L_out, double* dL_out,
                      uint32_t* sig_out, uint64_t* rays_out) {
     ocam cam = make_cam(eye, target, up, vfov_deg, W, H);
-    ropts op = {max_depth, rr_start, rr_fixed, use_bvh};
+    ropts op = {max_depth, rr_start, rr_fixed, use_bvh, (opts & OR_OPT_MIS) != 0};
     dirs_t dr = {nd > OR_MAXK ? OR_MAXK : nd, s->n_mats, dir_a, dir_e};
     uint64_t r0 = 0, r1 = 0;
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads(n_threads)) reduction(+ : r0, r1)
     for (int64_t i = 0; i < n; ++i) {
         uint32_t pixel = (uint32_t)(path_ids[i] / spp), sample = (uint32_t)(path_ids[i] % spp);
         uint32_t key = or_path_key(seed, pixel, sample);
+        double u0, u1;
+        pixel_jitter(opts & OR_OPT_HALTON, seed, pixel, sample, key, &u0, &u1);
         v3 o, d;
-        camera_ray(&cam, pixel, key, &o, &d);
+        camera_ray(&cam, pixel, u0, u1, &o, &d);
         dc L;
         uint32_t sig;
         uint64_t rays[2] = {0, 0};
@@ -880,10 +983,10 @@ void or_render_paths(const or_scene* s, const float* eye, const float* target, c
 /* Image of the listed pixels: mean over spp samples, summed in increasing sample order. */
 void or_render_pixels(const or_scene* s, const float* eye, const float* target, const float* up, float vfov_deg,
                       uint32_t W, uint32_t H, uint32_t spp, uint32_t max_depth, uint64_t seed, uint32_t rr_start,
-                      double rr_fixed, int use_bvh, const uint32_t* pixels, int64_t n, int n_threads,
+                      double rr_fixed, uint32_t opts, int use_bvh, const uint32_t* pixels, int64_t n, int n_threads,
                       double* img_out, uint64_t* rays_out) {
     ocam cam = make_cam(eye, target, up, vfov_deg, W, H);
-    ropts op = {max_depth, rr_start, rr_fixed, use_bvh};
+    ropts op = {max_depth, rr_start, rr_fixed, use_bvh, (opts & OR_OPT_MIS) != 0};
     dirs_t dr = {0, s->n_mats, NULL, NULL};
     uint64_t r0 = 0, r1 = 0;
 #pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads(n_threads)) reduction(+ : r0, r1)
@@ -891,8 +994,10 @@ void or_render_pixels(const or_scene* s, const float* eye, const float* target, 
         double acc[3] = {0, 0, 0};
         for (uint32_t smp = 0; smp < spp; ++smp) {
             uint32_t key = or_path_key(seed, pixels[i], smp);
+            double u0, u1;
+            pixel_jitter(opts & OR_OPT_HALTON, seed, pixels[i], smp, key, &u0, &u1);
             v3 o, d;
-            camera_ray(&cam, pixels[i], key, &o, &d);
+            camera_ray(&cam, pixels[i], u0, u1, &o, &d);
             dc L;
             uint32_t sig;
             uint64_t rays[2] = {0, 0};
@@ -908,9 +1013,9 @@ void or_render_pixels(const or_scene* s, const float* eye, const float* target, 
 
 /* Paths started from explicit rays (closed-form tests): ray i uses path key keys[i]. */
 void or_trace_rays(const or_scene* s, const double* o, const double* d, const uint32_t* keys, int64_t n,
-                   uint32_t max_depth, uint32_t rr_start, double rr_fixed, int use_bvh, int nd,
+                   uint32_t max_depth, uint32_t rr_start, double rr_fixed, uint32_t opts, int use_bvh, int nd,
                    const double* dir_a, const double* dir_e, int n_threads, double* L_out, double* dL_out) {
-    ropts op = {max_depth, rr_start, rr_fixed, use_bvh};
+    ropts op = {max_depth, rr_start, rr_fixed, use_bvh, (opts & OR_OPT_MIS) != 0};
     dirs_t dr = {nd > OR_MAXK ? OR_MAXK : nd, s->n_mats, dir_a, dir_e};
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads(n_threads))
     for (int64_t i = 0; i < n; ++i) {
@@ -930,16 +1035,18 @@ void or_trace_rays(const or_scene* s, const double* o, const double* d, const ui
  * implementations part ways).  ev: n x 64 x 2 u32, pay: n x 64 x 2 f64, n_ev: n. */
 void or_trace_path_events(const or_scene* s, const float* eye, const float* target, const float* up, float vfov_deg,
                           uint32_t W, uint32_t H, uint32_t spp, uint32_t max_depth, uint64_t seed, uint32_t rr_start,
-                          double rr_fixed, const uint64_t* path_ids, int64_t n, uint32_t* ev, double* pay,
+                          double rr_fixed, uint32_t opts, const uint64_t* path_ids, int64_t n, uint32_t* ev, double* pay,
                           uint32_t* n_ev, double* L_out) {
     ocam cam = make_cam(eye, target, up, vfov_deg, W, H);
-    ropts op = {max_depth, rr_start, rr_fixed, 1};
+    ropts op = {max_depth, rr_start, rr_fixed, 1, (opts & OR_OPT_MIS) != 0};
     dirs_t dr = {0, s->n_mats, NULL, NULL};
     for (int64_t i = 0; i < n; ++i) {
         uint32_t pixel = (uint32_t)(path_ids[i] / spp), sample = (uint32_t)(path_ids[i] % spp);
         uint32_t key = or_path_key(seed, pixel, sample);
+        double u0, u1;
+        pixel_jitter(opts & OR_OPT_HALTON, seed, pixel, sample, key, &u0, &u1);
         v3 o, d;
-        camera_ray(&cam, pixel, key, &o, &d);
+        camera_ray(&cam, pixel, u0, u1, &o, &d);
         evlog lg = {ev + (size_t)i * 2 * OR_MAX_EVENTS, pay + (size_t)i * 2 * OR_MAX_EVENTS, 0};
         dc L;
         uint32_t sig;

@@ -5,5 +5,5 @@ The estimator (Eq. 1-3, Sec. 2.2) runs as a megakernel or as a wavefront pipelin
 include/pt.h.  This package holds the ctypes binding (capi), the Python front (tracer), the build
 step (build) and the seeded scene generators (scenes).
 """
-from .tracer import (Scene, autotune_batch, debug_rng, make_camera, make_opts, render_batch,  # noqa: F401
-                     render_differentiable)
+from .tracer import (Progressive, Scene, autotune_batch, debug_rng, make_camera, make_opts,  # noqa: F401
+                     render_batch, render_differentiable)

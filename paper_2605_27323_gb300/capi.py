@@ -18,11 +18,12 @@ STATUS_NAMES = {0: "PT_OK", 1: "PT_ERR_INVALID_ARG", 2: "PT_ERR_OOM", 3: "PT_ERR
                 7: "PT_ERR_UNSUPPORTED"}
 MODE = {"megakernel": 0, "wavefront": 1}
 SORT = {"none": 0, "type": 1, "material": 2}
-FLAG_PROFILE, FLAG_NO_GRAPH, FLAG_MK_STATIC = 1, 2, 4
+FLAG_PROFILE, FLAG_NO_GRAPH, FLAG_MK_STATIC, FLAG_HALTON = 1, 2, 4, 8
 
 # Every function that include/pt.h declares (the symbol-export test checks this list against the
 # header and the shared object).
-EXPORTED = ["pt_scene_create", "pt_scene_set_materials", "pt_render", "pt_render_backward", "pt_render_batch",
+EXPORTED = ["pt_scene_create", "pt_scene_set_materials", "pt_render", "pt_render_progressive", "pt_render_backward",
+            "pt_render_batch",
             "pt_autotune_batch", "pt_trace_closest", "pt_get_stats", "pt_debug_rng", "pt_debug_trace_paths",
             "pt_scene_info", "pt_render_wavefront_static",
             "pt_status_string", "pt_last_error", "pt_scene_destroy"]
@@ -40,7 +41,7 @@ class Camera(C.Structure):
 
 class RenderOpts(C.Structure):
     _fields_ = [("mode", u32), ("rr_start", u32), ("rr_fixed", f32), ("sort_mode", u32), ("block_size", u32),
-                ("flags", u32), ("queue_capacity", u64), ("d_path_sig", vp), ("reserved", u64)]
+                ("flags", u32), ("queue_capacity", u64), ("d_path_sig", vp), ("hybrid_threshold", u64)]
 
 
 class Stats(C.Structure):
@@ -79,6 +80,8 @@ def load(build_if_missing: bool = True):
     L.pt_scene_set_materials.argtypes = [vp, vp, vp, vp]
     L.pt_render.restype = u32
     L.pt_render.argtypes = [vp, P(Camera), u32, u32, u64, P(RenderOpts), vp, vp, vp]
+    L.pt_render_progressive.restype = u32
+    L.pt_render_progressive.argtypes = [vp, P(Camera), u32, u32, u64, u32, P(RenderOpts), vp, vp, vp]
     L.pt_render_backward.restype = u32
     L.pt_render_backward.argtypes = [vp, P(Camera), u32, u32, u64, P(RenderOpts), vp, vp, vp, vp]
     L.pt_render_batch.restype = u32

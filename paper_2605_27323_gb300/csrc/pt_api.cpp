@@ -203,6 +203,7 @@ struct pt_scene {
 
     pt_status ensure_counters() { return counters.ensure(256 + 8 * 132); }
     unsigned long long* next_path() const { return hist() + 130; }
+    unsigned long long* finish_claim() const { return hist() + 131; }
 
     // One allocation carved into the wavefront arrays for `cap` paths per wave.
     pt_status ensure_wf(uint64_t cap) {
@@ -327,9 +328,11 @@ pt_status set_device(const pt_scene* sc) {
     return PT_OK;
 }
 
-// The wavefront pipeline over one scene and camera, waves of `cap` paths (a multiple of spp).
+// The wavefront pipeline over one scene and camera, waves of `cap` paths (a multiple of spp).  With
+// `accum`, each wave's samples continue the per-pixel running sums and img = sum / count.
 pt_status run_wavefront(pt_scene* sc, const pt::DevCamera& cam, const pt::RenderParams& p0, const pt_render_opts& o,
-                        uint64_t n_paths, float* img, float* path_L, uint32_t* sig, cudaStream_t st) {
+                        uint64_t n_paths, float* img, float* path_L, uint32_t* sig, cudaStream_t st,
+                        float* accum = nullptr, uint32_t count = 0) {
     uint64_t cap = o.queue_capacity ? std::min<uint64_t>(o.queue_capacity, n_paths) : n_paths;
     cap = std::max<uint64_t>(cap - cap % p0.spp, p0.spp);
     if (cap >= (1ull << 32)) cap = ((1ull << 32) - (1ull << 20)) / p0.spp * p0.spp;
@@ -376,11 +379,24 @@ pt_status run_wavefront(pt_scene* sc, const pt::DevCamera& cam, const pt::Render
             PT_TRY(sc->ev_end(ev, st));
             PT_CUDA(pt::launch_prepare(st, w, b));
             sc->launches += 4 + (sorted ? 3 : 0);
+            if (o.hybrid_threshold && b + 1 < p.max_depth) {
+                // hybrid: finish the remaining bounces in one kernel if few paths are left
+                const uint32_t thr = (uint32_t)std::min<uint64_t>(o.hybrid_threshold, 0xFFFFFFFFull);
+                pt::Launch lf = launch_for(sc, pt::K_FINISH, 128, 128, st, std::min<uint64_t>(n, thr));
+                PT_TRY(sc->ev_begin(ST_MEGA, st, ev));
+                PT_CUDA(pt::launch_finish(lf, ds, p, w, (int)((b + 1) & 1u), b + 1, thr, sc->finish_claim()));
+                PT_TRY(sc->ev_end(ev, st));
+                sc->launches += 2;
+            }
         }
         (void)lr;
         PT_TRY(sc->ev_begin(ST_REDUCE, st, ev));
-        PT_CUDA(pt::launch_reduce(simple_launch(sc, st, n / p.spp), reinterpret_cast<const float*>(w.L), 4,
-                                  w0 / p.spp, n / p.spp, p.spp, img));
+        if (accum)
+            PT_CUDA(pt::launch_accumulate(simple_launch(sc, st, n / p.spp), reinterpret_cast<const float*>(w.L), 4,
+                                          w0 / p.spp, n / p.spp, p.spp, accum, count, img));
+        else
+            PT_CUDA(pt::launch_reduce(simple_launch(sc, st, n / p.spp), reinterpret_cast<const float*>(w.L), 4,
+                                      w0 / p.spp, n / p.spp, p.spp, img));
         if (path_L) PT_CUDA(pt::launch_copy_L(simple_launch(sc, st, n), w.L, n, path_L + 3 * w0));
         PT_TRY(sc->ev_end(ev, st));
         sc->launches += path_L ? 2 : 1;
@@ -578,6 +594,7 @@ pt_status batch_render(pt_scene* const* scenes, const pt_camera* cams, const uin
     p.max_depth = max_depth;
     p.rr_start = o.rr_start;
     p.rr_fixed = o.rr_fixed;
+    p.sampler = (o.flags & PT_FLAG_HALTON) ? pt::SAMPLER_HALTON_ID : 0u;
     uint32_t n_keys = 0;
     if (o.sort_mode == PT_SORT_TYPE) n_keys = 4;
     if (o.sort_mode == PT_SORT_MATERIAL) n_keys = std::min<uint32_t>(max_mats + 1, pt::kMaxSortKeys);
@@ -645,6 +662,112 @@ pt_status batch_render(pt_scene* const* scenes, const pt_camera* cams, const uin
     PT_CUDA(pt::launch_scale_batch(plain(px_off[n], st), t, px_dev, px_off[n]));
     return PT_OK;
 }
+
+namespace {
+
+// pt_render and pt_render_progressive.  With `accum` the samples are pixel samples
+// sample_offset .. sample_offset + spp - 1, added to the running sums, and the image (if any) is
+// sum / (sample_offset + spp).
+pt_status render_impl(pt_scene* sc, const pt_camera* cam, uint32_t spp, uint32_t max_depth, uint64_t seed,
+                      const pt_render_opts* opts, float* d_out_rgb, float* d_path_L_or_null, void* stream,
+                      uint32_t sample_offset, float* accum) {
+    if (!sc) return fail(PT_ERR_INVALID_ARG, "scene is NULL");
+    if (!d_out_rgb && !accum) return fail(PT_ERR_INVALID_ARG, "output image is NULL");
+    if (spp == 0) return fail(PT_ERR_INVALID_ARG, "spp must be >= 1");
+    if (max_depth > 64) return fail(PT_ERR_INVALID_ARG, "max_depth must be <= 64");
+    if ((uint64_t)sample_offset + spp > 0xFFFFFFFFull) return fail(PT_ERR_INVALID_ARG, "sample_offset + spp overflows 32 bits");
+    pt_render_opts o = opts ? *opts : default_opts();
+    PT_TRY(check_opts(o));
+    pt::DevCamera dc;
+    PT_TRY(make_camera(cam, dc));
+    const uint64_t n_pixels = (uint64_t)cam->width * cam->height;
+    const uint64_t n_paths = n_pixels * spp;
+    if (n_paths >= (1ull << 40)) return fail(PT_ERR_INVALID_ARG, "too many paths");
+    if (d_path_L_or_null && !is_device_ptr(d_path_L_or_null)) return fail(PT_ERR_INVALID_ARG, "path_L must be a device pointer");
+    if (o.d_path_sig && !is_device_ptr(o.d_path_sig)) return fail(PT_ERR_INVALID_ARG, "d_path_sig must be a device pointer");
+    if (accum && !is_device_ptr(accum)) return fail(PT_ERR_INVALID_ARG, "d_accum_rgb must be a device pointer");
+    if (accum && d_out_rgb && !is_device_ptr(d_out_rgb))
+        return fail(PT_ERR_INVALID_ARG, "d_out_rgb must be a device pointer for progressive rendering");
+    std::lock_guard<std::mutex> g(sc->mu);
+    PT_TRY(set_device(sc));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool host_out = d_out_rgb && !is_device_ptr(d_out_rgb);
+    float* img = d_out_rgb;
+    if (host_out) {
+        PT_TRY(sc->img_stage.ensure(n_pixels * 12));
+        img = sc->img_stage.as<float>();
+    }
+    const uint32_t count = sample_offset + spp;
+    sc->profiling = (o.flags & PT_FLAG_PROFILE) != 0;
+    sc->ev_used = 0;
+    sc->last_stream = st;
+    sc->last_mode = o.mode;
+    sc->last_paths = n_paths;
+    sc->launches = 0;
+    PT_CUDA(cudaMemsetAsync(sc->counters.p, 0, sc->counters.bytes, st));
+    PT_CUDA(cudaMemsetAsync(sc->status.p, 0, 4, st));
+    if (accum && sample_offset == 0) PT_CUDA(cudaMemsetAsync(accum, 0, n_pixels * 12, st));
+    pt::RenderParams p;
+    p.seed = seed;
+    p.path_begin = 0;
+    p.spp = spp;
+    p.max_depth = max_depth;
+    p.rr_start = o.rr_start;
+    p.rr_fixed = o.rr_fixed;
+    p.sampler = (o.flags & PT_FLAG_HALTON) ? pt::SAMPLER_HALTON_ID : 0u;
+    p.sample_offset = sample_offset;
+    if (max_depth == 0) {
+        // every sample is black: the sums are unchanged and the image is sum / count
+        if (accum) {
+            size_t ev = 0;
+            PT_TRY(sc->ev_begin(ST_REDUCE, st, ev));
+            PT_CUDA(pt::launch_accumulate(simple_launch(sc, st, n_pixels), nullptr, 3, 0, n_pixels, 0, accum, count, img));
+            PT_TRY(sc->ev_end(ev, st));
+            sc->launches += 1;
+        } else {
+            PT_CUDA(cudaMemsetAsync(img, 0, n_pixels * 12, st));
+        }
+        if (d_path_L_or_null) PT_CUDA(cudaMemsetAsync(d_path_L_or_null, 0, n_paths * 12, st));
+        if (o.d_path_sig) PT_CUDA(cudaMemsetAsync(o.d_path_sig, 0, n_paths * 4, st));
+    } else if (o.mode == PT_MODE_MEGAKERNEL) {
+        float* outL = d_path_L_or_null;
+        if (!outL && (spp > 1 || accum)) {
+            PT_TRY(sc->pathL.ensure(n_paths * 12));
+            outL = sc->pathL.as<float>();
+        }
+        size_t ev = 0;
+        PT_TRY(sc->ev_begin(ST_MEGA, st, ev));
+        if (o.flags & PT_FLAG_MK_STATIC) {
+            pt::Launch l = launch_for(sc, pt::K_MEGA, o.block_size, 128, st, n_paths);
+            PT_CUDA(pt::launch_megakernel(l, sc->view(), dc, p, n_paths, outL, img, o.d_path_sig, sc->rays()));
+        } else {
+            pt::Launch l = launch_for(sc, pt::K_MEGA_REGEN, o.block_size ? std::min<uint32_t>(o.block_size, 128) : 128, 128,
+                                      st, n_paths);
+            PT_CUDA(pt::launch_megakernel_regen(l, sc->view(), dc, p, n_paths, outL, img, o.d_path_sig, sc->rays(),
+                                                sc->next_path()));
+        }
+        PT_TRY(sc->ev_end(ev, st));
+        sc->launches += 1;
+        if (outL) {
+            sc->launches += 1;
+            PT_TRY(sc->ev_begin(ST_REDUCE, st, ev));
+            if (accum)
+                PT_CUDA(pt::launch_accumulate(simple_launch(sc, st, n_pixels), outL, 3, 0, n_pixels, spp, accum, count, img));
+            else
+                PT_CUDA(pt::launch_reduce(simple_launch(sc, st, n_pixels), outL, 3, 0, n_pixels, spp, img));
+            PT_TRY(sc->ev_end(ev, st));
+        }
+    } else {
+        PT_TRY(run_wavefront(sc, dc, p, o, n_paths, img, d_path_L_or_null, o.d_path_sig, st, accum, count));
+    }
+    if (host_out) {
+        PT_CUDA(cudaMemcpyAsync(d_out_rgb, img, n_pixels * 12, cudaMemcpyDeviceToHost, st));
+        PT_CUDA(cudaStreamSynchronize(st));
+    }
+    return PT_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -830,80 +953,16 @@ pt_status pt_scene_info(const pt_scene* sc, uint64_t* n_tris, uint64_t* n_nodes,
 
 pt_status pt_render(pt_scene* sc, const pt_camera* cam, uint32_t spp, uint32_t max_depth, uint64_t seed,
                     const pt_render_opts* opts, float* d_out_rgb, float* d_path_L_or_null, void* stream) {
-    if (!sc) return fail(PT_ERR_INVALID_ARG, "scene is NULL");
     if (!d_out_rgb) return fail(PT_ERR_INVALID_ARG, "output image is NULL");
-    if (spp == 0) return fail(PT_ERR_INVALID_ARG, "spp must be >= 1");
-    if (max_depth > 64) return fail(PT_ERR_INVALID_ARG, "max_depth must be <= 64");
-    pt_render_opts o = opts ? *opts : default_opts();
-    PT_TRY(check_opts(o));
-    pt::DevCamera dc;
-    PT_TRY(make_camera(cam, dc));
-    const uint64_t n_pixels = (uint64_t)cam->width * cam->height;
-    const uint64_t n_paths = n_pixels * spp;
-    if (n_paths >= (1ull << 40)) return fail(PT_ERR_INVALID_ARG, "too many paths");
-    if (d_path_L_or_null && !is_device_ptr(d_path_L_or_null)) return fail(PT_ERR_INVALID_ARG, "path_L must be a device pointer");
-    if (o.d_path_sig && !is_device_ptr(o.d_path_sig)) return fail(PT_ERR_INVALID_ARG, "d_path_sig must be a device pointer");
-    std::lock_guard<std::mutex> g(sc->mu);
-    PT_TRY(set_device(sc));
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const bool host_out = !is_device_ptr(d_out_rgb);
-    float* img = d_out_rgb;
-    if (host_out) {
-        PT_TRY(sc->img_stage.ensure(n_pixels * 12));
-        img = sc->img_stage.as<float>();
-    }
-    sc->profiling = (o.flags & PT_FLAG_PROFILE) != 0;
-    sc->ev_used = 0;
-    sc->last_stream = st;
-    sc->last_mode = o.mode;
-    sc->last_paths = n_paths;
-    sc->launches = 0;
-    PT_CUDA(cudaMemsetAsync(sc->counters.p, 0, sc->counters.bytes, st));
-    PT_CUDA(cudaMemsetAsync(sc->status.p, 0, 4, st));
-    pt::RenderParams p;
-    p.seed = seed;
-    p.path_begin = 0;
-    p.spp = spp;
-    p.max_depth = max_depth;
-    p.rr_start = o.rr_start;
-    p.rr_fixed = o.rr_fixed;
-    if (max_depth == 0) {
-        PT_CUDA(cudaMemsetAsync(img, 0, n_pixels * 12, st));
-        if (d_path_L_or_null) PT_CUDA(cudaMemsetAsync(d_path_L_or_null, 0, n_paths * 12, st));
-        if (o.d_path_sig) PT_CUDA(cudaMemsetAsync(o.d_path_sig, 0, n_paths * 4, st));
-    } else if (o.mode == PT_MODE_MEGAKERNEL) {
-        float* outL = d_path_L_or_null;
-        if (!outL && spp > 1) {
-            PT_TRY(sc->pathL.ensure(n_paths * 12));
-            outL = sc->pathL.as<float>();
-        }
-        size_t ev = 0;
-        PT_TRY(sc->ev_begin(ST_MEGA, st, ev));
-        if (o.flags & PT_FLAG_MK_STATIC) {
-            pt::Launch l = launch_for(sc, pt::K_MEGA, o.block_size, 128, st, n_paths);
-            PT_CUDA(pt::launch_megakernel(l, sc->view(), dc, p, n_paths, outL, img, o.d_path_sig, sc->rays()));
-        } else {
-            pt::Launch l = launch_for(sc, pt::K_MEGA_REGEN, o.block_size ? std::min<uint32_t>(o.block_size, 128) : 128, 128,
-                                      st, n_paths);
-            PT_CUDA(pt::launch_megakernel_regen(l, sc->view(), dc, p, n_paths, outL, img, o.d_path_sig, sc->rays(),
-                                                sc->next_path()));
-        }
-        PT_TRY(sc->ev_end(ev, st));
-        sc->launches += 1;
-        if (outL) {
-            sc->launches += 1;
-            PT_TRY(sc->ev_begin(ST_REDUCE, st, ev));
-            PT_CUDA(pt::launch_reduce(simple_launch(sc, st, n_pixels), outL, 3, 0, n_pixels, spp, img));
-            PT_TRY(sc->ev_end(ev, st));
-        }
-    } else {
-        PT_TRY(run_wavefront(sc, dc, p, o, n_paths, img, d_path_L_or_null, o.d_path_sig, st));
-    }
-    if (host_out) {
-        PT_CUDA(cudaMemcpyAsync(d_out_rgb, img, n_pixels * 12, cudaMemcpyDeviceToHost, st));
-        PT_CUDA(cudaStreamSynchronize(st));
-    }
-    return PT_OK;
+    return render_impl(sc, cam, spp, max_depth, seed, opts, d_out_rgb, d_path_L_or_null, stream, 0, nullptr);
+}
+
+pt_status pt_render_progressive(pt_scene* sc, const pt_camera* cam, uint32_t spp, uint32_t max_depth, uint64_t seed,
+                                uint32_t sample_offset, const pt_render_opts* opts, float* d_accum_rgb,
+                                float* d_out_rgb_or_null, void* stream) {
+    if (!d_accum_rgb) return fail(PT_ERR_INVALID_ARG, "d_accum_rgb is NULL");
+    return render_impl(sc, cam, spp, max_depth, seed, opts, d_out_rgb_or_null, nullptr, stream, sample_offset,
+                       d_accum_rgb);
 }
 
 pt_status pt_render_backward(pt_scene* sc, const pt_camera* cam, uint32_t spp, uint32_t max_depth, uint64_t seed,
@@ -947,6 +1006,7 @@ pt_status pt_render_backward(pt_scene* sc, const pt_camera* cam, uint32_t spp, u
     p.max_depth = max_depth;
     p.rr_start = o.rr_start;
     p.rr_fixed = o.rr_fixed;
+    p.sampler = (o.flags & PT_FLAG_HALTON) ? pt::SAMPLER_HALTON_ID : 0u;
     size_t ev = 0;
     PT_TRY(sc->ev_begin(ST_ADJOINT, st, ev));
     if (o.mode == PT_MODE_MEGAKERNEL) {
@@ -1047,6 +1107,7 @@ pt_status pt_debug_trace_paths(pt_scene* sc, const pt_camera* cam, uint32_t spp,
     p.max_depth = max_depth;
     p.rr_start = o.rr_start;
     p.rr_fixed = o.rr_fixed;
+    p.sampler = (o.flags & PT_FLAG_HALTON) ? pt::SAMPLER_HALTON_ID : 0u;
     PT_CUDA(pt::launch_debug_paths(st, sc->view(), dc, p, reinterpret_cast<const unsigned long long*>(d_path_ids), n,
                                    d_events, d_payload, d_n_events, d_path_L));
     return PT_OK;

@@ -63,6 +63,7 @@ __device__ __forceinline__ float u01(uint32_t key, uint32_t bounce, uint32_t dim
     return (float)(h >> 8) * 5.9604644775390625e-8f;
 }
 enum : uint32_t { D_JX = 0, D_JY = 1, D_LIGHT = 2, D_LU = 3, D_LV = 4, D_LOBE = 5, D_DIR0 = 6, D_DIR1 = 7, D_RR = 8 };
+enum : uint32_t { SAMPLER_PCG = 0, SAMPLER_HALTON = SAMPLER_HALTON_ID };
 
 // Branch signature event (order-free XOR of per-event hashes; testing aid).
 __device__ __forceinline__ uint32_t sig_event(uint32_t bounce, uint32_t kind, uint32_t value) {
@@ -70,11 +71,41 @@ __device__ __forceinline__ uint32_t sig_event(uint32_t bounce, uint32_t kind, ui
 }
 
 // ------------------------------------------------------------------ camera (ray generation stage)
+// Sub-pixel jitter (Sec. 2.3).  SAMPLER_PCG: the path's uniforms of bounce 0, dims D_JX / D_JY.
+// SAMPLER_HALTON: the Halton sequence in bases 2 and 3 over the pixel's sample index, shifted per
+// pixel by a Cranley-Patterson rotation modulo 1.  All terms are 24-bit fixed-point fractions, so
+// the value is exact in FP32: phi_2(s) is s bit-reversed (top 24 bits); phi_3(s) reverses the 21
+// base-3 digits of s into R and takes floor(2^24 R / 3^21); the rotation of dim d is the top 24
+// bits of the hash of (seed, pixel, sample 2^32 - 1) for (bounce 0, d).
+__device__ __forceinline__ uint32_t halton3_24(uint32_t s) {
+    uint64_t r = 0;
+#pragma unroll
+    for (int k = 0; k < 21; ++k) {
+        r = r * 3u + s % 3u;
+        s /= 3u;
+    }
+    return (uint32_t)((r << 24) / 10460353203ull);    // 3^21
+}
+
+__device__ __forceinline__ void pixel_jitter(uint32_t sampler, uint64_t seed, uint32_t pixel, uint32_t sample,
+                                             uint32_t key, float& u0, float& u1) {
+    if (sampler == SAMPLER_HALTON) {
+        const uint32_t kp = path_key(seed, pixel, 0xFFFFFFFFu);
+        const uint32_t r0 = pcg_hash(kp ^ pcg_hash(D_JX)) >> 8, r1 = pcg_hash(kp ^ pcg_hash(D_JY)) >> 8;
+        u0 = (float)(((__brev(sample) >> 8) + r0) & 0xFFFFFFu) * 5.9604644775390625e-8f;
+        u1 = (float)((halton3_24(sample) + r1) & 0xFFFFFFu) * 5.9604644775390625e-8f;
+    } else {
+        u0 = u01(key, 0, D_JX);
+        u1 = u01(key, 0, D_JY);
+    }
+}
+
 // Pinhole ray through (x + u0, y + u1); row 0 at the top (Sec. 2.3 ray generation, Sec. 2.2 step 1).
-__device__ __forceinline__ void camera_ray(const DevCamera& c, uint32_t pixel, uint32_t key, float3& o, float3& d) {
+__device__ __forceinline__ void camera_ray(const DevCamera& c, uint32_t pixel, float u0, float u1, float3& o,
+                                           float3& d) {
     uint32_t y = pixel / c.W, x = pixel - y * c.W;
-    float sx = ((float)x + u01(key, 0, D_JX)) / (float)c.W;
-    float sy = ((float)y + u01(key, 0, D_JY)) / (float)c.H;
+    float sx = ((float)x + u0) / (float)c.W;
+    float sy = ((float)y + u1) / (float)c.H;
     float a = 2.0f * sx - 1.0f, b = 1.0f - 2.0f * sy;
     o = f3(c.ex, c.ey, c.ez);
     d = normalize(f3(c.ux, c.uy, c.uz) * a + f3(c.vx, c.vy, c.vz) * b - f3(c.wx, c.wy, c.wz));

@@ -68,10 +68,12 @@ __device__ __forceinline__ float3 mk_path(const DevScene& s, const DevCamera& c,
                                           Rec& rec, unsigned long long& n_ext, unsigned long long& n_shd) {
     const float3 env = f3(s.env_r, s.env_g, s.env_b);
     const uint32_t pixel = (uint32_t)(path / p.spp);
-    const uint32_t sample = (uint32_t)(path - (uint64_t)pixel * p.spp);
+    const uint32_t sample = p.sample_offset + (uint32_t)(path - (uint64_t)pixel * p.spp);
     const uint32_t key = path_key(p.seed, pixel, sample);
     float3 o, d;
-    camera_ray(c, pixel, key, o, d);                           // step 1
+    float u0, u1;
+    pixel_jitter(p.sampler, p.seed, pixel, sample, key, u0, u1);
+    camera_ray(c, pixel, u0, u1, o, d);                        // step 1
     float3 tp = f3(1.f, 1.f, 1.f), L = f3(0.f, 0.f, 0.f);
     bool prev_delta = true;
     for (uint32_t b = 0; b < p.max_depth; ++b) {
@@ -138,6 +140,46 @@ __global__ void __launch_bounds__(256) k_megakernel(DevScene s, DevCamera c, Ren
     warp_add_u64(rays + 1, n_shd);
 }
 
+// One bounce of a path held in registers (extend, shade, shadow evaluation), the loop body of the
+// regenerating megakernel and of the wavefront's continuation kernel.  Returns true when the path
+// ends; otherwise the state has moved to bounce b + 1.
+template <bool SIG>
+__device__ __forceinline__ bool mk_bounce(const DevScene& s, const RenderParams& p, float3 env, uint32_t key,
+                                          uint32_t& b, float3& o, float3& d, float3& tp, bool& prev_delta, float3& L,
+                                          uint32_t& sg, unsigned long long& n_ext, unsigned long long& n_shd) {
+    ++n_ext;
+    Hit h = trace_closest(s, o, d);
+    if (h.tri == kMiss) {
+        L = add_rn(L, mul_rn(tp, env));
+        if (SIG) sg ^= sig_event(b, 0, kMiss);
+        return true;
+    }
+    Vertex V = shade_vertex(s, p, key, b, o, d, tp, prev_delta, h.t, h.tri);
+    if (SIG) sg ^= sig_event(b, 0, V.prim);
+    if (V.emit_counted) L = add_rn(L, V.emit);
+    if (V.last) return true;
+    if (V.nee) {
+        uint32_t vis = 0;
+        if (V.cast) {
+            ++n_shd;
+            vis = trace_any(s, V.s_o, V.s_d, V.s_tmax) ? 0u : 1u;
+            if (vis) L = add_rn(L, V.contrib);
+        }
+        if (SIG) sg ^= sig_event(b, 1, (V.light_j << 2) | ((uint32_t)V.cast << 1) | vis);
+    }
+    if (SIG) {
+        sg ^= sig_event(b, 2, V.bsdf_code);
+        if (V.rr >= 0) sg ^= sig_event(b, 3, (uint32_t)V.rr);
+    }
+    if (!V.cont) return true;
+    o = V.no;
+    d = V.nd;
+    tp = V.ntp;
+    prev_delta = V.delta;
+    ++b;
+    return false;
+}
+
 // Persistent megakernel with path regeneration.  Each thread still traces one path at a time from
 // its camera ray to termination, one bounce per loop iteration; a lane whose path ended claims the
 // next path id (warp-aggregated atomic on a device counter) instead of idling until the longest
@@ -170,9 +212,11 @@ __global__ void __launch_bounds__(128, 8) k_megakernel_regen(DevScene s, DevCame
                 if (i < n_paths) {
                     const uint64_t path = p.path_begin + i;
                     pixel = (uint32_t)(path / p.spp);
-                    const uint32_t sample = (uint32_t)(path - (uint64_t)pixel * p.spp);
+                    const uint32_t sample = p.sample_offset + (uint32_t)(path - (uint64_t)pixel * p.spp);
                     key = path_key(p.seed, pixel, sample);
-                    camera_ray(c, pixel, key, o, d);
+                    float u0, u1;
+                    pixel_jitter(p.sampler, p.seed, pixel, sample, key, u0, u1);
+                    camera_ray(c, pixel, u0, u1, o, d);
                     tp = f3(1.f, 1.f, 1.f);
                     L = f3(0.f, 0.f, 0.f);
                     prev_delta = true;
@@ -186,44 +230,7 @@ __global__ void __launch_bounds__(128, 8) k_megakernel_regen(DevScene s, DevCame
         }
         if (!__any_sync(0xFFFFFFFFu, active)) break;
         if (active) {
-            bool end = false;
-            ++n_ext;
-            Hit h = trace_closest(s, o, d);
-            if (h.tri == kMiss) {
-                L = add_rn(L, mul_rn(tp, env));
-                if (SIG) sg ^= sig_event(b, 0, kMiss);
-                end = true;
-            } else {
-                Vertex V = shade_vertex(s, p, key, b, o, d, tp, prev_delta, h.t, h.tri);
-                if (SIG) sg ^= sig_event(b, 0, V.prim);
-                if (V.emit_counted) L = add_rn(L, V.emit);
-                if (V.last) {
-                    end = true;
-                } else {
-                    if (V.nee) {
-                        uint32_t vis = 0;
-                        if (V.cast) {
-                            ++n_shd;
-                            vis = trace_any(s, V.s_o, V.s_d, V.s_tmax) ? 0u : 1u;
-                            if (vis) L = add_rn(L, V.contrib);
-                        }
-                        if (SIG) sg ^= sig_event(b, 1, (V.light_j << 2) | ((uint32_t)V.cast << 1) | vis);
-                    }
-                    if (SIG) {
-                        sg ^= sig_event(b, 2, V.bsdf_code);
-                        if (V.rr >= 0) sg ^= sig_event(b, 3, (uint32_t)V.rr);
-                    }
-                    if (V.cont) {
-                        o = V.no;
-                        d = V.nd;
-                        tp = V.ntp;
-                        prev_delta = V.delta;
-                        ++b;
-                    } else {
-                        end = true;
-                    }
-                }
-            }
+            const bool end = mk_bounce<SIG>(s, p, env, key, b, o, d, tp, prev_delta, L, sg, n_ext, n_shd);
             if (end) {
                 if (out_L) {
                     out_L[3 * i] = L.x;
@@ -280,7 +287,7 @@ struct SingleSrc {
         PathLoc l;
         l.path = base + pid;
         l.pixel = (uint32_t)(l.path / p.spp);
-        l.sample = (uint32_t)(l.path - (uint64_t)l.pixel * p.spp);
+        l.sample = p.sample_offset + (uint32_t)(l.path - (uint64_t)l.pixel * p.spp);
         l.sid = 0;
         return l;
     }
@@ -360,7 +367,9 @@ __global__ void __launch_bounds__(256) k_raygen(Src src, uint64_t base, uint32_t
         const RenderParams p = src.params(l.sid);
         const uint32_t key = path_key(p.seed, l.pixel, l.sample);
         float3 o, d;
-        camera_ray(src.camera(l.sid), l.pixel, key, o, d);
+        float u0, u1;
+        pixel_jitter(p.sampler, p.seed, l.pixel, l.sample, key, u0, u1);
+        camera_ray(src.camera(l.sid), l.pixel, u0, u1, o, d);
         w.q_o[0][i] = f4(o, __uint_as_float(i));
         w.q_d[0][i] = f4(d, __uint_as_float(src.ray_tag(l.sid, 1u)));   // previous vertex "delta": the camera
         w.q_tp[0][i] = make_float4(1.f, 1.f, 1.f, 0.f);
@@ -567,6 +576,83 @@ __global__ void __launch_bounds__(256) k_shadow(Src src, WfBuffers w, uint32_t b
     }
 }
 
+// ---- hybrid wavefront / megakernel (the hybrid of the paper's future work, Sec. 5): once the
+// active count entering a bounce is at most `threshold`, one persistent kernel finishes every
+// remaining path in registers (the megakernel's loop body, lanes claiming queue entries as they
+// free up) instead of running the remaining bounces as sparse wavefront stages.  The decision is
+// taken on the device; k_finish_commit then empties the queue so the remaining stage launches find
+// no work.  The arithmetic per path is the same as in the wavefront stages, so images are identical.
+template <bool SIG>
+__global__ void __launch_bounds__(128, 8) k_finish(SingleSrc src, WfBuffers w, int in, uint32_t b0, uint32_t threshold,
+                                                  unsigned long long* __restrict__ claim) {
+    __shared__ unsigned int h_s[128];     // [b]: extension rays, [64 + b]: shadow rays of bounce b
+    const uint32_t n = min(w.counts[0], w.capacity);
+    if (n == 0u || n > threshold) return;  // the same value for every thread of the grid
+    for (uint32_t k = threadIdx.x; k < 128u; k += blockDim.x) h_s[k] = 0u;
+    __syncthreads();
+    const DevScene& s = src.s;
+    const RenderParams& p = src.p;
+    const float3 env = f3(s.env_r, s.env_g, s.env_b);
+    unsigned long long n_ext = 0, n_shd = 0;
+    bool active = false, exhausted = false;
+    uint32_t pid = 0, key = 0, b = 0, sg = 0;
+    uint64_t path = 0;
+    float3 o = f3(0.f, 0.f, 0.f), d = o, tp = o, L = o;
+    bool prev_delta = true;
+    while (true) {
+        const bool want = !active && !exhausted;
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, want);
+        if (m) {
+            const uint32_t leader = __ffs(m) - 1u;
+            unsigned long long first = 0;
+            if (lane_id() == leader) first = atomicAdd(claim, (unsigned long long)__popc(m));
+            first = __shfl_sync(0xFFFFFFFFu, first, leader);
+            if (want) {
+                const uint64_t j = first + (uint64_t)__popc(m & ((1u << lane_id()) - 1u));
+                if (j < n) {
+                    const float4 o4 = w.q_o[in][j], d4 = w.q_d[in][j], tp4 = w.q_tp[in][j];
+                    pid = __float_as_uint(o4.w);
+                    const PathLoc l = src.locate(p.path_begin, pid);
+                    path = l.path;
+                    key = path_key(p.seed, l.pixel, l.sample);
+                    o = xyz(o4);
+                    d = xyz(d4);
+                    tp = xyz(tp4);
+                    prev_delta = (__float_as_uint(d4.w) & 1u) != 0u;
+                    L = xyz(w.L[pid]);
+                    b = b0;
+                    sg = 0;
+                    active = true;
+                } else {
+                    exhausted = true;
+                }
+            }
+        }
+        if (!__any_sync(0xFFFFFFFFu, active)) break;
+        if (active) {
+            const uint32_t bb = b;
+            const unsigned long long shd0 = n_shd;
+            atomicAdd(&h_s[bb & 63u], 1u);
+            const bool end = mk_bounce<SIG>(s, p, env, key, b, o, d, tp, prev_delta, L, sg, n_ext, n_shd);
+            if (n_shd != shd0) atomicAdd(&h_s[64u + (bb & 63u)], 1u);
+            if (end) {
+                w.L[pid] = f4(L, 0.f);
+                if (SIG) w.sig[path] ^= sg;
+                active = false;
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < 128u; k += blockDim.x)
+        if (h_s[k]) atomicAdd(&w.hist[k], (unsigned long long)h_s[k]);
+}
+
+__global__ void k_finish_commit(WfBuffers w, uint32_t threshold, unsigned long long* claim) {
+    const uint32_t n = min(w.counts[0], w.capacity);
+    if (n > 0u && n <= threshold) w.counts[0] = 0u;
+    *claim = 0ull;
+}
+
 // ---- wavefront adjoint: shading that records what the reverse pass needs instead of adding
 // radiance (the same shade_vertex decisions, so the replay follows the forward paths exactly).
 __global__ void __launch_bounds__(256, 3) k_shade_adj(SingleSrc src, WfBuffers w, AdjBuffers a, int in, uint32_t b) {
@@ -686,6 +772,36 @@ __global__ void __launch_bounds__(256) k_reduce(const float* __restrict__ L, uin
         o[0] = __fmul_rn(r, inv);
         o[1] = __fmul_rn(g, inv);
         o[2] = __fmul_rn(bl, inv);
+    }
+}
+
+// Progressive accumulation (the running average of Sec. 2.3): add this call's samples of each
+// pixel, in sample order, to the pixel's FP32 running sum and write sum / count (img may be null).
+// Continuing the sum is exactly what the one-call reduce does, so frames of k1, k2, ... samples end
+// at the image of one call with k1 + k2 + ... samples, bit for bit.
+__global__ void __launch_bounds__(256) k_accumulate(const float* __restrict__ L, uint32_t stride_f,
+                                                    uint64_t pixel_begin, uint64_t n_pixels, uint32_t spp,
+                                                    float* __restrict__ sum, uint32_t count, float* __restrict__ img) {
+    const float inv = 1.0f / (float)count;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t px = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; px < n_pixels; px += stride) {
+        float* a = sum + 3 * (pixel_begin + px);
+        float r = a[0], g = a[1], bl = a[2];
+        const float* q = L + px * spp * stride_f;
+        for (uint32_t smp = 0; smp < spp; ++smp) {
+            r = __fadd_rn(r, q[smp * stride_f]);
+            g = __fadd_rn(g, q[smp * stride_f + 1]);
+            bl = __fadd_rn(bl, q[smp * stride_f + 2]);
+        }
+        a[0] = r;
+        a[1] = g;
+        a[2] = bl;
+        if (img) {
+            float* o = img + 3 * (pixel_begin + px);
+            o[0] = __fmul_rn(r, inv);
+            o[1] = __fmul_rn(g, inv);
+            o[2] = __fmul_rn(bl, inv);
+        }
     }
 }
 
@@ -831,10 +947,12 @@ __global__ void __launch_bounds__(256) k_adjoint(DevScene s, DevCamera c, Render
         if (i < n_paths) {
             const uint64_t path = p.path_begin + i;
             const uint32_t pixel = (uint32_t)(path / p.spp);
-            const uint32_t sample = (uint32_t)(path - (uint64_t)pixel * p.spp);
+            const uint32_t sample = p.sample_offset + (uint32_t)(path - (uint64_t)pixel * p.spp);
             const uint32_t key = path_key(p.seed, pixel, sample);
             float3 o, d;
-            camera_ray(c, pixel, key, o, d);
+            float u0, u1;
+            pixel_jitter(p.sampler, p.seed, pixel, sample, key, u0, u1);
+            camera_ray(c, pixel, u0, u1, o, d);
             float3 tp = f3(1.f, 1.f, 1.f);
             bool prev_delta = true;
             for (uint32_t b = 0; b < p.max_depth && b < (uint32_t)MAXD; ++b) {
@@ -1083,6 +1201,17 @@ cudaError_t launch_shadow(const Launch& l, const DevScene& s, const RenderParams
     return cudaGetLastError();
 }
 
+cudaError_t launch_finish(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w, int in,
+                          uint32_t b0, uint32_t threshold, unsigned long long* claim) {
+    SingleSrc src{s, DevCamera{}, p};
+    if (w.sig) k_finish<true><<<l.grid, l.block, 0, l.st>>>(src, w, in, b0, threshold, claim);
+    else k_finish<false><<<l.grid, l.block, 0, l.st>>>(src, w, in, b0, threshold, claim);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_finish_commit<<<1, 1, 0, l.st>>>(w, threshold, claim);
+    return cudaGetLastError();
+}
+
 // ---- batched (TableSrc) launchers
 cudaError_t launch_raygen_batch(const Launch& l, const BatchTables& t, const RenderParams& p, uint64_t base, uint32_t n,
                                 const WfBuffers& w) {
@@ -1131,6 +1260,12 @@ cudaError_t launch_prepare(cudaStream_t st, const WfBuffers& w, uint32_t bounce)
 cudaError_t launch_reduce(const Launch& l, const float* L, uint32_t stride, uint64_t pixel_begin, uint64_t n_pixels,
                           uint32_t spp, float* img) {
     k_reduce<<<l.grid, l.block, 0, l.st>>>(L, stride, pixel_begin, n_pixels, spp, img);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(const Launch& l, const float* L, uint32_t stride, uint64_t pixel_begin, uint64_t n_pixels,
+                              uint32_t spp, float* sum, uint32_t count, float* img) {
+    k_accumulate<<<l.grid, l.block, 0, l.st>>>(L, stride, pixel_begin, n_pixels, spp, sum, count, img);
     return cudaGetLastError();
 }
 
@@ -1210,6 +1345,7 @@ int max_blocks_per_sm(int which, int block) {
         case K_ADJOINT: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adjoint<16>, block, 16 * 1024); break;
         case K_SHADE_ADJ: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade_adj, block, 0); break;
         case K_SHADOW_ADJ: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shadow_adj, block, 0); break;
+        case K_FINISH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_finish<false>, block, 0); break;
         default: break;
     }
     return (e == cudaSuccess && nb > 0) ? nb : 1;

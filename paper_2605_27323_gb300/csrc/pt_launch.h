@@ -59,6 +59,13 @@ cudaError_t launch_reduce(const Launch& l, const float* L, uint32_t stride, uint
                           uint32_t spp, float* img);
 // Copy wave-local float4 radiance into the caller's N_p x 3 buffer at path offset `path_begin`.
 cudaError_t launch_copy_L(const Launch& l, const float4* L4, uint64_t n, float* out_L3);
+// sum[px] += the pixel's spp samples (in order); img[px] = sum[px] / count unless img is null
+cudaError_t launch_accumulate(const Launch& l, const float* L, uint32_t stride, uint64_t pixel_begin, uint64_t n_pixels,
+                              uint32_t spp, float* sum, uint32_t count, float* img);
+// Hybrid: finish every active path of the wave in one kernel when at most `threshold` are active
+// entering bounce b0 (queue `in`), then empty the queue; `claim` is a zeroed device u64.
+cudaError_t launch_finish(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w, int in,
+                          uint32_t b0, uint32_t threshold, unsigned long long* claim);
 
 // Path-replay adjoint (one thread per path).  grad_img is H x W x 3.
 cudaError_t launch_adjoint(const Launch& l, const DevScene& s, const DevCamera& c, const RenderParams& p,
@@ -86,6 +93,6 @@ cudaError_t launch_debug_rng(const Launch& l, uint64_t seed, const uint32_t* px,
 int max_blocks_per_sm(int which, int block);   // which: 0 megakernel, 1 extend, 2 shade, 3 shadow, 4 adjoint
 enum { K_MEGA = 0, K_EXTEND = 1, K_SHADE = 2, K_SHADOW = 3, K_ADJOINT = 4, K_EXTEND_BATCH = 5, K_SHADE_BATCH = 6,
        K_SHADOW_BATCH = 7, K_SHADE_ADJ = 8, K_SHADOW_ADJ = 9,
-       K_MEGA_REGEN = 10 };
+       K_MEGA_REGEN = 10, K_FINISH = 11 };
 
 }  // namespace pt

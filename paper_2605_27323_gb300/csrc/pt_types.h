@@ -44,9 +44,12 @@ struct RenderParams {
     uint32_t max_depth;
     uint32_t rr_start;
     float rr_fixed;
+    uint32_t sample_offset = 0;   // sample index of a pixel's first path (progressive accumulation)
+    uint32_t sampler = 0;         // pixel jitter: 0 PCG uniforms, 1 Halton (2,3) + Cranley-Patterson
 };
 
 enum : uint32_t { MAT_LAMBERT = 0, MAT_GGX = 1, MAT_DIELECTRIC = 2 };
+constexpr uint32_t SAMPLER_HALTON_ID = 1;   // RenderParams::sampler value of the Halton jitter
 enum : uint32_t { ST_TRAVERSAL = 1u, ST_QUEUE = 2u, ST_TIMEOUT = 4u };
 
 // Wavefront buffers of one wave (Sec. 2.3 / 3.1): ping-pong ray queues, hit records, sort

@@ -244,6 +244,29 @@ def spheres_scene(seed: int = 0, n_spheres=200, level=4, ground_quads=256, n_lig
     return _scene(b, mats, (0.1, 0.1, 0.1), camera=cam, spp=1, max_depth=5, rr_start=3)
 
 
+def diff_scene(seed: int = 0, width=512, height=512):
+    """Inverse-rendering workload: the procedural spheres geometry with 256 shared materials (254 on
+    the spheres, the ground, the lights), 512x512, 64 spp, depth 6, roulette from bounce 3 with a
+    fixed survival probability 0.9 (so that the estimator is smooth in the parameters)."""
+    sc = spheres_scene(seed=seed, n_materials=256, width=width, height=height)
+    sc.update(spp=64, max_depth=6, rr_start=3, rr_fixed=0.9)
+    return sc
+
+
+def diff_target(sc: dict, seed: int = 7):
+    """Hidden target parameters for diff_scene: albedos redrawn per material type (Lambert
+    U[0.1,0.9]^3, GGX F0 U[0.5,1]^3, dielectric tint unchanged) and emission scaled by U[0.7,1.3]."""
+    rng = np.random.default_rng(seed)
+    t = np.asarray(sc["mat_type"])
+    n = len(t)
+    alb = np.asarray(sc["mat_albedo"], np.float32).reshape(n, 3).copy()
+    lam, ggx = t == LAMBERT, t == GGX
+    alb[lam] = rng.uniform(0.1, 0.9, size=(int(lam.sum()), 3))
+    alb[ggx] = rng.uniform(0.5, 1.0, size=(int(ggx.sum()), 3))
+    em = np.asarray(sc["mat_emission"], np.float32).reshape(n) * rng.uniform(0.7, 1.3, size=n)
+    return alb.astype(np.float32), em.astype(np.float32)
+
+
 def _value_noise(rng, res=256):
     table = rng.uniform(-1.0, 1.0, size=(res, res))
 

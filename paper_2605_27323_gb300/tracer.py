@@ -38,7 +38,7 @@ def make_camera(cam: dict) -> capi.Camera:
 
 
 def make_opts(mode="wavefront", rr_start=3, rr_fixed=0.0, sort="none", block_size=0, queue_capacity=0,
-              profile=False, sig=None, graph=True, mk_static=False) -> capi.RenderOpts:
+              profile=False, sig=None, graph=True, mk_static=False, hybrid=0, sampler="pcg") -> capi.RenderOpts:
     o = capi.RenderOpts()
     o.mode = capi.MODE[mode] if isinstance(mode, str) else int(mode)
     o.rr_start = int(rr_start)
@@ -46,9 +46,12 @@ def make_opts(mode="wavefront", rr_start=3, rr_fixed=0.0, sort="none", block_siz
     o.sort_mode = capi.SORT[sort] if isinstance(sort, str) else int(sort)
     o.block_size = int(block_size)
     o.flags = ((capi.FLAG_PROFILE if profile else 0) | (0 if graph else capi.FLAG_NO_GRAPH)
-               | (capi.FLAG_MK_STATIC if mk_static else 0))
+               | (capi.FLAG_MK_STATIC if mk_static else 0) | (capi.FLAG_HALTON if sampler == "halton" else 0))
+    if sampler not in ("pcg", "halton"):
+        raise ValueError("sampler must be 'pcg' or 'halton'")
     o.queue_capacity = int(queue_capacity)
     o.d_path_sig = sig.data_ptr() if sig is not None else None
+    o.hybrid_threshold = int(hybrid)
     return o
 
 
@@ -133,6 +136,19 @@ class Scene:
             return {"img": img, "path_L": pl, "sig": sg}
         return img
 
+    def render_progressive(self, cam: dict, spp: int, max_depth: int, seed: int, sample_offset: int, accum,
+                           out=None, **opt_kw):
+        """Add samples sample_offset .. sample_offset + spp - 1 of every pixel to the running sums
+        `accum` (H x W x 3 float32 CUDA tensor; zeroed when sample_offset == 0) and return the running
+        mean (into `out` if given)."""
+        torch = _torch()
+        c = make_camera(cam)
+        img = out if out is not None else torch.empty((c.height, c.width, 3), device="cuda", dtype=torch.float32)
+        o = make_opts(**opt_kw)
+        capi.check(self._lib.pt_render_progressive(self.h, C.byref(c), spp, max_depth, seed, int(sample_offset),
+                                                   C.byref(o), _ptr(accum), _ptr(img), _stream(torch)))
+        return img
+
     def backward(self, cam: dict, spp: int, max_depth: int, seed: int, grad_img, g_albedo=None, g_emission=None,
                  **opt_kw):
         """Accumulate d(loss)/d(albedo) (n_mats x 3) and d(loss)/d(emission) (n_mats) for the image
@@ -189,6 +205,34 @@ class Scene:
         d = {k: getattr(s, k) for k, _ in capi.Stats._fields_ if k != "active"}
         d["active"] = list(s.active)[: s.bounces]
         return d
+
+
+class Progressive:
+    """Progressive rendering of one view: each add(spp) renders the next spp samples of every pixel
+    and returns the running mean; state() / Progressive.resume() save and continue the render from
+    (per-pixel sums, sample count)."""
+
+    def __init__(self, scene: Scene, cam: dict, max_depth: int, seed: int = 0, **opt_kw):
+        torch = _torch()
+        self.scene, self.cam, self.max_depth, self.seed, self.opt_kw = scene, cam, max_depth, seed, opt_kw
+        self.sums = torch.zeros((cam["height"], cam["width"], 3), device="cuda", dtype=torch.float32)
+        self.count = 0
+
+    def add(self, spp: int, out=None):
+        img = self.scene.render_progressive(self.cam, spp, self.max_depth, self.seed, self.count, self.sums, out=out,
+                                            **self.opt_kw)
+        self.count += int(spp)
+        return img
+
+    def state(self) -> dict:
+        return {"sums": self.sums.clone(), "count": self.count, "seed": self.seed}
+
+    @classmethod
+    def resume(cls, scene: Scene, cam: dict, max_depth: int, state: dict, **opt_kw) -> "Progressive":
+        p = cls(scene, cam, max_depth, state["seed"], **opt_kw)
+        p.sums.copy_(state["sums"])
+        p.count = int(state["count"])
+        return p
 
 
 def debug_rng(seed: int, pixel, sample, bounce, dim):
