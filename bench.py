@@ -329,6 +329,24 @@ def run_gpu(args):
     hyb = hybrid_sweep(g, cam, spp, depth, (1 << 16, 1 << 18, 1 << 20), max(3, args.steps // 2), flush,
                        dict(mode="wavefront", rr_start=3, sort=args.sort))
     hyb_thr = min(hyb, key=hyb.get)
+    # estimator variants (not in the step): MIS, and the Halton (2,3) + Cranley-Patterson jitter
+    variants = {}
+    for name, kw in (("mis_wavefront", dict(mode="wavefront", mis=True)),
+                     ("mis_megakernel", dict(mode="megakernel", mis=True)),
+                     ("halton_wavefront", dict(mode="wavefront", sampler="halton"))):
+        g.render(cam, spp, depth, 900, rr_start=3, **kw)
+        ms = []
+        for k in range(max(3, args.steps // 2)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.render(cam, spp, depth, 910 + k, rr_start=3, **kw)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            flush.fill_(k & 0xFF)
+        st_v = g.stats()
+        variants[name] = {"ms_per_frame": float(np.mean(ms)),
+                          "mrays_s": (st_v["extension_rays"] + st_v["shadow_rays"]) / (float(np.mean(ms)) * 1e-3) / 1e6}
     out = None
     if rank == 0:
         e2e = measure_e2e(g, cam, spp, depth, grad, args, wf_opts, mk_opts) if world == 1 else None
@@ -347,6 +365,7 @@ def run_gpu(args):
                        "wavefront_over_hybrid": wf_frame / hyb[hyb_thr],
                        "note": "wavefront frame whose remaining bounces run in one persistent kernel once at "
                                "most `threshold` paths are active; same image; not in the step"},
+            "estimator_variants": variants,
             "megakernel_static": {"ms_per_frame": float(np.mean(st_ms)),
                                   "mrays_s": float(np.mean(mk_rays)) / (float(np.mean(st_ms)) * 1e-3) / 1e6,
                                   "note": "one thread per path over all paths (the paper's layout); not in the step"},

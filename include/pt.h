@@ -75,9 +75,14 @@ enum {
     PT_FLAG_NO_GRAPH = 2u,      /* batched wavefront: launch the bounce loop directly, not as a CUDA graph */
     PT_FLAG_MK_STATIC = 4u,     /* megakernel: one thread per path, launched over all paths (the paper's
                                    layout) instead of the persistent kernel with path regeneration */
-    PT_FLAG_HALTON = 8u         /* pixel jitter from the Halton sequence in bases 2 and 3 over the pixel's
+    PT_FLAG_HALTON = 8u,        /* pixel jitter from the Halton sequence in bases 2 and 3 over the pixel's
                                    sample index with a per-pixel Cranley-Patterson rotation (Sec. 2.3),
                                    in 24-bit fixed point; default: the path's PCG uniforms */
+    PT_FLAG_MIS = 16u           /* combine next-event estimation and BSDF-sampled hits on listed lights
+                                   with the power heuristic (Veach 1997) instead of leaving those hits
+                                   to NEE; the expectation is unchanged, the variance on glossy surfaces
+                                   and large lights is lower.  Gradients follow (the weights do not
+                                   depend on albedo or emission). */
 };
 
 typedef struct {
@@ -121,7 +126,7 @@ typedef struct pt_scene pt_scene;
  * with cudaMemcpyAsync on `cuda_stream` (the call returns after the upload is enqueued and the host
  * staging is released, i.e. it synchronises that stream).  n_tris may be 0 (every ray misses).
  * Errors: PT_ERR_INVALID_ARG (NULL pointers with non-zero counts, index out of range, negative or
- * non-finite parameters), PT_ERR_OOM, PT_ERR_CUDA.  The scene is owned by the library until
+ * non-finite parameters, n_mats >= 2^28), PT_ERR_OOM, PT_ERR_CUDA.  The scene is owned by the library until
  * pt_scene_destroy. */
 pt_status pt_scene_create(const float* verts, uint32_t n_verts, const uint32_t* tris, uint32_t n_tris,
                           const uint32_t* tri_material, const pt_material* mats, uint32_t n_mats,

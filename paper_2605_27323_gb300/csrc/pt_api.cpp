@@ -595,6 +595,7 @@ pt_status batch_render(pt_scene* const* scenes, const pt_camera* cams, const uin
     p.rr_start = o.rr_start;
     p.rr_fixed = o.rr_fixed;
     p.sampler = (o.flags & PT_FLAG_HALTON) ? pt::SAMPLER_HALTON_ID : 0u;
+    p.mis = (o.flags & PT_FLAG_MIS) ? 1u : 0u;
     uint32_t n_keys = 0;
     if (o.sort_mode == PT_SORT_TYPE) n_keys = 4;
     if (o.sort_mode == PT_SORT_MATERIAL) n_keys = std::min<uint32_t>(max_mats + 1, pt::kMaxSortKeys);
@@ -715,6 +716,7 @@ pt_status render_impl(pt_scene* sc, const pt_camera* cam, uint32_t spp, uint32_t
     p.rr_start = o.rr_start;
     p.rr_fixed = o.rr_fixed;
     p.sampler = (o.flags & PT_FLAG_HALTON) ? pt::SAMPLER_HALTON_ID : 0u;
+    p.mis = (o.flags & PT_FLAG_MIS) ? 1u : 0u;
     p.sample_offset = sample_offset;
     if (max_depth == 0) {
         // every sample is black: the sums are unchanged and the image is sum / count
@@ -796,6 +798,7 @@ pt_status pt_scene_create(const float* verts, uint32_t n_verts, const uint32_t* 
         return fail(PT_ERR_INVALID_ARG, "verts, tris and tri_material are required when n_tris > 0");
     if (n_mats > 0 && !mats) return fail(PT_ERR_INVALID_ARG, "mats is NULL");
     if (n_tris > 0 && n_mats == 0) return fail(PT_ERR_INVALID_ARG, "n_mats must be > 0 when n_tris > 0");
+    if (n_mats >= (1u << 28)) return fail(PT_ERR_INVALID_ARG, "n_mats must be < 2^28");
     if (n_tris >= (1u << 28)) return fail(PT_ERR_INVALID_ARG, "n_tris must be < 2^28");
     for (uint64_t i = 0; i < 3ull * n_verts; ++i)
         if (!std::isfinite(verts[i])) return fail(PT_ERR_INVALID_ARG, "vertex %llu is not finite", (unsigned long long)(i / 3));
@@ -1007,6 +1010,7 @@ pt_status pt_render_backward(pt_scene* sc, const pt_camera* cam, uint32_t spp, u
     p.rr_start = o.rr_start;
     p.rr_fixed = o.rr_fixed;
     p.sampler = (o.flags & PT_FLAG_HALTON) ? pt::SAMPLER_HALTON_ID : 0u;
+    p.mis = (o.flags & PT_FLAG_MIS) ? 1u : 0u;
     size_t ev = 0;
     PT_TRY(sc->ev_begin(ST_ADJOINT, st, ev));
     if (o.mode == PT_MODE_MEGAKERNEL) {
@@ -1108,6 +1112,7 @@ pt_status pt_debug_trace_paths(pt_scene* sc, const pt_camera* cam, uint32_t spp,
     p.rr_start = o.rr_start;
     p.rr_fixed = o.rr_fixed;
     p.sampler = (o.flags & PT_FLAG_HALTON) ? pt::SAMPLER_HALTON_ID : 0u;
+    p.mis = (o.flags & PT_FLAG_MIS) ? 1u : 0u;
     PT_CUDA(pt::launch_debug_paths(st, sc->view(), dc, p, reinterpret_cast<const unsigned long long*>(d_path_ids), n,
                                    d_events, d_payload, d_n_events, d_path_L));
     return PT_OK;

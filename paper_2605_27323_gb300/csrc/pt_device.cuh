@@ -206,6 +206,28 @@ __device__ __forceinline__ BsdfEval bsdf_eval(const MatV& m, float3 n, float3 wo
     return r;
 }
 
+// Solid-angle density with which bsdf_sample draws wi (non-delta materials; n faces wo), for the
+// multiple-importance weights: Lambert cos(n, wi) / pi; GGX the visible-normal density
+// G1(wo) max(0, wo.h) D(h) / (n.wo) (Heitz 2018) times the reflection Jacobian 1 / (4 wo.h), i.e.
+// G1(wo) D(h) / (4 n.wo).
+__device__ __forceinline__ float bsdf_pdf(const MatV& m, float3 n, float3 wo, float3 wi) {
+    float co = dot(n, wo), ci = dot(n, wi);
+    if (co <= 0.0f || ci <= 0.0f || m.type == MAT_DIELECTRIC) return 0.0f;
+    if (m.type == MAT_LAMBERT) return ci * 0.318309886183791f;
+    float alpha = ggx_alpha(m.roughness);
+    float3 h = normalize(wo + wi);
+    float ch = dot(n, h);
+    float3 nxh = cross(n, h);
+    float g1 = 1.0f / (1.0f + ggx_lambda(alpha, co));
+    return g1 * ggx_D(alpha, ch * ch, dot(nxh, nxh)) / (4.0f * co);
+}
+
+// Power heuristic with exponent 2 (Veach 1997): weight of the strategy with density pa against pb.
+__device__ __forceinline__ float power_heuristic(float pa, float pb) {
+    float a2 = pa * pa, b2 = pb * pb;
+    return a2 + b2 > 0.0f ? a2 / (a2 + b2) : 0.0f;
+}
+
 // Visible-normal sample of GGX in the local frame (n = +z), after Heitz, "Sampling the GGX
 // Distribution of Visible Normals" (JCGT 2018): stretch, sample the projected disk warped toward the
 // visible half, lift to the hemisphere, unstretch.
@@ -326,8 +348,9 @@ __device__ __forceinline__ BsdfSample bsdf_sample(const MatV& m, float3 n, float
 struct Vertex {
     uint32_t mat;           // material id of the hit triangle
     uint32_t prim;          // original triangle id
-    bool emit_counted;      // emission term added (front face and light-list rule)
-    float3 emit;            // tp * Le when counted
+    bool emit_counted;      // emission term added (front face and light-list rule, or MIS)
+    float emit_w;           // its weight: 1, or the MIS weight of a BSDF-sampled light hit
+    float3 emit;            // tp * Le * emit_w when counted
     bool last;              // b == max_depth - 1: stop after emission
     bool nee;               // an NEE light sample was drawn (non-delta material, lights exist)
     float nee_cx, nee_cl;   // the two cosines that decide whether the shadow ray is cast
@@ -347,6 +370,7 @@ struct Vertex {
     int rr;                 // -1: no roulette at this bounce, 0: killed, 1: survived
     float rr_q;             // survival probability used
     float3 no, nd, ntp;     // continuation ray and throughput
+    float pdf;              // solid-angle density of the continuation sample (MIS only; 0 if delta)
 };
 
 // Light index with cdf[j-1] <= u < cdf[j] (first entry whose inclusive cdf exceeds u).
@@ -360,10 +384,13 @@ __device__ __forceinline__ uint32_t pick_light(const DevScene& s, float u) {
     return lo;
 }
 
-// Shade the hit of ray (o, d) at distance t on reordered triangle `tri`.
+// Shade the hit of ray (o, d) at distance t on reordered triangle `tri`.  MIS = false compiles the
+// multiple-importance terms out (the megakernels are instantiated both ways, since the extra code
+// costs them registers); with MIS = true they apply when p.mis is set.
+template <bool MIS = true>
 __device__ __forceinline__ Vertex shade_vertex(const DevScene& s, const RenderParams& p, uint32_t key, uint32_t b,
-                                               float3 o, float3 d, float3 tp, bool prev_delta, float t,
-                                               uint32_t tri) {
+                                               float3 o, float3 d, float3 tp, bool prev_delta, float prev_pdf,
+                                               float t, uint32_t tri) {
     Vertex V;
     const float4* tr = s.tris + 3 * (size_t)tri;
     float4 t0 = __ldg(tr), t1 = __ldg(tr + 1), t2 = __ldg(tr + 2);
@@ -374,9 +401,18 @@ __device__ __forceinline__ Vertex shade_vertex(const DevScene& s, const RenderPa
     float3 x = o + d * t;
     MatV m = load_mat(s.mats, V.mat);
     bool front = dot(d, ng) < 0.0f;
-    // step 3: accumulate emitted radiance (listed lights only at bounce 0 or after a delta bounce)
+    // step 3: accumulate emitted radiance (listed lights only at bounce 0 or after a delta bounce;
+    // with MIS, also after a non-delta bounce, weighted against the density with which NEE would
+    // have drawn this point: (1 / total light area) * t^2 / cos at the light)
     V.emit_counted = front && (!is_light || b == 0 || prev_delta);
-    V.emit = V.emit_counted ? mul_rn(tp, f3(m.emission, m.emission, m.emission)) : f3(0.f, 0.f, 0.f);
+    V.emit_w = 1.0f;
+    if (MIS && !V.emit_counted && front && p.mis) {
+        V.emit_counted = true;
+        V.emit_w = power_heuristic(prev_pdf, t * t / (-dot(d, ng) * s.light_area));
+    }
+    const float Le_w = m.emission * V.emit_w;
+    V.emit = V.emit_counted ? mul_rn(tp, f3(Le_w, Le_w, Le_w)) : f3(0.f, 0.f, 0.f);
+    V.pdf = 0.0f;
     V.last = (b + 1 == p.max_depth);
     V.nee = false;
     V.cast = false;
@@ -423,6 +459,7 @@ __device__ __forceinline__ Vertex shade_vertex(const DevScene& s, const RenderPa
             V.cast = true;
             BsdfEval fe = bsdf_eval(m, n, wo, wi);
             float g = cx * cl * s.light_area / dist2;
+            if (MIS && p.mis) g = g * power_heuristic(dist2 / (cl * s.light_area), bsdf_pdf(m, n, wo, wi));
             MatV lm = load_mat(s.mats, V.light_mat);
             float3 Le = f3(lm.emission, lm.emission, lm.emission);
             V.nee_g = fe.f * g;
@@ -461,6 +498,7 @@ __device__ __forceinline__ Vertex shade_vertex(const DevScene& s, const RenderPa
     V.ntp = ntp;
     V.no = x + n * (eps * bs.side);
     V.nd = bs.wi;
+    if (MIS && p.mis && !bs.delta) V.pdf = bsdf_pdf(m, n, wo, bs.wi);
     return V;
 }
 

@@ -63,7 +63,7 @@ struct LogRec {   // event list with two diagnostic numbers per event (testing a
 };
 
 // One whole path (Sec. 2.2 steps 1-5) in registers: the body of the megakernel.
-template <class Rec>
+template <class Rec, bool MIS>
 __device__ __forceinline__ float3 mk_path(const DevScene& s, const DevCamera& c, const RenderParams& p, uint64_t path,
                                           Rec& rec, unsigned long long& n_ext, unsigned long long& n_shd) {
     const float3 env = f3(s.env_r, s.env_g, s.env_b);
@@ -76,6 +76,7 @@ __device__ __forceinline__ float3 mk_path(const DevScene& s, const DevCamera& c,
     camera_ray(c, pixel, u0, u1, o, d);                        // step 1
     float3 tp = f3(1.f, 1.f, 1.f), L = f3(0.f, 0.f, 0.f);
     bool prev_delta = true;
+    float prev_pdf = 0.f;
     for (uint32_t b = 0; b < p.max_depth; ++b) {
         ++n_ext;
         Hit h = trace_closest(s, o, d);                  // step 2
@@ -84,7 +85,7 @@ __device__ __forceinline__ float3 mk_path(const DevScene& s, const DevCamera& c,
             rec.ev(b, 0, kMiss, __int_as_float(0x7f800000), tp.x);
             break;
         }
-        Vertex V = shade_vertex(s, p, key, b, o, d, tp, prev_delta, h.t, h.tri);
+        Vertex V = shade_vertex<MIS>(s, p, key, b, o, d, tp, prev_delta, prev_pdf, h.t, h.tri);
         rec.ev(b, 0, V.prim, h.t, tp.x);
         if (V.emit_counted) L = add_rn(L, V.emit);             // step 3
         if (V.last) break;
@@ -104,11 +105,12 @@ __device__ __forceinline__ float3 mk_path(const DevScene& s, const DevCamera& c,
         d = V.nd;
         tp = V.ntp;
         prev_delta = V.delta;
+        prev_pdf = V.pdf;
     }
     return L;
 }
 
-template <bool SIG>
+template <bool SIG, bool MIS>
 __global__ void __launch_bounds__(256) k_megakernel(DevScene s, DevCamera c, RenderParams p, uint64_t n_paths,
                                                     float* __restrict__ out_L, float* __restrict__ img,
                                                     uint32_t* __restrict__ sig, unsigned long long* __restrict__ rays) {
@@ -119,11 +121,11 @@ __global__ void __launch_bounds__(256) k_megakernel(DevScene s, DevCamera c, Ren
         float3 L;
         if (SIG) {
             SigRec r;
-            L = mk_path(s, c, p, path, r, n_ext, n_shd);
+            L = mk_path<SigRec, MIS>(s, c, p, path, r, n_ext, n_shd);
             sig[path] = r.sg;
         } else {
             NoRec r;
-            L = mk_path(s, c, p, path, r, n_ext, n_shd);
+            L = mk_path<NoRec, MIS>(s, c, p, path, r, n_ext, n_shd);
         }
         if (out_L) {
             out_L[3 * i] = L.x;
@@ -143,10 +145,11 @@ __global__ void __launch_bounds__(256) k_megakernel(DevScene s, DevCamera c, Ren
 // One bounce of a path held in registers (extend, shade, shadow evaluation), the loop body of the
 // regenerating megakernel and of the wavefront's continuation kernel.  Returns true when the path
 // ends; otherwise the state has moved to bounce b + 1.
-template <bool SIG>
+template <bool SIG, bool MIS>
 __device__ __forceinline__ bool mk_bounce(const DevScene& s, const RenderParams& p, float3 env, uint32_t key,
-                                          uint32_t& b, float3& o, float3& d, float3& tp, bool& prev_delta, float3& L,
-                                          uint32_t& sg, unsigned long long& n_ext, unsigned long long& n_shd) {
+                                          uint32_t& b, float3& o, float3& d, float3& tp, bool& prev_delta,
+                                          float& prev_pdf, float3& L, uint32_t& sg, unsigned long long& n_ext,
+                                          unsigned long long& n_shd) {
     ++n_ext;
     Hit h = trace_closest(s, o, d);
     if (h.tri == kMiss) {
@@ -154,7 +157,7 @@ __device__ __forceinline__ bool mk_bounce(const DevScene& s, const RenderParams&
         if (SIG) sg ^= sig_event(b, 0, kMiss);
         return true;
     }
-    Vertex V = shade_vertex(s, p, key, b, o, d, tp, prev_delta, h.t, h.tri);
+    Vertex V = shade_vertex<MIS>(s, p, key, b, o, d, tp, prev_delta, prev_pdf, h.t, h.tri);
     if (SIG) sg ^= sig_event(b, 0, V.prim);
     if (V.emit_counted) L = add_rn(L, V.emit);
     if (V.last) return true;
@@ -176,6 +179,7 @@ __device__ __forceinline__ bool mk_bounce(const DevScene& s, const RenderParams&
     d = V.nd;
     tp = V.ntp;
     prev_delta = V.delta;
+    prev_pdf = V.pdf;
     ++b;
     return false;
 }
@@ -184,7 +188,7 @@ __device__ __forceinline__ bool mk_bounce(const DevScene& s, const RenderParams&
 // its camera ray to termination, one bounce per loop iteration; a lane whose path ended claims the
 // next path id (warp-aggregated atomic on a device counter) instead of idling until the longest
 // path of its warp finishes.  The per-path arithmetic is that of mk_path, so images are identical.
-template <bool SIG>
+template <bool SIG, bool MIS>
 // Register cap for 8 resident blocks of 128: occupancy outweighs the spills (measured 3.96 -> 3.11 ms
 // per 1080p frame against the uncapped 107 registers).
 __global__ void __launch_bounds__(128, 8) k_megakernel_regen(DevScene s, DevCamera c, RenderParams p, uint64_t n_paths,
@@ -199,6 +203,7 @@ __global__ void __launch_bounds__(128, 8) k_megakernel_regen(DevScene s, DevCame
     uint32_t pixel = 0, key = 0, b = 0, sg = 0;
     float3 o = f3(0.f, 0.f, 0.f), d = o, tp = o, L = o;
     bool prev_delta = true;
+    float prev_pdf = 0.f;
     while (true) {
         const bool want = !active && !exhausted;
         const uint32_t m = __ballot_sync(0xFFFFFFFFu, want);
@@ -220,6 +225,7 @@ __global__ void __launch_bounds__(128, 8) k_megakernel_regen(DevScene s, DevCame
                     tp = f3(1.f, 1.f, 1.f);
                     L = f3(0.f, 0.f, 0.f);
                     prev_delta = true;
+                    prev_pdf = 0.f;
                     b = 0;
                     sg = 0;
                     active = true;
@@ -230,7 +236,7 @@ __global__ void __launch_bounds__(128, 8) k_megakernel_regen(DevScene s, DevCame
         }
         if (!__any_sync(0xFFFFFFFFu, active)) break;
         if (active) {
-            const bool end = mk_bounce<SIG>(s, p, env, key, b, o, d, tp, prev_delta, L, sg, n_ext, n_shd);
+            const bool end = mk_bounce<SIG, MIS>(s, p, env, key, b, o, d, tp, prev_delta, prev_pdf, L, sg, n_ext, n_shd);
             if (end) {
                 if (out_L) {
                     out_L[3 * i] = L.x;
@@ -260,7 +266,7 @@ __global__ void k_debug_paths(DevScene s, DevCamera c, RenderParams p, const uns
     LogRec r;
     r.ev_u = ev_u + (size_t)i * 2 * kMaxEvents;
     r.ev_f = ev_f + (size_t)i * 2 * kMaxEvents;
-    float3 L = mk_path(s, c, p, ids[i], r, a, b);
+    float3 L = mk_path<LogRec, true>(s, c, p, ids[i], r, a, b);
     n_ev[i] = r.n;
     out_L[3 * i] = L.x;
     out_L[3 * i + 1] = L.y;
@@ -499,7 +505,7 @@ __global__ void __launch_bounds__(256, 3) k_shade(Src src, WfBuffers w, int in, 
                 const RenderParams p = src.params(l.sid);
                 const uint32_t key = path_key(p.seed, l.pixel, l.sample);
                 Vertex V = shade_vertex(s, p, key, b, xyz(o4), xyz(d4), tp, (__float_as_uint(d4.w) & 1u) != 0u,
-                                        hh.x, tri);
+                                        tp4.w, hh.x, tri);
                 if (V.emit_counted) {
                     float3 L = add_rn(xyz(w.L[pid]), V.emit);
                     w.L[pid] = f4(L, 0.f);
@@ -525,7 +531,7 @@ __global__ void __launch_bounds__(256, 3) k_shade(Src src, WfBuffers w, int in, 
                         want_ray = true;
                         ro = f4(V.no, __uint_as_float(pid));
                         rd = f4(V.nd, __uint_as_float(src.ray_tag(l.sid, V.delta ? 1u : 0u)));
-                        rtp = f4(V.ntp, 0.f);
+                        rtp = f4(V.ntp, V.pdf);
                     }
                 }
                 if (SIG) w.sig[l.path] ^= sg;
@@ -582,7 +588,7 @@ __global__ void __launch_bounds__(256) k_shadow(Src src, WfBuffers w, uint32_t b
 // free up) instead of running the remaining bounces as sparse wavefront stages.  The decision is
 // taken on the device; k_finish_commit then empties the queue so the remaining stage launches find
 // no work.  The arithmetic per path is the same as in the wavefront stages, so images are identical.
-template <bool SIG>
+template <bool SIG, bool MIS>
 __global__ void __launch_bounds__(128, 8) k_finish(SingleSrc src, WfBuffers w, int in, uint32_t b0, uint32_t threshold,
                                                   unsigned long long* __restrict__ claim) {
     __shared__ unsigned int h_s[128];     // [b]: extension rays, [64 + b]: shadow rays of bounce b
@@ -599,6 +605,7 @@ __global__ void __launch_bounds__(128, 8) k_finish(SingleSrc src, WfBuffers w, i
     uint64_t path = 0;
     float3 o = f3(0.f, 0.f, 0.f), d = o, tp = o, L = o;
     bool prev_delta = true;
+    float prev_pdf = 0.f;
     while (true) {
         const bool want = !active && !exhausted;
         const uint32_t m = __ballot_sync(0xFFFFFFFFu, want);
@@ -619,6 +626,7 @@ __global__ void __launch_bounds__(128, 8) k_finish(SingleSrc src, WfBuffers w, i
                     d = xyz(d4);
                     tp = xyz(tp4);
                     prev_delta = (__float_as_uint(d4.w) & 1u) != 0u;
+                    prev_pdf = tp4.w;
                     L = xyz(w.L[pid]);
                     b = b0;
                     sg = 0;
@@ -633,7 +641,7 @@ __global__ void __launch_bounds__(128, 8) k_finish(SingleSrc src, WfBuffers w, i
             const uint32_t bb = b;
             const unsigned long long shd0 = n_shd;
             atomicAdd(&h_s[bb & 63u], 1u);
-            const bool end = mk_bounce<SIG>(s, p, env, key, b, o, d, tp, prev_delta, L, sg, n_ext, n_shd);
+            const bool end = mk_bounce<SIG, MIS>(s, p, env, key, b, o, d, tp, prev_delta, prev_pdf, L, sg, n_ext, n_shd);
             if (n_shd != shd0) atomicAdd(&h_s[64u + (bb & 63u)], 1u);
             if (end) {
                 w.L[pid] = f4(L, 0.f);
@@ -678,9 +686,9 @@ __global__ void __launch_bounds__(256, 3) k_shade_adj(SingleSrc src, WfBuffers w
                 const RenderParams& p = src.p;
                 const uint32_t key = path_key(p.seed, l.pixel, l.sample);
                 Vertex V = shade_vertex(src.s, p, key, b, xyz(o4), xyz(d4), xyz(tp4), (__float_as_uint(d4.w) & 1u) != 0u,
-                                        hh.x, tri);
+                                        tp4.w, hh.x, tri);
                 uint32_t flags = V.emit_counted ? 4u : 0u;
-                const float Le = V.emit_counted ? __ldg(&src.s.mats[V.mat].emission) : 0.f;
+                const float Le = V.emit_counted ? __ldg(&src.s.mats[V.mat].emission) * V.emit_w : 0.f;
                 float Lj = 0.f;
                 float4 r1 = make_float4(0.f, 0.f, 0.f, 0.f), r2 = r1;
                 if (!V.last) {
@@ -698,14 +706,14 @@ __global__ void __launch_bounds__(256, 3) k_shade_adj(SingleSrc src, WfBuffers w
                         r1 = f4(V.w, V.dwa.x);
                         ro = f4(V.no, __uint_as_float(pid));
                         rd = f4(V.nd, __uint_as_float(V.delta ? 1u : 0u));
-                        rtp = f4(V.ntp, 0.f);
+                        rtp = f4(V.ntp, V.pdf);
                     }
                 }
                 float4* r = a.rec + 4 * ((size_t)b * cap + pid);
                 r[0] = make_float4(tp4.x, tp4.y, tp4.z, __uint_as_float(V.mat));
                 r[1] = r1;
                 r[2] = r2;
-                r[3] = make_float4(Le, Lj, __uint_as_float(V.light_mat), __uint_as_float(flags));
+                r[3] = make_float4(Le, Lj, V.emit_w, __uint_as_float(flags | (V.light_mat << 4)));
                 if (!V.cont || V.last) a.pend[pid] = b + 1u;
             }
         }
@@ -876,7 +884,8 @@ struct AdjRec {
     float3 dwa;      // d w / d albedo
     float3 nee_g;    // f G A of a visible NEE sample (0 otherwise)
     float3 nee_dfa;  // d(f G A Le_light) / d albedo
-    float Le;        // emission of the hit material when its term is counted
+    float Le;        // emission of the hit material times its weight when its term is counted
+    float we;        // that weight (1, or the MIS weight of a BSDF-sampled light hit)
     float Lj;        // emission of the sampled light's material
     uint32_t mat, lmat;
     uint32_t flags;  // 1: continues, 2: NEE visible, 4: emission counted
@@ -955,18 +964,20 @@ __global__ void __launch_bounds__(256) k_adjoint(DevScene s, DevCamera c, Render
             camera_ray(c, pixel, u0, u1, o, d);
             float3 tp = f3(1.f, 1.f, 1.f);
             bool prev_delta = true;
+            float prev_pdf = 0.f;
             for (uint32_t b = 0; b < p.max_depth && b < (uint32_t)MAXD; ++b) {
                 Hit h = trace_closest(s, o, d);
                 if (h.tri == kMiss) {
                     end_miss = true;
                     break;
                 }
-                Vertex V = shade_vertex(s, p, key, b, o, d, tp, prev_delta, h.t, h.tri);
+                Vertex V = shade_vertex(s, p, key, b, o, d, tp, prev_delta, prev_pdf, h.t, h.tri);
                 AdjRec& r = rec[nv++];
                 r.tp = tp;
                 r.mat = V.mat;
                 r.flags = V.emit_counted ? 4u : 0u;
-                r.Le = V.emit_counted ? __ldg(&s.mats[V.mat].emission) : 0.f;
+                r.Le = V.emit_counted ? __ldg(&s.mats[V.mat].emission) * V.emit_w : 0.f;
+                r.we = V.emit_w;
                 r.lmat = V.light_mat;
                 r.nee_g = f3(0.f, 0.f, 0.f);
                 r.nee_dfa = r.nee_g;
@@ -988,6 +999,7 @@ __global__ void __launch_bounds__(256) k_adjoint(DevScene s, DevCamera c, Render
                 d = V.nd;
                 tp = V.ntp;
                 prev_delta = V.delta;
+                prev_pdf = V.pdf;
             }
             delta = f3(grad[3 * (size_t)pixel], grad[3 * (size_t)pixel + 1], grad[3 * (size_t)pixel + 2]) * inv_spp;
         }
@@ -1012,7 +1024,7 @@ __global__ void __launch_bounds__(256) k_adjoint(DevScene s, DevCamera c, Render
                     R = R + r.nee_g * r.Lj;
                 }
                 if (r.flags & 4u) {
-                    ge = dtp.x + dtp.y + dtp.z;
+                    ge = (dtp.x + dtp.y + dtp.z) * r.we;
                     R = R + f3(r.Le, r.Le, r.Le);
                 }
                 key_m = r.mat;
@@ -1070,7 +1082,7 @@ __global__ void __launch_bounds__(256) k_adjoint_reverse(DevScene s, RenderParam
             if (b < nv) {
                 const float4* r = a.rec + 4 * ((size_t)b * cap + pid);
                 const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3];
-                const uint32_t flags = __float_as_uint(r3.w);
+                const uint32_t flags = __float_as_uint(r3.w) & 15u;
                 const float3 dtp = delta * xyz(r0);
                 float3 ga = f3(0.f, 0.f, 0.f);
                 float ge = 0.f;
@@ -1081,12 +1093,12 @@ __global__ void __launch_bounds__(256) k_adjoint_reverse(DevScene s, RenderParam
                 if ((flags & 10u) == 10u) {            // cast and visible
                     const float3 ng = xyz(r2);
                     ga = ga + dtp * r2.w;
-                    key_l = __float_as_uint(r3.z);
+                    key_l = __float_as_uint(r3.w) >> 4;
                     vl.w = dot(dtp, ng);
                     R = R + ng * r3.y;
                 }
                 if (flags & 4u) {
-                    ge = dtp.x + dtp.y + dtp.z;
+                    ge = (dtp.x + dtp.y + dtp.z) * r3.z;
                     R = R + f3(r3.x, r3.x, r3.x);
                 }
                 key_m = __float_as_uint(r0.w);
@@ -1142,15 +1154,25 @@ __global__ void k_debug_rng(uint64_t seed, const uint32_t* px, const uint32_t* s
 cudaError_t launch_megakernel_regen(const Launch& l, const DevScene& s, const DevCamera& c, const RenderParams& p,
                                     uint64_t n_paths, float* out_L, float* img, uint32_t* sig, unsigned long long* rays,
                                     unsigned long long* next_path) {
-    if (sig) k_megakernel_regen<true><<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays, next_path);
-    else k_megakernel_regen<false><<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays, next_path);
+    if (p.mis) {
+        if (sig) k_megakernel_regen<true, true><<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays, next_path);
+        else k_megakernel_regen<false, true><<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays, next_path);
+    } else {
+        if (sig) k_megakernel_regen<true, false><<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays, next_path);
+        else k_megakernel_regen<false, false><<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays, next_path);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_megakernel(const Launch& l, const DevScene& s, const DevCamera& c, const RenderParams& p,
                               uint64_t n_paths, float* out_L, float* img, uint32_t* sig, unsigned long long* rays) {
-    if (sig) k_megakernel<true><<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays);
-    else k_megakernel<false><<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays);
+    if (p.mis) {
+        if (sig) k_megakernel<true, true><<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays);
+        else k_megakernel<false, true><<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays);
+    } else {
+        if (sig) k_megakernel<true, false><<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays);
+        else k_megakernel<false, false><<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays);
+    }
     return cudaGetLastError();
 }
 
@@ -1204,8 +1226,13 @@ cudaError_t launch_shadow(const Launch& l, const DevScene& s, const RenderParams
 cudaError_t launch_finish(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w, int in,
                           uint32_t b0, uint32_t threshold, unsigned long long* claim) {
     SingleSrc src{s, DevCamera{}, p};
-    if (w.sig) k_finish<true><<<l.grid, l.block, 0, l.st>>>(src, w, in, b0, threshold, claim);
-    else k_finish<false><<<l.grid, l.block, 0, l.st>>>(src, w, in, b0, threshold, claim);
+    if (p.mis) {
+        if (w.sig) k_finish<true, true><<<l.grid, l.block, 0, l.st>>>(src, w, in, b0, threshold, claim);
+        else k_finish<false, true><<<l.grid, l.block, 0, l.st>>>(src, w, in, b0, threshold, claim);
+    } else {
+        if (w.sig) k_finish<true, false><<<l.grid, l.block, 0, l.st>>>(src, w, in, b0, threshold, claim);
+        else k_finish<false, false><<<l.grid, l.block, 0, l.st>>>(src, w, in, b0, threshold, claim);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_finish_commit<<<1, 1, 0, l.st>>>(w, threshold, claim);
@@ -1334,8 +1361,8 @@ int max_blocks_per_sm(int which, int block) {
     int nb = 0;
     cudaError_t e = cudaErrorInvalidValue;
     switch (which) {
-        case K_MEGA: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_megakernel<false>, block, 0); break;
-        case K_MEGA_REGEN: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_megakernel_regen<false>, block, 0); break;
+        case K_MEGA: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_megakernel<false, false>, block, 0); break;
+        case K_MEGA_REGEN: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_megakernel_regen<false, false>, block, 0); break;
         case K_EXTEND: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend<SingleSrc>, block, 0); break;
         case K_SHADE: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade<SingleSrc, false>, block, 0); break;
         case K_SHADOW: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shadow<SingleSrc, false>, block, 0); break;
@@ -1345,7 +1372,7 @@ int max_blocks_per_sm(int which, int block) {
         case K_ADJOINT: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adjoint<16>, block, 16 * 1024); break;
         case K_SHADE_ADJ: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade_adj, block, 0); break;
         case K_SHADOW_ADJ: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shadow_adj, block, 0); break;
-        case K_FINISH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_finish<false>, block, 0); break;
+        case K_FINISH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_finish<false, false>, block, 0); break;
         default: break;
     }
     return (e == cudaSuccess && nb > 0) ? nb : 1;

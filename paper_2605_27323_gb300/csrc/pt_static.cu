@@ -168,6 +168,7 @@ extern "C" pt_status pt_render_wavefront_static(pt_scene* scene, const pt_camera
     p.rr_start = o.rr_start;
     p.rr_fixed = o.rr_fixed;
     p.sampler = (o.flags & PT_FLAG_HALTON) ? pt::SAMPLER_HALTON_ID : 0u;
+    p.mis = (o.flags & PT_FLAG_MIS) ? 1u : 0u;
     for (uint64_t w0 = 0; w0 < n_paths; w0 += cap) {
         const uint32_t n = (uint32_t)std::min<uint64_t>(cap, n_paths - w0);
         p.path_begin = w0;

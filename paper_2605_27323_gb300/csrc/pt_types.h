@@ -46,6 +46,7 @@ struct RenderParams {
     float rr_fixed;
     uint32_t sample_offset = 0;   // sample index of a pixel's first path (progressive accumulation)
     uint32_t sampler = 0;         // pixel jitter: 0 PCG uniforms, 1 Halton (2,3) + Cranley-Patterson
+    uint32_t mis = 0;             // 1: NEE and BSDF-sampled light hits combined by the power heuristic
 };
 
 enum : uint32_t { MAT_LAMBERT = 0, MAT_GGX = 1, MAT_DIELECTRIC = 2 };
@@ -61,7 +62,7 @@ enum : uint32_t { ST_TRAVERSAL = 1u, ST_QUEUE = 2u, ST_TIMEOUT = 4u };
 struct WfBuffers {
     float4* q_o[2];          // o.xyz | path index (wave-local) bits
     float4* q_d[2];          // d.xyz | flags (bit 0: previous vertex was delta)
-    float4* q_tp[2];         // throughput.xyz | -
+    float4* q_tp[2];         // throughput.xyz | solid-angle density of the BSDF sample (MIS weights)
     float2* hit;             // per queue slot: t, reordered triangle bits (0xFFFFFFFF: miss)
     uint32_t* keys;          // per queue slot: sort key
     uint32_t* perm;          // per sorted position: queue slot
@@ -101,7 +102,8 @@ struct BatchSegment {
 
 // Wavefront adjoint: one 64-byte record per path and vertex, bounce-major (rec[b * cap + pid]):
 //   r0 = throughput arriving at the vertex | material,  r1 = continuation weight w | dw/dalbedo,
-//   r2 = f G A of the NEE sample | d(f G A Le)/dalbedo,  r3 = (Le, Le_light, light material, flags);
+//   r2 = f G A of the NEE sample (times its MIS weight) | d(f G A Le)/dalbedo,
+//   r3 = (Le * w_e, Le_light, w_e, flags | light material << 4) with w_e the emission term's weight;
 // flags: 1 continues, 2 NEE visible, 4 emission counted, 8 shadow ray cast.  pend[pid] = number of
 // vertices | (path ended in a miss) << 8.
 struct AdjBuffers {
