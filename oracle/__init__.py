@@ -72,6 +72,8 @@ def lib():
             L.or_scene_create.restype = vp
             L.or_scene_create.argtypes = [vp, i64, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp]
             L.or_scene_destroy.argtypes = [vp]
+            L.or_scene_create_corners.restype = vp
+            L.or_scene_create_corners.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp, vp, vp]
             L.or_scene_set_materials.argtypes = [vp, vp, vp]
             L.or_scene_n_lights.restype = i64
             L.or_scene_n_lights.argtypes = [vp]
@@ -203,8 +205,36 @@ class Scene:
 
     @classmethod
     def from_dict(cls, sc: dict) -> "Scene":
+        if "meshes" in sc:
+            return cls.from_instanced(sc)
         return cls(sc["verts"], sc["tris"], sc["tri_mat"], sc["mat_type"], sc["mat_albedo"],
                    sc["mat_emission"], sc["mat_roughness"], sc["mat_ior"], sc["env"])
+
+    @classmethod
+    def from_instanced(cls, sc: dict) -> "Scene":
+        """A two-level scene placed in the world in FP64: every instance's mesh triangles, in
+        instance order, with world = R v + t from the instance's [R | t]; an instance material other
+        than 0xFFFFFFFF replaces the mesh's triangle materials."""
+        corners, tmat = [], []
+        for m, X, im in zip(sc["inst_mesh"], sc["inst_xform"], sc["inst_mat"]):
+            mesh = sc["meshes"][int(m)]
+            V = np.asarray(mesh["verts"], np.float32).astype(np.float64)
+            X = np.asarray(X, np.float32).astype(np.float64)
+            W = V @ X[:, :3].T + X[:, 3]
+            corners.append(W[np.asarray(mesh["tris"], np.int64)])
+            tm = np.asarray(mesh["tri_mat"], np.uint32)
+            tmat.append(tm if int(im) == 0xFFFFFFFF else np.full(len(tm), int(im), np.uint32))
+        self = cls.__new__(cls)
+        c = np.ascontiguousarray(np.concatenate(corners).reshape(-1, 9), np.float64) if corners else np.zeros((0, 9))
+        self._keep = [c, _f(np.concatenate(tmat) if tmat else np.zeros(0), np.uint32), _f(sc["mat_type"], np.uint32),
+                      _f(sc["mat_albedo"], np.float32).reshape(-1, 3), _f(sc["mat_emission"], np.float32),
+                      _f(sc["mat_roughness"], np.float32), _f(sc["mat_ior"], np.float32), _f(sc["env"], np.float32)]
+        c, tm, mt, ma, me, mr, mi, ev = self._keep
+        self.n_tris = c.shape[0]
+        self.n_mats = mt.shape[0]
+        self.h = lib().or_scene_create_corners(_p(c), c.shape[0], _p(tm), mt.shape[0], _p(mt), _p(ma), _p(me),
+                                               _p(mr), _p(mi), _p(ev))
+        return self
 
     def close(self):
         if getattr(self, "h", None):

@@ -283,11 +283,7 @@ void or_scene_set_materials(or_scene* s, const float* albedo, const float* emiss
     }
 }
 
-or_scene* or_scene_create(const float* verts, int64_t n_verts, const uint32_t* tris, int64_t n_tris,
-                          const uint32_t* tri_mat, int64_t n_mats, const uint32_t* mat_type,
-                          const float* mat_albedo, const float* mat_emission, const float* mat_roughness,
-                          const float* mat_ior, const float* env) {
-    (void)n_verts;
+static or_scene* scene_alloc(int64_t n_tris) {
     or_scene* s = (or_scene*)calloc(1, sizeof(or_scene));
     s->n_tris = n_tris;
     size_t nt = (size_t)(n_tris > 0 ? n_tris : 1);
@@ -296,6 +292,19 @@ or_scene* or_scene_create(const float* verts, int64_t n_verts, const uint32_t* t
     s->p2 = (v3*)malloc(sizeof(v3) * nt);
     s->mat = (uint32_t*)malloc(sizeof(uint32_t) * nt);
     s->is_light = (unsigned char*)calloc(nt, 1);
+    return s;
+}
+
+static or_scene* scene_finish(or_scene* s, int64_t n_mats, const uint32_t* mat_type, const float* mat_albedo,
+                              const float* mat_emission, const float* mat_roughness, const float* mat_ior,
+                              const float* env);
+
+or_scene* or_scene_create(const float* verts, int64_t n_verts, const uint32_t* tris, int64_t n_tris,
+                          const uint32_t* tri_mat, int64_t n_mats, const uint32_t* mat_type,
+                          const float* mat_albedo, const float* mat_emission, const float* mat_roughness,
+                          const float* mat_ior, const float* env) {
+    (void)n_verts;
+    or_scene* s = scene_alloc(n_tris);
     for (int64_t i = 0; i < n_tris; ++i) {
         const float* a = verts + 3 * (size_t)tris[3 * i];
         const float* b = verts + 3 * (size_t)tris[3 * i + 1];
@@ -305,6 +314,30 @@ or_scene* or_scene_create(const float* verts, int64_t n_verts, const uint32_t* t
         s->p2[i] = mk(c[0], c[1], c[2]);
         s->mat[i] = tri_mat[i];
     }
+    return scene_finish(s, n_mats, mat_type, mat_albedo, mat_emission, mat_roughness, mat_ior, env);
+}
+
+/* A scene given as world-space triangle corners in FP64 (n_tris x 3 x 3): used for instanced
+ * scenes, whose instances the caller has already placed in the world (triangle order = instances
+ * in order, each mesh's triangles in order; that order is the triangle id). */
+or_scene* or_scene_create_corners(const double* corners, int64_t n_tris, const uint32_t* tri_mat, int64_t n_mats,
+                                  const uint32_t* mat_type, const float* mat_albedo, const float* mat_emission,
+                                  const float* mat_roughness, const float* mat_ior, const float* env) {
+    or_scene* s = scene_alloc(n_tris);
+    for (int64_t i = 0; i < n_tris; ++i) {
+        const double* c = corners + 9 * (size_t)i;
+        s->p0[i] = mk(c[0], c[1], c[2]);
+        s->p1[i] = mk(c[3], c[4], c[5]);
+        s->p2[i] = mk(c[6], c[7], c[8]);
+        s->mat[i] = tri_mat[i];
+    }
+    return scene_finish(s, n_mats, mat_type, mat_albedo, mat_emission, mat_roughness, mat_ior, env);
+}
+
+static or_scene* scene_finish(or_scene* s, int64_t n_mats, const uint32_t* mat_type, const float* mat_albedo,
+                              const float* mat_emission, const float* mat_roughness, const float* mat_ior,
+                              const float* env) {
+    const int64_t n_tris = s->n_tris;
     s->n_mats = n_mats;
     s->mats = (omat*)calloc((size_t)(n_mats > 0 ? n_mats : 1), sizeof(omat));
     for (int64_t m = 0; m < n_mats; ++m) {

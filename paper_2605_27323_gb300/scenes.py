@@ -26,12 +26,24 @@ A scene is a dict of arrays: verts (V,3) f32, tris (T,3) u32, tri_mat (T,) u32, 
 u32 (0 Lambert, 1 GGX conductor, 2 smooth dielectric), mat_albedo (M,3) f32, mat_emission (M,)
 f32, mat_roughness (M,) f32, mat_ior (M,) f32, env (3,) f32; and a camera dict with eye, target,
 up, vfov_deg, width, height.
+
+An instanced scene (two-level: meshes placed by instances) replaces verts/tris/tri_mat with
+meshes: a list of {verts, tris, tri_mat} in object space, and inst_mesh (I,) u32, inst_xform
+(I,3,4) f32 (object-to-world [R | t]: world = R v + t), inst_mat (I,) u32 (a material for every
+triangle of the instance, or NO_MATERIAL to keep the mesh's).  Its triangle ids run over the
+instances in order, each mesh's triangles in order.
+
+* ``instanced_spheres_scene`` / ``instanced_terrain_scene`` -- the spheres and terrain recipes with
+  one icosphere mesh (and one light quad) placed by instances;
+* ``split_as_instances`` -- any flat scene cut into meshes placed by exact transforms (signed axis
+  permutations times powers of two), so that the instanced scene is the flat one exactly.
 """
 from __future__ import annotations
 
 import numpy as np
 
 LAMBERT, GGX, DIELECTRIC = 0, 1, 2
+NO_MATERIAL = 0xFFFFFFFF
 
 
 # ------------------------------------------------------------------ geometry helpers
@@ -161,6 +173,152 @@ def _scene(b: _Builder, mats: dict, env, **extra):
     sc.update(mats)
     sc.update(extra)
     return sc
+
+
+# ------------------------------------------------------------------ instanced scenes
+def _instanced(meshes, inst_mesh, inst_xform, inst_mat, mats, env, **extra):
+    sc = {"meshes": [{"verts": np.asarray(m[0], np.float32).reshape(-1, 3),
+                      "tris": np.asarray(m[1], np.uint32).reshape(-1, 3),
+                      "tri_mat": np.asarray(m[2], np.uint32).reshape(-1)} for m in meshes],
+          "inst_mesh": np.asarray(inst_mesh, np.uint32).reshape(-1),
+          "inst_xform": np.asarray(inst_xform, np.float32).reshape(-1, 3, 4),
+          "inst_mat": np.asarray(inst_mat, np.uint32).reshape(-1),
+          "env": np.asarray(env, np.float32)}
+    sc.update(mats)
+    sc.update(extra)
+    return sc
+
+
+def _xform(scale=1.0, translate=(0.0, 0.0, 0.0), R=None):
+    M = np.zeros((3, 4))
+    M[:, :3] = (np.eye(3) if R is None else np.asarray(R, np.float64)) * np.asarray(scale, np.float64)
+    M[:, 3] = translate
+    return M
+
+
+def instance_tri_count(sc) -> int:
+    return int(sum(len(sc["meshes"][m]["tris"]) for m in sc["inst_mesh"]))
+
+
+def split_as_instances(sc: dict, n_pieces: int = 5, seed: int = 0) -> dict:
+    """The flat scene `sc` cut into n_pieces meshes (contiguous triangle ranges), each stored in its
+    own object frame and placed back by an exact transform: a signed axis permutation times a power
+    of two (world = 2^k P v, object vertices 2^-k P^T v, both exact in FP32).  Triangle ids,
+    materials and world geometry equal the flat scene's."""
+    rng = np.random.default_rng(seed)
+    V, T, M = np.asarray(sc["verts"], np.float32), np.asarray(sc["tris"]), np.asarray(sc["tri_mat"])
+    cuts = np.linspace(0, len(T), n_pieces + 1).round().astype(int)
+    meshes, xf = [], []
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        used, inv = np.unique(T[a:b].ravel(), return_inverse=True)
+        P = np.eye(3)[rng.permutation(3)] * rng.choice([-1.0, 1.0], size=3)[:, None]
+        k = int(rng.integers(-3, 4))
+        obj = ((V[used].astype(np.float64) @ P) * 2.0 ** (-k)).astype(np.float32)   # P^T v, row form
+        meshes.append((obj, inv.reshape(-1, 3), M[a:b]))
+        xf.append(_xform(2.0 ** k, (0.0, 0.0, 0.0), P))
+    mats = {k: sc[k] for k in ("mat_type", "mat_albedo", "mat_emission", "mat_roughness", "mat_ior")}
+    extra = {k: v for k, v in sc.items() if k in ("camera", "spp", "max_depth", "rr_start", "rr_fixed")}
+    return _instanced(meshes, np.arange(len(meshes)), xf, np.full(len(meshes), NO_MATERIAL), mats, sc["env"],
+                      **extra)
+
+
+def _rotation(rng):
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def instanced_spheres_scene(seed: int = 0, n_spheres=200, level=4, ground_quads=256, n_lights=8, width=1920,
+                            height=1080, extent=60.0, rotate=True, n_materials=None):
+    """The spheres recipe with one icosphere mesh placed by n_spheres instances (randomly rotated,
+    uniformly scaled by lognormal(0, 0.5) radii, resting on the ground, one material each), the
+    ground as one mesh and one light quad mesh placed by n_lights translated instances."""
+    rng = np.random.default_rng(seed)
+    S, ST = icosphere(level)
+    radii = rng.lognormal(0.0, 0.5, size=n_spheres)
+    cx = rng.uniform(-0.7 * extent, 0.7 * extent, size=n_spheres)
+    cz = rng.uniform(-0.7 * extent, 0.7 * extent, size=n_spheres)
+    n_sph_mats = n_spheres if n_materials is None else n_materials - 2
+    sph_mat = np.arange(n_spheres) if n_materials is None else rng.integers(0, n_sph_mats, size=n_spheres)
+    types, albedo, rough = _mix_materials(rng, n_sph_mats)
+    ground_mat, light_mat = n_sph_mats, n_sph_mats + 1
+    g = 2.5 * extent
+    GV, GT = grid_mesh(ground_quads, -g, g, -g, g)
+    h = 3.0
+    LV, LT = quad((-h, 0.0, -h), (h, 0.0, -h), (h, 0.0, h), (-h, 0.0, h))
+    meshes = [(S, ST, np.zeros(len(ST))), (GV, GT, np.full(len(GT), ground_mat)), (LV, LT, np.full(len(LT), light_mat))]
+    im, ix, imat = [], [], []
+    for k in range(n_spheres):
+        im.append(0)
+        ix.append(_xform(radii[k], (cx[k], radii[k], cz[k]), _rotation(rng) if rotate else None))
+        imat.append(sph_mat[k])
+    im.append(1)
+    ix.append(_xform())
+    imat.append(NO_MATERIAL)
+    for k in range(n_lights):
+        ang = 2 * np.pi * k / n_lights
+        im.append(2)
+        ix.append(_xform(1.0, (0.45 * extent * np.cos(ang), 25.0, 0.45 * extent * np.sin(ang))))
+        imat.append(NO_MATERIAL)
+    types = np.concatenate([types, [LAMBERT, LAMBERT]])
+    albedo = np.concatenate([albedo, [[0.5, 0.5, 0.5], [0.8, 0.8, 0.8]]])
+    rough = np.concatenate([rough, [0.5, 0.5]])
+    emission = np.zeros(len(types))
+    emission[light_mat] = 15.0
+    mats = _materials(types, albedo, emission, rough, np.full(len(types), 1.5))
+    cam = camera((0.0, 0.5 * extent, 0.95 * extent), (0.0, 0.0, -0.1 * extent), (0, 1, 0), 50.0, width, height)
+    return _instanced(meshes, im, ix, imat, mats, (0.1, 0.1, 0.1), camera=cam, spp=1, max_depth=5, rr_start=3)
+
+
+def instanced_terrain_scene(seed: int = 0, grid=2048, n_spheres=5000, level=2, n_lights=64, width=3840,
+                            height=2160, extent=200.0, relief=12.0):
+    """The terrain recipe with real instancing: the heightfield as one mesh, one level-2 icosphere
+    mesh placed by n_spheres instances (uniform scale, translation, one of 253 materials each) and
+    one light quad mesh placed by n_lights instances."""
+    rng = np.random.default_rng(seed)
+    h = fbm(rng)
+    scale = (grid - 1) / (2 * extent)
+
+    def height_fn(X, Z):
+        return relief * h(X * scale, Z * scale)
+
+    GV, GT = grid_mesh(grid - 1, -extent, extent, -extent, extent, height_fn)
+    n_sph_mats = 253
+    types, albedo, rough = _mix_materials(rng, n_sph_mats)
+    ground_mat, light_mat = n_sph_mats, n_sph_mats + 1
+    S, ST = icosphere(level)
+    radii = rng.lognormal(0.0, 0.5, size=n_spheres)
+    cx = rng.uniform(-0.9 * extent, 0.9 * extent, size=n_spheres)
+    cz = rng.uniform(-0.9 * extent, 0.9 * extent, size=n_spheres)
+    cy = height_fn(cx, cz) + radii
+    smat = rng.integers(0, n_sph_mats, size=n_spheres)
+    hh = 4.0
+    LV, LT = quad((-hh, 0.0, -hh), (hh, 0.0, -hh), (hh, 0.0, hh), (-hh, 0.0, hh))
+    meshes = [(GV, GT, np.full(len(GT), ground_mat)), (S, ST, np.zeros(len(ST))), (LV, LT, np.full(len(LT), light_mat))]
+    im, ix, imat = [0], [_xform()], [NO_MATERIAL]
+    for k in range(n_spheres):
+        im.append(1)
+        ix.append(_xform(radii[k], (cx[k], cy[k], cz[k])))
+        imat.append(smat[k])
+    side = int(round(np.sqrt(n_lights)))
+    for k in range(n_lights):
+        i, j = k % side, k // side
+        x = -0.8 * extent + 1.6 * extent * (i + 0.5) / side
+        z = -0.8 * extent + 1.6 * extent * (j + 0.5) / side
+        im.append(2)
+        ix.append(_xform(1.0, (x, 60.0, z)))
+        imat.append(NO_MATERIAL)
+    types = np.concatenate([types, [LAMBERT, LAMBERT]])
+    albedo = np.concatenate([albedo, [[0.45, 0.4, 0.35], [0.8, 0.8, 0.8]]])
+    rough = np.concatenate([rough, [0.5, 0.5]])
+    emission = np.zeros(len(types))
+    emission[light_mat] = 15.0
+    matd = _materials(types, albedo, emission, rough, np.full(len(types), 1.5))
+    cam = camera((0.0, 0.45 * extent, 1.1 * extent), (0.0, 0.0, 0.0), (0, 1, 0), 55.0, width, height)
+    return _instanced(meshes, im, ix, imat, matd, (0.1, 0.1, 0.1), camera=cam, spp=4, max_depth=8, rr_start=3)
 
 
 # ------------------------------------------------------------------ benchmark scenes
