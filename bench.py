@@ -33,8 +33,8 @@ METRIC = "Mrays/s and ms/frame (1080p, 1 spp) wavefront vs megakernel; bwd/fwd t
 WORKLOAD = ("procedural spheres scene: 200 level-4 icospheres + 256x256-quad ground (1,155,088 tris), "
             "8 emissive quads + constant environment, 1920x1080, 1 spp, max depth 5, roulette from bounce 3; "
             "step = wavefront frame + megakernel frame + adjoint pass")
-KERNEL_SOURCES = ["paper_2605_27323_gb300/csrc/pt_kernels.cu", "paper_2605_27323_gb300/csrc/pt_device.cuh",
-                  "paper_2605_27323_gb300/csrc/pt_trace.cuh"]
+KERNEL_SOURCES = ["paper_2605_27323_gb300/csrc/pt_k_wave.cu", "paper_2605_27323_gb300/csrc/pt_common.cuh",
+                  "paper_2605_27323_gb300/csrc/pt_device.cuh", "paper_2605_27323_gb300/csrc/pt_trace.cuh"]
 # Algorithmic bytes per unit of each stage (queue/state traffic, "Roofline").
 BYTES_PER_UNIT = {
     "extend": 40,      # per extension ray: ray o|id + d|flags (32 B) read, hit record (8 B) written
@@ -460,6 +460,31 @@ def run_large(args):
     res["hybrid"] = {"ms_per_frame": hyb[hyb_thr], "threshold": hyb_thr, "sweep_ms": hyb,
                      "wavefront_over_hybrid": res["wavefront"]["ms_per_frame"] / hyb[hyb_thr]}
     info = g.info()
+    # the same recipe as a two-level scene: one icosphere mesh placed 5000 times (TLAS/BLAS)
+    t0 = time.perf_counter()
+    isc = scenes.instanced_terrain_scene(seed=0)
+    gi = pt.Scene.from_dict(isc)
+    isetup = time.perf_counter() - t0
+    ires = {}
+    for mode in ("wavefront", "megakernel"):
+        for k in range(args.warmup):
+            gi.render(cam, spp, depth, 100 + k, mode=mode)
+        ms, rays = [], []
+        for k in range(max(3, min(args.steps, 10))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gi.render(cam, spp, depth, k, mode=mode)
+            e1.record(stream)
+            st = gi.stats()
+            ms.append(e0.elapsed_time(e1))
+            rays.append(st["extension_rays"] + st["shadow_rays"])
+        ires[mode] = {"ms_per_frame": float(np.mean(ms)),
+                      "mrays_s": float(np.sum(rays) / (np.sum(ms) * 1e-3) / 1e6)}
+    iinfo = gi.info()
+    ires.update({"triangles_placed": int(iinfo["n_tris"]), "device_bytes": int(iinfo["device_bytes"]),
+                 "scene_setup_s": isetup, "instances": int(len(isc["inst_mesh"])),
+                 "device_bytes_saved_vs_flat": int(info["device_bytes"]) - int(iinfo["device_bytes"])})
+    del gi
     line = {"metric": "Mrays/s and ms/frame, large scene (3840x2160, 4 spp, depth 8)", "value": res["wavefront"]["mrays_s"],
             "unit": "Mrays/s", "n_gpus": 1, "steps": max(3, min(args.steps, 10)), "warmup": args.warmup,
             "ms_per_step": res["wavefront"]["ms_per_frame"], "higher_is_better": True, "scaling": "weak",
@@ -468,6 +493,7 @@ def run_large(args):
                        "triangles": int(info["n_tris"]), "bvh_nodes": int(info["n_nodes"]),
                        "device_bytes": int(info["device_bytes"]), "scene_setup_s": setup_s},
             "wavefront": res["wavefront"], "megakernel": res["megakernel"], "hybrid": res["hybrid"],
+            "two_level": ires,
             "wf_over_mk_speedup": res["megakernel"]["ms_per_frame"] / res["wavefront"]["ms_per_frame"]}
     print(json.dumps(line), flush=True)
 

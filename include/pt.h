@@ -132,6 +132,36 @@ pt_status pt_scene_create(const float* verts, uint32_t n_verts, const uint32_t* 
                           const uint32_t* tri_material, const pt_material* mats, uint32_t n_mats,
                           const float env_radiance[3], void* cuda_stream, pt_scene** out);
 
+/* One placed copy of a mesh in a two-level scene. */
+#define PT_NO_MATERIAL 0xFFFFFFFFu
+typedef struct {
+    float xform[12];            /* object-to-world affine transform, row-major 3 x 4 [R | t]: world = R v + t
+                                   (R invertible; any rotation, scale or shear) */
+    uint32_t mesh;              /* index of the mesh */
+    uint32_t material;          /* material of every triangle of this copy, or PT_NO_MATERIAL (the mesh's) */
+    uint32_t reserved[2];       /* 0 */
+} pt_instance;                  /* 64 bytes */
+
+/* Build a two-level scene (the TLAS/BLAS acceleration structure of Sec. 2.3): n_meshes meshes in
+ * object space (mesh m: host verts[m] n_verts[m] x 3 float, tris[m] n_tris[m] x 3 uint32,
+ * tri_material[m] n_tris[m] uint32) and n_instances placed copies.  One binned-SAH BVH is built per
+ * mesh and one over the instances' world boxes; rays are taken into each instance's object space
+ * with the inverse transform, so a mesh is stored once however often it is placed.  Triangle ids
+ * (returned by pt_trace_closest, used to break ties and in branch signatures) run over the
+ * instances in order, each mesh's triangles in order.  The light list holds every instance's
+ * triangles whose (instance or mesh) material emits at creation, placed in the world, ascending
+ * id; its pmf is proportional to world area.  Renders, backward passes, progressive renders and
+ * queries take the scene like any other; pt_render_batch and pt_autotune_batch reject it
+ * (PT_ERR_UNSUPPORTED).  Errors: PT_ERR_INVALID_ARG (no mesh or instance, an empty mesh, NULL
+ * arrays, out-of-range indices or materials, non-finite or singular transforms, n_mats >= 2^28,
+ * >= 2^28 mesh triangles or >= 2^32 - 1 placed triangles), PT_ERR_OOM, PT_ERR_CUDA; the upload
+ * synchronises cuda_stream. */
+pt_status pt_scene_create_instanced(uint32_t n_meshes, const float* const* verts, const uint32_t* n_verts,
+                                    const uint32_t* const* tris, const uint32_t* n_tris,
+                                    const uint32_t* const* tri_material, const pt_instance* instances,
+                                    uint32_t n_instances, const pt_material* mats, uint32_t n_mats,
+                                    const float env_radiance[3], void* cuda_stream, pt_scene** out);
+
 /* Replace per-material albedo (device n_mats x 3) and emission (device n_mats) -- the
  * differentiable parameters -- asynchronously on `stream`.  Either pointer may be NULL (kept).
  * The light list stays the one fixed at creation. */
@@ -204,7 +234,7 @@ pt_status pt_trace_closest(pt_scene* scene, const float* d_rays, uint32_t n, flo
  * except: d_out_rgb (and opts->d_path_sig, if set) must be device memory (nothing is staged), there
  * is no per-path output, opts->queue_capacity is ignored, and pt_get_stats does not report this call.
  * Errors: PT_ERR_INVALID_ARG also when one pixel's spp samples need more than the array
- * (spp x 176 bytes > 32 MiB).  The first call on a device looks up the array's device address
+ * (spp x 180 bytes > 32 MiB).  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share the
  * array and it keeps the last call's contents: each call clears its own counters, and calls that
  * overlap on the GPU (other streams or threads without ordering between them) race. */

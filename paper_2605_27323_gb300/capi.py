@@ -22,7 +22,7 @@ FLAG_PROFILE, FLAG_NO_GRAPH, FLAG_MK_STATIC, FLAG_HALTON, FLAG_MIS = 1, 2, 4, 8,
 
 # Every function that include/pt.h declares (the symbol-export test checks this list against the
 # header and the shared object).
-EXPORTED = ["pt_scene_create", "pt_scene_set_materials", "pt_render", "pt_render_progressive", "pt_render_backward",
+EXPORTED = ["pt_scene_create", "pt_scene_create_instanced", "pt_scene_set_materials", "pt_render", "pt_render_progressive", "pt_render_backward",
             "pt_render_batch",
             "pt_autotune_batch", "pt_trace_closest", "pt_get_stats", "pt_debug_rng", "pt_debug_trace_paths",
             "pt_scene_info", "pt_render_wavefront_static",
@@ -32,6 +32,13 @@ EXPORTED = ["pt_scene_create", "pt_scene_set_materials", "pt_render", "pt_render
 class Material(C.Structure):
     _fields_ = [("type", u32), ("albedo", f32 * 3), ("emission", f32), ("roughness", f32), ("ior", f32),
                 ("flags", u32)]
+
+
+class Instance(C.Structure):
+    _fields_ = [("xform", f32 * 12), ("mesh", u32), ("material", u32), ("reserved", u32 * 2)]
+
+
+NO_MATERIAL = 0xFFFFFFFF
 
 
 class Camera(C.Structure):
@@ -76,6 +83,9 @@ def load(build_if_missing: bool = True):
     P = C.POINTER
     L.pt_scene_create.restype = u32
     L.pt_scene_create.argtypes = [vp, u32, vp, u32, vp, vp, u32, vp, vp, P(vp)]
+    L.pt_scene_create_instanced.restype = u32
+    L.pt_scene_create_instanced.argtypes = [u32, P(vp), P(u32), P(vp), P(u32), P(vp), P(Instance), u32, vp, u32, vp,
+                                            vp, P(vp)]
     L.pt_scene_set_materials.restype = u32
     L.pt_scene_set_materials.argtypes = [vp, vp, vp, vp]
     L.pt_render.restype = u32

@@ -6,6 +6,7 @@
 #include <cuda_runtime_api.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -118,10 +119,10 @@ int blocks_per_sm(int which, int block) {
 
 enum Stage { ST_RAYGEN, ST_EXTEND, ST_SORT, ST_SHADE, ST_SHADOW, ST_REDUCE, ST_MEGA, ST_ADJOINT, ST_COUNT };
 
-// One device allocation carved into the wavefront arrays for `cap` paths (176 bytes each).
+// One device allocation carved into the wavefront arrays for `cap` paths (180 bytes each).
 pt_status carve_wavefront(DevBuf& buf, uint64_t cap, pt::WfBuffers& w) {
     size_t q = align256(cap * 16), h = align256(cap * 8), k = align256(cap * 4);
-    size_t total = 6 * q + h + 2 * k + align256(pt::kMaxSortKeys * 4) + 3 * q + q;
+    size_t total = 6 * q + h + 3 * k + align256(pt::kMaxSortKeys * 4) + 3 * q + q;
     PT_TRY(buf.ensure(total));
     char* base = buf.as<char>();
     size_t off = 0;
@@ -136,6 +137,7 @@ pt_status carve_wavefront(DevBuf& buf, uint64_t cap, pt::WfBuffers& w) {
         w.q_tp[i] = reinterpret_cast<float4*>(take(q));
     }
     w.hit = reinterpret_cast<float2*>(take(h));
+    w.hit_inst = reinterpret_cast<uint32_t*>(take(k));
     w.keys = reinterpret_cast<uint32_t*>(take(k));
     w.perm = reinterpret_cast<uint32_t*>(take(k));
     w.bucket = reinterpret_cast<uint32_t*>(take(align256(pt::kMaxSortKeys * 4)));
@@ -155,6 +157,8 @@ struct pt_scene {
     float light_area = 0.f;
     float env[3] = {0.f, 0.f, 0.f};
     DevBuf nodes, tris, mats, lights, cdf, status;
+    DevBuf tlas, inst;          // two-level scenes: top-level nodes and instance records
+    bool instanced = false;
     // workspaces (grown on demand, kept until destroy)
     DevBuf wf;
     uint64_t wf_capacity = 0;
@@ -195,6 +199,8 @@ struct pt_scene {
         s.env_b = env[2];
         s.n_mats = n_mats;
         s.status = status.as<uint32_t>();
+        s.tlas = instanced ? tlas.as<const float4>() : nullptr;
+        s.inst = instanced ? inst.as<const float4>() : nullptr;
         return s;
     }
     uint32_t* counts() const { return counters.as<uint32_t>(); }
@@ -481,6 +487,7 @@ pt_status batch_render(pt_scene* const* scenes, const pt_camera* cams, const uin
     for (uint32_t i = 0; i < n; ++i) {
         if (!scenes[i]) return fail(PT_ERR_INVALID_ARG, "scene %u is NULL", i);
         if (scenes[i]->device != device) return fail(PT_ERR_INVALID_ARG, "scene %u is on another device", i);
+        if (scenes[i]->instanced) return fail(PT_ERR_UNSUPPORTED, "scene %u is a two-level scene: batched rendering takes single-level scenes", i);
         if (spp[i] == 0) return fail(PT_ERR_INVALID_ARG, "spp[%u] must be >= 1", i);
         PT_TRY(make_camera(&cams[i], dcs[i]));
         if (!d_out[i] || !is_device_ptr(d_out[i])) return fail(PT_ERR_INVALID_ARG, "d_out[%u] must be device memory", i);
@@ -922,6 +929,279 @@ pt_status pt_scene_create(const float* verts, uint32_t n_verts, const uint32_t* 
     return PT_OK;
 }
 
+// Two-level scene (the paper's TLAS/BLAS structure, Sec. 2.3): one binned-SAH BVH per mesh over its
+// object-space triangles, a top-level BVH over the instances' world boxes, and a light list of
+// the instances' emissive triangles placed in the world.  Triangle ids run over the instances in
+// order, each mesh's triangles in order.
+pt_status pt_scene_create_instanced(uint32_t n_meshes, const float* const* verts, const uint32_t* n_verts,
+                                    const uint32_t* const* tris, const uint32_t* n_tris,
+                                    const uint32_t* const* tri_material, const pt_instance* instances,
+                                    uint32_t n_instances, const pt_material* mats, uint32_t n_mats,
+                                    const float env_radiance[3], void* cuda_stream, pt_scene** out) {
+    if (!out) return fail(PT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_meshes == 0 || !verts || !n_verts || !tris || !n_tris || !tri_material)
+        return fail(PT_ERR_INVALID_ARG, "at least one mesh with its arrays is required");
+    if (n_instances == 0 || !instances) return fail(PT_ERR_INVALID_ARG, "at least one instance is required");
+    if (n_mats == 0 || !mats) return fail(PT_ERR_INVALID_ARG, "materials are required");
+    if (n_mats >= (1u << 28)) return fail(PT_ERR_INVALID_ARG, "n_mats must be < 2^28");
+    uint64_t total_records = 0;
+    for (uint32_t m = 0; m < n_meshes; ++m) {
+        if (n_tris[m] == 0) return fail(PT_ERR_INVALID_ARG, "mesh %u has no triangles", m);
+        if (!verts[m] || !tris[m] || !tri_material[m]) return fail(PT_ERR_INVALID_ARG, "mesh %u: NULL array", m);
+        for (uint64_t i = 0; i < 3ull * n_verts[m]; ++i)
+            if (!std::isfinite(verts[m][i])) return fail(PT_ERR_INVALID_ARG, "mesh %u: vertex %llu is not finite", m, (unsigned long long)(i / 3));
+        for (uint64_t i = 0; i < 3ull * n_tris[m]; ++i)
+            if (tris[m][i] >= n_verts[m]) return fail(PT_ERR_INVALID_ARG, "mesh %u: triangle %llu references vertex %u >= n_verts", m, (unsigned long long)(i / 3), tris[m][i]);
+        for (uint32_t i = 0; i < n_tris[m]; ++i)
+            if (tri_material[m][i] >= n_mats) return fail(PT_ERR_INVALID_ARG, "mesh %u: triangle %u has material %u >= n_mats", m, i, tri_material[m][i]);
+        total_records += n_tris[m];
+    }
+    if (total_records >= (1u << 28)) return fail(PT_ERR_INVALID_ARG, "the meshes hold >= 2^28 triangles");
+    for (uint32_t m = 0; m < n_mats; ++m) {
+        const pt_material& M = mats[m];
+        if (M.type > PT_MAT_DIELECTRIC) return fail(PT_ERR_INVALID_ARG, "material %u: unknown type %u", m, M.type);
+        if (!finite3(M.albedo) || M.albedo[0] < 0 || M.albedo[1] < 0 || M.albedo[2] < 0)
+            return fail(PT_ERR_INVALID_ARG, "material %u: albedo must be finite and >= 0", m);
+        if (!std::isfinite(M.emission) || M.emission < 0) return fail(PT_ERR_INVALID_ARG, "material %u: emission must be finite and >= 0", m);
+        if (!std::isfinite(M.roughness) || M.roughness < 0) return fail(PT_ERR_INVALID_ARG, "material %u: roughness must be finite and >= 0", m);
+        if (!std::isfinite(M.ior) || !(M.ior > 0)) return fail(PT_ERR_INVALID_ARG, "material %u: ior must be finite and > 0", m);
+    }
+    if (env_radiance && (!finite3(env_radiance) || env_radiance[0] < 0 || env_radiance[1] < 0 || env_radiance[2] < 0))
+        return fail(PT_ERR_INVALID_ARG, "env_radiance must be finite and >= 0");
+    // instance transforms and their inverses (FP64)
+    std::vector<double> inv(12 * (size_t)n_instances);
+    uint64_t total_prims = 0;
+    for (uint32_t i = 0; i < n_instances; ++i) {
+        const pt_instance& I = instances[i];
+        if (I.mesh >= n_meshes) return fail(PT_ERR_INVALID_ARG, "instance %u: mesh %u >= n_meshes", i, I.mesh);
+        if (I.material != PT_NO_MATERIAL && I.material >= n_mats)
+            return fail(PT_ERR_INVALID_ARG, "instance %u: material %u >= n_mats", i, I.material);
+        for (int k = 0; k < 12; ++k)
+            if (!std::isfinite(I.xform[k])) return fail(PT_ERR_INVALID_ARG, "instance %u: transform is not finite", i);
+        const double r[9] = {I.xform[0], I.xform[1], I.xform[2], I.xform[4], I.xform[5], I.xform[6],
+                             I.xform[8], I.xform[9], I.xform[10]};
+        const double c00 = r[4] * r[8] - r[5] * r[7], c01 = r[5] * r[6] - r[3] * r[8], c02 = r[3] * r[7] - r[4] * r[6];
+        const double det = r[0] * c00 + r[1] * c01 + r[2] * c02;
+        double scale = 0;
+        for (double v : r) scale = std::max(scale, std::fabs(v));
+        if (!(std::fabs(det) > 1e-12 * scale * scale * scale)) return fail(PT_ERR_INVALID_ARG, "instance %u: transform is singular", i);
+        // inverse of the 3x3 part by cofactors; b = -A t
+        double A[9] = {c00 / det, (r[2] * r[7] - r[1] * r[8]) / det, (r[1] * r[5] - r[2] * r[4]) / det,
+                       c01 / det, (r[0] * r[8] - r[2] * r[6]) / det, (r[2] * r[3] - r[0] * r[5]) / det,
+                       c02 / det, (r[1] * r[6] - r[0] * r[7]) / det, (r[0] * r[4] - r[1] * r[3]) / det};
+        const double t[3] = {I.xform[3], I.xform[7], I.xform[11]};
+        for (int row = 0; row < 3; ++row) {
+            double* o = &inv[12 * (size_t)i + 4 * row];
+            o[0] = A[3 * row];
+            o[1] = A[3 * row + 1];
+            o[2] = A[3 * row + 2];
+            o[3] = -(A[3 * row] * t[0] + A[3 * row + 1] * t[1] + A[3 * row + 2] * t[2]);
+        }
+        total_prims += n_tris[I.mesh];
+    }
+    if (total_prims >= 0xFFFFFFFFull) return fail(PT_ERR_INVALID_ARG, "the instances hold >= 2^32 - 1 triangles");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    pt_scene* sc = new (std::nothrow) pt_scene();
+    if (!sc) return fail(PT_ERR_OOM, "host allocation failed");
+    auto bail = [&](pt_status s) {
+        delete sc;
+        return s;
+    };
+    if (cudaGetDevice(&sc->device) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(PT_ERR_CUDA, "no CUDA device"));
+    }
+    sc->instanced = true;
+    sc->n_tris = total_prims;
+    sc->n_mats = n_mats;
+    if (env_radiance)
+        for (int k = 0; k < 3; ++k) sc->env[k] = env_radiance[k];
+    auto bits = [](uint32_t u) {
+        float f;
+        std::memcpy(&f, &u, 4);
+        return f;
+    };
+    auto ubits = [](float f) {
+        uint32_t u;
+        std::memcpy(&u, &f, 4);
+        return u;
+    };
+    // bottom level: one BVH per mesh, nodes and triangle records concatenated (refs relocated)
+    std::vector<float> nodes, trec;
+    std::vector<uint32_t> node_base(n_meshes), rec_base(n_meshes);
+    std::vector<std::array<double, 6>> mesh_box(n_meshes);
+    for (uint32_t m = 0; m < n_meshes; ++m) {
+        pt::BvhOut bvh;
+        std::string err;
+        if (!pt::build_bvh(verts[m], tris[m], n_tris[m], bvh, err))
+            return bail(fail(PT_ERR_INVALID_ARG, "mesh %u: BVH build: %s", m, err.c_str()));
+        node_base[m] = (uint32_t)(nodes.size() / 16);
+        rec_base[m] = (uint32_t)(trec.size() / 12);
+        const uint32_t nb = node_base[m], rb = rec_base[m];
+        for (size_t n = 0; n < bvh.nodes.size() / 16; ++n) {
+            float f[16];
+            std::memcpy(f, &bvh.nodes[16 * n], sizeof f);
+            for (int c = 12; c < 14; ++c) {
+                uint32_t ref = ubits(f[c]);
+                if (ref & 0x80000000u) {
+                    const uint32_t first = (ref & 0x7FFFFFFFu) >> 3, cnt = ref & 7u;
+                    ref = 0x80000000u | ((first + rb) << 3) | cnt;
+                } else {
+                    ref += nb;
+                }
+                f[c] = bits(ref);
+            }
+            nodes.insert(nodes.end(), f, f + 16);
+        }
+        std::array<double, 6> box = {1e300, 1e300, 1e300, -1e300, -1e300, -1e300};
+        for (uint32_t k = 0; k < n_tris[m]; ++k) {
+            const uint32_t i = bvh.order[k];
+            const float* pa = verts[m] + 3 * (size_t)tris[m][3 * (size_t)i];
+            const float* pb = verts[m] + 3 * (size_t)tris[m][3 * (size_t)i + 1];
+            const float* pc = verts[m] + 3 * (size_t)tris[m][3 * (size_t)i + 2];
+            const uint32_t mat = tri_material[m][i];
+            const float r[12] = {pa[0], pa[1], pa[2], bits(i), pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2], bits(mat),
+                                 pc[0] - pa[0], pc[1] - pa[1], pc[2] - pa[2], bits(mats[mat].emission > 0.f ? 1u : 0u)};
+            trec.insert(trec.end(), r, r + 12);
+            for (const float* p : {pa, pb, pc})
+                for (int c = 0; c < 3; ++c) {
+                    box[c] = std::min(box[c], (double)p[c]);
+                    box[3 + c] = std::max(box[3 + c], (double)p[c]);
+                }
+        }
+        mesh_box[m] = box;
+    }
+    // top level: the instances' world boxes (the 8 transformed corners of the mesh box, padded a
+    // few ulps outward), built as degenerate triangles (lo, hi, hi) so the same builder applies
+    std::vector<float> ibox(6 * (size_t)n_instances);
+    std::vector<uint32_t> itri(3 * (size_t)n_instances);
+    for (uint32_t i = 0; i < n_instances; ++i) {
+        const pt_instance& I = instances[i];
+        const auto& b = mesh_box[I.mesh];
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int corner = 0; corner < 8; ++corner) {
+            const double p[3] = {corner & 1 ? b[3] : b[0], corner & 2 ? b[4] : b[1], corner & 4 ? b[5] : b[2]};
+            for (int r = 0; r < 3; ++r) {
+                const double w = I.xform[4 * r] * p[0] + I.xform[4 * r + 1] * p[1] + I.xform[4 * r + 2] * p[2] + I.xform[4 * r + 3];
+                lo[r] = std::min(lo[r], w);
+                hi[r] = std::max(hi[r], w);
+            }
+        }
+        double ext = 0;
+        for (int r = 0; r < 3; ++r) ext = std::max(ext, std::max(std::fabs(lo[r]), std::fabs(hi[r])));
+        const double pad = 1e-6 * ext + 1e-30;
+        for (int r = 0; r < 3; ++r) {
+            ibox[6 * (size_t)i + r] = std::nextafter((float)(lo[r] - pad), -INFINITY);
+            ibox[6 * (size_t)i + 3 + r] = std::nextafter((float)(hi[r] + pad), INFINITY);
+        }
+        itri[3 * (size_t)i] = 2 * i;
+        itri[3 * (size_t)i + 1] = 2 * i + 1;
+        itri[3 * (size_t)i + 2] = 2 * i + 1;
+    }
+    pt::BvhOut top;
+    std::string err;
+    if (!pt::build_bvh(ibox.data(), itri.data(), n_instances, top, err))
+        return bail(fail(PT_ERR_INVALID_ARG, "top-level BVH build: %s", err.c_str()));
+    std::vector<uint32_t> prim_base(n_instances);
+    {
+        uint64_t acc = 0;
+        for (uint32_t i = 0; i < n_instances; ++i) {
+            prim_base[i] = (uint32_t)acc;
+            acc += n_tris[instances[i].mesh];
+        }
+    }
+    // instance records in top-level leaf order
+    std::vector<float> irec(24 * (size_t)n_instances);
+    for (uint32_t k = 0; k < n_instances; ++k) {
+        const uint32_t i = top.order[k];
+        const pt_instance& I = instances[i];
+        float* r = &irec[24 * (size_t)k];
+        for (int q = 0; q < 12; ++q) r[q] = (float)inv[12 * (size_t)i + q];
+        for (int row = 0; row < 3; ++row)
+            for (int c = 0; c < 3; ++c) r[12 + 4 * row + c] = I.xform[4 * row + c];
+        uint32_t mw = 0;
+        if (I.material != PT_NO_MATERIAL) mw = (I.material + 1u) | (mats[I.material].emission > 0.f ? 0x80000000u : 0u);
+        r[15] = bits(node_base[I.mesh]);
+        r[19] = bits(prim_base[i]);
+        r[23] = bits(mw);
+    }
+    // lights: every instance's emissive triangles in the world, ascending triangle id
+    std::vector<float> lrec;
+    std::vector<double> areas;
+    for (uint32_t i = 0; i < n_instances; ++i) {
+        const pt_instance& I = instances[i];
+        const uint32_t m = I.mesh;
+        for (uint32_t j = 0; j < n_tris[m]; ++j) {
+            const uint32_t mat = I.material != PT_NO_MATERIAL ? I.material : tri_material[m][j];
+            if (!(mats[mat].emission > 0.f)) continue;
+            double w[3][3];
+            for (int v = 0; v < 3; ++v) {
+                const float* p = verts[m] + 3 * (size_t)tris[m][3 * (size_t)j + v];
+                for (int r = 0; r < 3; ++r)
+                    w[v][r] = I.xform[4 * r] * (double)p[0] + I.xform[4 * r + 1] * (double)p[1] +
+                              I.xform[4 * r + 2] * (double)p[2] + I.xform[4 * r + 3];
+            }
+            double e1[3], e2[3];
+            for (int r = 0; r < 3; ++r) {
+                e1[r] = w[1][r] - w[0][r];
+                e2[r] = w[2][r] - w[0][r];
+            }
+            const double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2],
+                         cz = e1[0] * e2[1] - e1[1] * e2[0];
+            areas.push_back(0.5 * std::sqrt(cx * cx + cy * cy + cz * cz));
+            const float rec[12] = {(float)w[0][0], (float)w[0][1], (float)w[0][2], bits(mat),
+                                   (float)w[1][0], (float)w[1][1], (float)w[1][2], 0.f,
+                                   (float)w[2][0], (float)w[2][1], (float)w[2][2], 0.f};
+            lrec.insert(lrec.end(), rec, rec + 12);
+        }
+    }
+    sc->n_lights = areas.size();
+    std::vector<float> cdf(std::max<size_t>(areas.size(), 1), 0.f);
+    double total = 0;
+    for (double x : areas) total += x;
+    double acc = 0;
+    for (size_t j = 0; j < areas.size(); ++j) {
+        acc += areas[j];
+        cdf[j] = total > 0 ? (float)(acc / total) : 0.f;
+    }
+    if (!areas.empty() && total > 0) cdf.back() = 1.0f;
+    sc->light_area = (float)total;
+    sc->n_nodes = nodes.size() / 16 + top.nodes.size() / 16;
+    std::vector<pt::DevMat> dm(n_mats);
+    for (uint32_t m = 0; m < n_mats; ++m) {
+        const pt_material& M = mats[m];
+        dm[m] = pt::DevMat{M.type, M.albedo[0], M.albedo[1], M.albedo[2], M.emission, M.roughness, M.ior, 0u};
+    }
+    pt_status s;
+    if ((s = sc->nodes.ensure(nodes.size() * 4)) != PT_OK) return bail(s);
+    if ((s = sc->tris.ensure(trec.size() * 4)) != PT_OK) return bail(s);
+    if ((s = sc->tlas.ensure(top.nodes.size() * 4)) != PT_OK) return bail(s);
+    if ((s = sc->inst.ensure(irec.size() * 4)) != PT_OK) return bail(s);
+    if ((s = sc->mats.ensure(dm.size() * sizeof(pt::DevMat))) != PT_OK) return bail(s);
+    if ((s = sc->lights.ensure(std::max<size_t>(lrec.size() * 4, 48))) != PT_OK) return bail(s);
+    if ((s = sc->cdf.ensure(cdf.size() * 4)) != PT_OK) return bail(s);
+    if ((s = sc->status.ensure(256)) != PT_OK) return bail(s);
+    if ((s = sc->ensure_counters()) != PT_OK) return bail(s);
+    cudaError_t e = cudaMemcpyAsync(sc->nodes.p, nodes.data(), nodes.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sc->tris.p, trec.data(), trec.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sc->tlas.p, top.nodes.data(), top.nodes.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sc->inst.p, irec.data(), irec.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sc->mats.p, dm.data(), dm.size() * sizeof(pt::DevMat), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !lrec.empty()) e = cudaMemcpyAsync(sc->lights.p, lrec.data(), lrec.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sc->cdf.p, cdf.data(), cdf.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc->status.p, 0, 256, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc->counters.p, 0, sc->counters.bytes, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(PT_ERR_CUDA, "scene upload: %s", cudaGetErrorString(e)));
+    }
+    sc->last_stream = st;
+    *out = sc;
+    return PT_OK;
+}
+
 void pt_scene_destroy(pt_scene* scene) {
     if (!scene) return;
     if (scene->last_stream) cudaStreamSynchronize(scene->last_stream);
@@ -949,8 +1229,9 @@ pt_status pt_scene_info(const pt_scene* sc, uint64_t* n_tris, uint64_t* n_nodes,
     if (n_lights) *n_lights = sc->n_lights;
     if (light_area) *light_area = sc->light_area;
     if (device_bytes)
-        *device_bytes = sc->nodes.bytes + sc->tris.bytes + sc->mats.bytes + sc->lights.bytes + sc->cdf.bytes +
-                        sc->wf.bytes + sc->pathL.bytes + sc->img_stage.bytes + sc->grad_stage.bytes + sc->counters.bytes;
+        *device_bytes = sc->nodes.bytes + sc->tris.bytes + sc->tlas.bytes + sc->inst.bytes + sc->mats.bytes +
+                        sc->lights.bytes + sc->cdf.bytes + sc->wf.bytes + sc->pathL.bytes + sc->img_stage.bytes +
+                        sc->grad_stage.bytes + sc->counters.bytes + sc->adj.bytes;
     return PT_OK;
 }
 

@@ -387,17 +387,35 @@ __device__ __forceinline__ uint32_t pick_light(const DevScene& s, float u) {
 // Shade the hit of ray (o, d) at distance t on reordered triangle `tri`.  MIS = false compiles the
 // multiple-importance terms out (the megakernels are instantiated both ways, since the extra code
 // costs them registers); with MIS = true they apply when p.mis is set.
-template <bool MIS = true>
+template <bool MIS = true, bool INST = false>
 __device__ __forceinline__ Vertex shade_vertex(const DevScene& s, const RenderParams& p, uint32_t key, uint32_t b,
                                                float3 o, float3 d, float3 tp, bool prev_delta, float prev_pdf,
-                                               float t, uint32_t tri) {
+                                               float t, uint32_t tri, uint32_t inst = 0xFFFFFFFFu) {
     Vertex V;
     const float4* tr = s.tris + 3 * (size_t)tri;
     float4 t0 = __ldg(tr), t1 = __ldg(tr + 1), t2 = __ldg(tr + 2);
     V.prim = __float_as_uint(t0.w);
     V.mat = __float_as_uint(t1.w);
     bool is_light = __float_as_uint(t2.w) != 0u;
-    float3 ng = normalize(cross(xyz(t1), xyz(t2)));
+    float3 ng;
+    if (INST) {
+        // two-level scene: the mesh's object-space edges taken to the world by the instance's
+        // rotation/scale rows; the instance may replace the material
+        const float4* ip = s.inst + 6 * (size_t)inst;
+        const float4 m0 = __ldg(ip + 3), m1 = __ldg(ip + 4), m2 = __ldg(ip + 5);
+        const float3 e1 = xyz(t1), e2 = xyz(t2);
+        const float3 E1 = f3(dot(xyz(m0), e1), dot(xyz(m1), e1), dot(xyz(m2), e1));
+        const float3 E2 = f3(dot(xyz(m0), e2), dot(xyz(m1), e2), dot(xyz(m2), e2));
+        ng = normalize(cross(E1, E2));
+        V.prim += __float_as_uint(m1.w);
+        const uint32_t mw = __float_as_uint(m2.w);
+        if (mw != 0u) {
+            V.mat = (mw & 0x7FFFFFFFu) - 1u;
+            is_light = (mw >> 31) != 0u;
+        }
+    } else {
+        ng = normalize(cross(xyz(t1), xyz(t2)));
+    }
     float3 x = o + d * t;
     MatV m = load_mat(s.mats, V.mat);
     bool front = dot(d, ng) < 0.0f;

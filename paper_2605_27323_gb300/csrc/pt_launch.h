@@ -1,4 +1,4 @@
-// pt_launch.h -- host-callable launchers of the CUDA kernels (defined in pt_kernels.cu), used by
+// pt_launch.h -- host-callable launchers of the CUDA kernels (defined in the pt_k_*.cu units), used by
 // the C-ABI layer (pt_api.cpp).  Every launcher is asynchronous on `st` and returns the launch error.
 #pragma once
 #include <cstdint>
@@ -90,6 +90,11 @@ cudaError_t launch_debug_rng(const Launch& l, uint64_t seed, const uint32_t* px,
                              const uint32_t* bo, const uint32_t* dm, uint32_t n, float* out);
 
 // Occupancy helpers.
+// occupancy of each kernel unit's kernels (0 when `which` is not one of them)
+int occupancy_mega(int which, int block);
+int occupancy_mega_static(int which, int block);
+int occupancy_wave(int which, int block);
+int occupancy_adj(int which, int block);
 int max_blocks_per_sm(int which, int block);   // which: 0 megakernel, 1 extend, 2 shade, 3 shadow, 4 adjoint
 enum { K_MEGA = 0, K_EXTEND = 1, K_SHADE = 2, K_SHADOW = 3, K_ADJOINT = 4, K_EXTEND_BATCH = 5, K_SHADE_BATCH = 6,
        K_SHADOW_BATCH = 7, K_SHADE_ADJ = 8, K_SHADOW_ADJ = 9,

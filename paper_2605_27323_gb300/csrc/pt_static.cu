@@ -30,7 +30,7 @@ bool static_is_device_ptr(const void* p);
 namespace {
 
 constexpr size_t kStaticScratchBytes = 32ull << 20;
-constexpr size_t kBytesPerPath = 176;           // the wavefront's per-path queue records
+constexpr size_t kBytesPerPath = 180;           // the wavefront's per-path queue records
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
@@ -61,7 +61,7 @@ pt_status scratch_address(int device, unsigned char** out) {
 
 // Paths one wave can hold after the fixed regions (counters, histories, sort buckets).
 uint64_t wave_capacity() {
-    size_t fixed = a256(256) + a256(8 * 128) + a256(pt::kMaxSortKeys * 4) + 16 * 256;
+    size_t fixed = a256(256) + a256(8 * 128) + a256(pt::kMaxSortKeys * 4) + 17 * 256;
     return (kStaticScratchBytes - fixed) / kBytesPerPath;
 }
 
@@ -121,6 +121,7 @@ extern "C" pt_status pt_render_wavefront_static(pt_scene* scene, const pt_camera
         w.q_tp[i] = reinterpret_cast<float4*>(take(cap * 16));
     }
     w.hit = reinterpret_cast<float2*>(take(cap * 8));
+    w.hit_inst = reinterpret_cast<uint32_t*>(take(cap * 4));
     w.keys = reinterpret_cast<uint32_t*>(take(cap * 4));
     w.perm = reinterpret_cast<uint32_t*>(take(cap * 4));
     w.s_o = reinterpret_cast<float4*>(take(cap * 16));

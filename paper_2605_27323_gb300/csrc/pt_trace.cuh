@@ -1,7 +1,8 @@
 // pt_trace.cuh -- BVH traversal (the scene-intersection stage of Sec. 2.3, "extend" of Sec. 2.2
 // step 2, and the shadow-evaluation query of Sec. 3), written for CUDA cores: the paper's hardware
 // ray queries are not reachable here, so traversal is a software loop over a host-built binary
-// BVH.
+// BVH -- one over all triangles, or (two-level scenes, the paper's TLAS/BLAS structure of Sec. 2.3)
+// one over instances whose leaves lead into per-mesh BVHs.
 //
 // Node layout (64 bytes, one 128-bit load per row, both children's boxes in the parent):
 //   n0 = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
@@ -26,6 +27,8 @@ constexpr uint32_t kLeafBit = 0x80000000u;
 struct Hit {
     float t;
     uint32_t tri;    // reordered triangle index, kMiss on miss
+    uint32_t prim;   // original triangle id (two-level scenes: the instance's first id + the mesh's)
+    uint32_t inst;   // instance (top-level leaf order) of a two-level scene, kMiss otherwise
 };
 
 __device__ __forceinline__ float3 ray_rcp(float3 d) {
@@ -144,6 +147,8 @@ __device__ __forceinline__ Hit trace_closest_plain(const DevScene& s, float3 o, 
     Hit h;
     h.t = tbest;
     h.tri = best;
+    h.prim = bprim;
+    h.inst = kMiss;
     return h;
 }
 
@@ -189,12 +194,248 @@ __device__ __forceinline__ bool trace_any_plain(const DevScene& s, float3 o, flo
     }
 }
 
+// ------------------------------------------------------------------ two-level scenes
+// The top-level BVH (same node layout) has instances in its leaves.  A ray entering an instance's
+// box is taken to the mesh's object space (o' = A o + b, d' = A d, d' not renormalised, so the
+// parameter t is the world one) and walks the mesh's BVH from its root; equal t still goes to the
+// lower original triangle id (the instance's first id + the mesh-local id).
+
+struct InstRay {
+    float3 o, d;
+    uint32_t root, prim_base;
+};
+
+__device__ __forceinline__ InstRay instance_ray(const DevScene& s, uint32_t k, float3 o, float3 d) {
+    const float4* p = s.inst + 6 * (size_t)k;
+    const float4 a0 = __ldg(p), a1 = __ldg(p + 1), a2 = __ldg(p + 2);
+    InstRay r;
+    r.o = f3(__fadd_rn(dot(xyz(a0), o), a0.w), __fadd_rn(dot(xyz(a1), o), a1.w), __fadd_rn(dot(xyz(a2), o), a2.w));
+    r.d = f3(dot(xyz(a0), d), dot(xyz(a1), d), dot(xyz(a2), d));
+    r.root = __float_as_uint(__ldg(p + 3).w);
+    r.prim_base = __float_as_uint(__ldg(p + 4).w);
+    return r;
+}
+
+// Closest hit inside one mesh (object-space ray), updating the running best over instances.
+__device__ __forceinline__ void blas_closest(const DevScene& s, const InstRay& r, uint32_t k, float& tbest,
+                                             uint32_t& best, uint32_t& bprim, uint32_t& binst, uint32_t& steps) {
+    const float3 id = ray_rcp(r.d);
+    uint32_t stack_ref[kStack];
+    float stack_t[kStack];
+    int sp = 0;
+    uint32_t ref = r.root;
+    while (true) {
+        if (!(ref & kLeafBit)) {
+            float4 n0, n1, n2;
+            uint2 c;
+            load_node(s.nodes, ref, n0, n1, n2, c);
+            float t0, t1;
+            bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, r.o, id, tbest, t0);
+            bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, r.o, id, tbest, t1);
+            if (h0 && h1) {
+                bool first0 = t0 <= t1;
+                if (sp < kStack) {
+                    stack_ref[sp] = first0 ? c.y : c.x;
+                    stack_t[sp] = first0 ? t1 : t0;
+                    ++sp;
+                } else {
+                    atomicOr(s.status, ST_TRAVERSAL);
+                }
+                ref = first0 ? c.x : c.y;
+                if (++steps < kMaxSteps) continue;
+            } else if (h0 || h1) {
+                ref = h0 ? c.x : c.y;
+                if (++steps < kMaxSteps) continue;
+            }
+        } else {
+            uint32_t first = (ref & 0x7FFFFFFFu) >> 3, cnt = (ref & 7u) + 1u;
+            for (uint32_t q = 0; q < cnt; ++q) {
+                float t;
+                uint32_t prim;
+                if (tri_test(s.tris, first + q, r.o, r.d, t, prim) && t > 0.0f) {
+                    const uint32_t gp = r.prim_base + prim;
+                    if (t < tbest || (t == tbest && gp < bprim)) {
+                        tbest = t;
+                        best = first + q;
+                        bprim = gp;
+                        binst = k;
+                    }
+                }
+            }
+        }
+        if (steps >= kMaxSteps) {
+            atomicOr(s.status, ST_TRAVERSAL);
+            return;
+        }
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            if (stack_t[sp] <= tbest * 1.0000005f) {
+                ref = stack_ref[sp];
+                found = true;
+                break;
+            }
+        }
+        if (!found) return;
+        ++steps;
+    }
+}
+
+__device__ __forceinline__ bool blas_any(const DevScene& s, const InstRay& r, float tmax, uint32_t& steps) {
+    const float3 id = ray_rcp(r.d);
+    uint32_t stack_ref[kStack];
+    int sp = 0;
+    uint32_t ref = r.root;
+    while (true) {
+        if (!(ref & kLeafBit)) {
+            float4 n0, n1, n2;
+            uint2 c;
+            load_node(s.nodes, ref, n0, n1, n2, c);
+            float t0, t1;
+            bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, r.o, id, tmax, t0);
+            bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, r.o, id, tmax, t1);
+            if (h0 && h1) {
+                if (sp < kStack) stack_ref[sp++] = c.y;
+                else atomicOr(s.status, ST_TRAVERSAL);
+                ref = c.x;
+                if (++steps < kMaxSteps) continue;
+            } else if (h0 || h1) {
+                ref = h0 ? c.x : c.y;
+                if (++steps < kMaxSteps) continue;
+            }
+        } else {
+            uint32_t first = (ref & 0x7FFFFFFFu) >> 3, cnt = (ref & 7u) + 1u;
+            for (uint32_t q = 0; q < cnt; ++q) {
+                float t;
+                uint32_t prim;
+                if (tri_test(s.tris, first + q, r.o, r.d, t, prim) && t > 0.0f && t < tmax) return true;
+            }
+        }
+        if (steps >= kMaxSteps) {
+            atomicOr(s.status, ST_TRAVERSAL);
+            return false;
+        }
+        if (sp == 0) return false;
+        ref = stack_ref[--sp];
+        ++steps;
+    }
+}
+
+__device__ __forceinline__ Hit trace_closest_inst(const DevScene& s, float3 o, float3 d) {
+    const float3 id = ray_rcp(d);
+    float tbest = __int_as_float(0x7f800000);
+    uint32_t best = kMiss, bprim = kMiss, binst = kMiss;
+    uint32_t stack_ref[kStack];
+    float stack_t[kStack];
+    int sp = 0;
+    uint32_t ref = 0;
+    uint32_t steps = 0;
+    while (true) {
+        if (!(ref & kLeafBit)) {
+            float4 n0, n1, n2;
+            uint2 c;
+            load_node(s.tlas, ref, n0, n1, n2, c);
+            float t0, t1;
+            bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tbest, t0);
+            bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tbest, t1);
+            if (h0 && h1) {
+                bool first0 = t0 <= t1;
+                if (sp < kStack) {
+                    stack_ref[sp] = first0 ? c.y : c.x;
+                    stack_t[sp] = first0 ? t1 : t0;
+                    ++sp;
+                } else {
+                    atomicOr(s.status, ST_TRAVERSAL);
+                }
+                ref = first0 ? c.x : c.y;
+                if (++steps < kMaxSteps) continue;
+            } else if (h0 || h1) {
+                ref = h0 ? c.x : c.y;
+                if (++steps < kMaxSteps) continue;
+            }
+        } else {
+            uint32_t first = (ref & 0x7FFFFFFFu) >> 3, cnt = (ref & 7u) + 1u;
+            for (uint32_t q = 0; q < cnt; ++q) {
+                const InstRay r = instance_ray(s, first + q, o, d);
+                blas_closest(s, r, first + q, tbest, best, bprim, binst, steps);
+            }
+        }
+        if (steps >= kMaxSteps) {
+            atomicOr(s.status, ST_TRAVERSAL);
+            break;
+        }
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            if (stack_t[sp] <= tbest * 1.0000005f) {
+                ref = stack_ref[sp];
+                found = true;
+                break;
+            }
+        }
+        if (!found) break;
+        ++steps;
+    }
+    Hit h;
+    h.t = tbest;
+    h.tri = best;
+    h.prim = bprim;
+    h.inst = binst;
+    return h;
+}
+
+__device__ __forceinline__ bool trace_any_inst(const DevScene& s, float3 o, float3 d, float tmax) {
+    const float3 id = ray_rcp(d);
+    uint32_t stack_ref[kStack];
+    int sp = 0;
+    uint32_t ref = 0;
+    uint32_t steps = 0;
+    while (true) {
+        if (!(ref & kLeafBit)) {
+            float4 n0, n1, n2;
+            uint2 c;
+            load_node(s.tlas, ref, n0, n1, n2, c);
+            float t0, t1;
+            bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tmax, t0);
+            bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tmax, t1);
+            if (h0 && h1) {
+                if (sp < kStack) stack_ref[sp++] = c.y;
+                else atomicOr(s.status, ST_TRAVERSAL);
+                ref = c.x;
+                if (++steps < kMaxSteps) continue;
+            } else if (h0 || h1) {
+                ref = h0 ? c.x : c.y;
+                if (++steps < kMaxSteps) continue;
+            }
+        } else {
+            uint32_t first = (ref & 0x7FFFFFFFu) >> 3, cnt = (ref & 7u) + 1u;
+            for (uint32_t q = 0; q < cnt; ++q)
+                if (blas_any(s, instance_ray(s, first + q, o, d), tmax, steps)) return true;
+        }
+        if (steps >= kMaxSteps) {
+            atomicOr(s.status, ST_TRAVERSAL);
+            return false;
+        }
+        if (sp == 0) return false;
+        ref = stack_ref[--sp];
+        ++steps;
+    }
+}
+
 // The extend and shadow queries.  (A "while-while" variant that voted across the warp with
 // __any_sync(__activemask(), ...) was tried and removed: its result depended on which paths shared a
 // warp -- lanes that are not converged may pass different masks to the vote -- so one path in 33M
 // differed between the megakernel and the wavefront.)
-__device__ __forceinline__ Hit trace_closest(const DevScene& s, float3 o, float3 d) { return trace_closest_plain(s, o, d); }
+// INST selects the two-level traversal at compile time (kernels are instantiated both ways, so the
+// single-level kernels carry none of its registers).
+template <bool INST = false>
+__device__ __forceinline__ Hit trace_closest(const DevScene& s, float3 o, float3 d) {
+    if (INST) return trace_closest_inst(s, o, d);
+    return trace_closest_plain(s, o, d);
+}
+template <bool INST = false>
 __device__ __forceinline__ bool trace_any(const DevScene& s, float3 o, float3 d, float tmax) {
+    if (INST) return trace_any_inst(s, o, d, tmax);
     return trace_any_plain(s, o, d, tmax);
 }
 

@@ -27,6 +27,13 @@ struct DevScene {
     float env_r, env_g, env_b;
     uint32_t n_mats;
     uint32_t* status;                      // device status word (atomicOr of fault bits)
+    // two-level scenes: `nodes`/`tris` hold every mesh's BVH and object-space triangles, `tlas` the
+    // top-level BVH over the instances, `inst` 6 float4 per instance in top-level leaf order:
+    //   i0..i2 = world-to-object rows (A | b), i3..i5 = object-to-world rotation/scale rows with
+    //   w = (mesh root node, first triangle id of the instance, material word); the material word
+    //   is 0 (the mesh's materials) or (material + 1) | (material emitted at creation) << 31.
+    const float4* __restrict__ tlas = nullptr;
+    const float4* __restrict__ inst = nullptr;
 };
 
 struct DevCamera {         // U = u * tan(fov/2) * aspect, V = v * tan(fov/2), Wd = w (view -> eye)
@@ -64,6 +71,7 @@ struct WfBuffers {
     float4* q_d[2];          // d.xyz | flags (bit 0: previous vertex was delta)
     float4* q_tp[2];         // throughput.xyz | solid-angle density of the BSDF sample (MIS weights)
     float2* hit;             // per queue slot: t, reordered triangle bits (0xFFFFFFFF: miss)
+    uint32_t* hit_inst;      // per queue slot: instance of the hit (two-level scenes only)
     uint32_t* keys;          // per queue slot: sort key
     uint32_t* perm;          // per sorted position: queue slot
     uint32_t* bucket;        // sort: per-key counts, then running offsets (up to kMaxSortKeys)

@@ -35,8 +35,8 @@ instances in order, each mesh's triangles in order.
 
 * ``instanced_spheres_scene`` / ``instanced_terrain_scene`` -- the spheres and terrain recipes with
   one icosphere mesh (and one light quad) placed by instances;
-* ``split_as_instances`` -- any flat scene cut into meshes placed by exact transforms (signed axis
-  permutations times powers of two), so that the instanced scene is the flat one exactly.
+* ``split_as_instances`` -- any flat scene cut into meshes placed by exact transforms (axis sign
+  flips times powers of two), so that the instanced scene is the flat one exactly.
 """
 from __future__ import annotations
 
@@ -202,16 +202,17 @@ def instance_tri_count(sc) -> int:
 
 def split_as_instances(sc: dict, n_pieces: int = 5, seed: int = 0) -> dict:
     """The flat scene `sc` cut into n_pieces meshes (contiguous triangle ranges), each stored in its
-    own object frame and placed back by an exact transform: a signed axis permutation times a power
-    of two (world = 2^k P v, object vertices 2^-k P^T v, both exact in FP32).  Triangle ids,
-    materials and world geometry equal the flat scene's."""
+    own object frame and placed back by an exact transform: axis sign flips times a power of two
+    (world = 2^k S v, object vertices 2^-k S v, both exact in FP32; no axis permutation, so every
+    sum and product is formed in the same order as in world space).  Triangle ids, materials and
+    world geometry equal the flat scene's."""
     rng = np.random.default_rng(seed)
     V, T, M = np.asarray(sc["verts"], np.float32), np.asarray(sc["tris"]), np.asarray(sc["tri_mat"])
     cuts = np.linspace(0, len(T), n_pieces + 1).round().astype(int)
     meshes, xf = [], []
     for a, b in zip(cuts[:-1], cuts[1:]):
         used, inv = np.unique(T[a:b].ravel(), return_inverse=True)
-        P = np.eye(3)[rng.permutation(3)] * rng.choice([-1.0, 1.0], size=3)[:, None]
+        P = np.diag(rng.choice([-1.0, 1.0], size=3))
         k = int(rng.integers(-3, 4))
         obj = ((V[used].astype(np.float64) @ P) * 2.0 ** (-k)).astype(np.float32)   # P^T v, row form
         meshes.append((obj, inv.reshape(-1, 3), M[a:b]))

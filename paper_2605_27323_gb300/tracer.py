@@ -57,8 +57,25 @@ def make_opts(mode="wavefront", rr_start=3, rr_fixed=0.0, sort="none", block_siz
     return o
 
 
+def _materials(sc: dict):
+    mt = np.asarray(sc["mat_type"], np.uint32).reshape(-1)
+    ma = np.asarray(sc["mat_albedo"], np.float32).reshape(-1, 3)
+    me = np.asarray(sc["mat_emission"], np.float32).reshape(-1)
+    mr = np.asarray(sc["mat_roughness"], np.float32).reshape(-1)
+    mi = np.asarray(sc["mat_ior"], np.float32).reshape(-1)
+    n_m = mt.size
+    mats = (capi.Material * max(n_m, 1))()
+    for k in range(n_m):
+        mats[k].type = int(mt[k])
+        mats[k].albedo[:] = [float(x) for x in ma[k]]
+        mats[k].emission = float(me[k])
+        mats[k].roughness = float(mr[k])
+        mats[k].ior = float(mi[k])
+    return mats
+
+
 class Scene:
-    """A scene uploaded to the current CUDA device (pt_scene_create)."""
+    """A scene uploaded to the current CUDA device (pt_scene_create, pt_scene_create_instanced)."""
 
     def __init__(self, verts, tris, tri_mat, mat_type, mat_albedo, mat_emission, mat_roughness, mat_ior,
                  env=(0.0, 0.0, 0.0)):
@@ -68,18 +85,8 @@ class Scene:
         t = np.ascontiguousarray(tris, np.uint32).reshape(-1, 3)
         tm = np.ascontiguousarray(tri_mat, np.uint32).reshape(-1)
         n_m = int(np.asarray(mat_type).size)
-        mats = (capi.Material * max(n_m, 1))()
-        mt = np.asarray(mat_type, np.uint32).reshape(-1)
-        ma = np.asarray(mat_albedo, np.float32).reshape(-1, 3)
-        me = np.asarray(mat_emission, np.float32).reshape(-1)
-        mr = np.asarray(mat_roughness, np.float32).reshape(-1)
-        mi = np.asarray(mat_ior, np.float32).reshape(-1)
-        for k in range(n_m):
-            mats[k].type = int(mt[k])
-            mats[k].albedo[:] = [float(x) for x in ma[k]]
-            mats[k].emission = float(me[k])
-            mats[k].roughness = float(mr[k])
-            mats[k].ior = float(mi[k])
+        mats = _materials({"mat_type": mat_type, "mat_albedo": mat_albedo, "mat_emission": mat_emission,
+                           "mat_roughness": mat_roughness, "mat_ior": mat_ior})
         envv = (C.c_float * 3)(*[float(x) for x in np.asarray(env, np.float32).reshape(3)])
         h = C.c_void_p()
         capi.check(self._lib.pt_scene_create(v.ctypes.data_as(C.c_void_p), v.shape[0], t.ctypes.data_as(C.c_void_p),
@@ -91,8 +98,53 @@ class Scene:
 
     @classmethod
     def from_dict(cls, sc: dict) -> "Scene":
+        if "meshes" in sc:
+            return cls.from_instanced(sc)
         return cls(sc["verts"], sc["tris"], sc["tri_mat"], sc["mat_type"], sc["mat_albedo"], sc["mat_emission"],
                    sc["mat_roughness"], sc["mat_ior"], sc["env"])
+
+    @classmethod
+    def from_instanced(cls, sc: dict) -> "Scene":
+        """A two-level scene (pt_scene_create_instanced): sc["meshes"] = [{verts, tris, tri_mat}] in object
+        space; sc["inst_mesh"] (I,), sc["inst_xform"] (I, 3, 4) object-to-world [R | t], sc["inst_mat"] (I,)
+        (capi.NO_MATERIAL keeps the mesh's materials)."""
+        torch = _torch()
+        self = cls.__new__(cls)
+        self._lib = capi.load()
+        meshes = sc["meshes"]
+        nm = len(meshes)
+        keep = []
+        vp = (C.c_void_p * nm)()
+        tp = (C.c_void_p * nm)()
+        mp = (C.c_void_p * nm)()
+        nv = (C.c_uint32 * nm)()
+        nt = (C.c_uint32 * nm)()
+        for k, m in enumerate(meshes):
+            v = np.ascontiguousarray(m["verts"], np.float32).reshape(-1, 3)
+            t = np.ascontiguousarray(m["tris"], np.uint32).reshape(-1, 3)
+            tm = np.ascontiguousarray(m["tri_mat"], np.uint32).reshape(-1)
+            keep += [v, t, tm]
+            vp[k], tp[k], mp[k] = v.ctypes.data, t.ctypes.data, tm.ctypes.data
+            nv[k], nt[k] = v.shape[0], t.shape[0]
+        im = np.asarray(sc["inst_mesh"], np.uint32).reshape(-1)
+        ix = np.asarray(sc["inst_xform"], np.float32).reshape(-1, 12)
+        imat = np.asarray(sc["inst_mat"], np.uint32).reshape(-1)
+        ni = im.size
+        inst = (capi.Instance * ni)()
+        for k in range(ni):
+            inst[k].xform[:] = [float(x) for x in ix[k]]
+            inst[k].mesh = int(im[k])
+            inst[k].material = int(imat[k])
+        mats = _materials(sc)
+        n_m = int(np.asarray(sc["mat_type"]).size)
+        envv = (C.c_float * 3)(*[float(x) for x in np.asarray(sc["env"], np.float32).reshape(3)])
+        h = C.c_void_p()
+        capi.check(self._lib.pt_scene_create_instanced(nm, vp, nv, tp, nt, mp, inst, ni, mats, n_m, envv,
+                                                       _stream(torch), C.byref(h)))
+        self.h = h
+        self.n_mats = n_m
+        self.n_tris = int(sum(int(nt[int(m)]) for m in im))
+        return self
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

@@ -2,8 +2,8 @@
 (world = R v + t), triangle ids run over the instances in order, and an instance material replaces
 its mesh's triangle materials.
 
-* a flat scene cut into meshes placed by exact transforms (signed axis permutations times powers
-  of two) renders exactly like the flat scene: same images and branch signatures, path by path;
+* a flat scene cut into meshes placed by exact transforms (axis sign flips times powers of
+  two) renders exactly like the flat scene: same images and branch signatures, path by path;
 * the white furnace placed by a rotated, scaled instance keeps its closed-form series;
 * direct light from a unit-square light mesh scaled non-uniformly into the rectangle keeps the
   point-to-rectangle form factor (the light's world area enters the light pdf);
