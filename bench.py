@@ -460,31 +460,36 @@ def run_large(args):
     res["hybrid"] = {"ms_per_frame": hyb[hyb_thr], "threshold": hyb_thr, "sweep_ms": hyb,
                      "wavefront_over_hybrid": res["wavefront"]["ms_per_frame"] / hyb[hyb_thr]}
     info = g.info()
-    # the same recipe as a two-level scene: one icosphere mesh placed 5000 times (TLAS/BLAS)
-    t0 = time.perf_counter()
-    isc = scenes.instanced_terrain_scene(seed=0)
-    gi = pt.Scene.from_dict(isc)
-    isetup = time.perf_counter() - t0
-    ires = {}
-    for mode in ("wavefront", "megakernel"):
-        for k in range(args.warmup):
-            gi.render(cam, spp, depth, 100 + k, mode=mode)
-        ms, rays = [], []
-        for k in range(max(3, min(args.steps, 10))):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            gi.render(cam, spp, depth, k, mode=mode)
-            e1.record(stream)
-            st = gi.stats()
-            ms.append(e0.elapsed_time(e1))
-            rays.append(st["extension_rays"] + st["shadow_rays"])
-        ires[mode] = {"ms_per_frame": float(np.mean(ms)),
-                      "mrays_s": float(np.sum(rays) / (np.sum(ms) * 1e-3) / 1e6)}
-    iinfo = gi.info()
-    ires.update({"triangles_placed": int(iinfo["n_tris"]), "device_bytes": int(iinfo["device_bytes"]),
-                 "scene_setup_s": isetup, "instances": int(len(isc["inst_mesh"])),
-                 "device_bytes_saved_vs_flat": int(info["device_bytes"]) - int(iinfo["device_bytes"])})
-    del gi
+    # the same recipe as a two-level scene: one icosphere mesh placed 5000 times (TLAS/BLAS), with the
+    # heightfield as one mesh or as 8 x 8 tile meshes
+    two_level = {}
+    for tiles in (1, 8):
+        t0 = time.perf_counter()
+        isc = scenes.instanced_terrain_scene(seed=0, tiles=tiles)
+        gi = pt.Scene.from_dict(isc)
+        isetup = time.perf_counter() - t0
+        ires = {}
+        for mode in ("wavefront", "megakernel"):
+            for k in range(args.warmup):
+                gi.render(cam, spp, depth, 100 + k, mode=mode)
+            ms, rays = [], []
+            for k in range(max(3, min(args.steps, 10))):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                gi.render(cam, spp, depth, k, mode=mode)
+                e1.record(stream)
+                st = gi.stats()
+                ms.append(e0.elapsed_time(e1))
+                rays.append(st["extension_rays"] + st["shadow_rays"])
+            ires[mode] = {"ms_per_frame": float(np.mean(ms)),
+                          "mrays_s": float(np.sum(rays) / (np.sum(ms) * 1e-3) / 1e6)}
+        iinfo = gi.info()
+        ires.update({"terrain_meshes": tiles * tiles, "instances": int(len(isc["inst_mesh"])),
+                     "triangles_placed": int(iinfo["n_tris"]), "device_bytes": int(iinfo["device_bytes"]),
+                     "device_bytes_saved_vs_flat": int(info["device_bytes"]) - int(iinfo["device_bytes"]),
+                     "scene_setup_s": isetup})
+        two_level[f"terrain_tiles_{tiles}x{tiles}"] = ires
+        del gi
     line = {"metric": "Mrays/s and ms/frame, large scene (3840x2160, 4 spp, depth 8)", "value": res["wavefront"]["mrays_s"],
             "unit": "Mrays/s", "n_gpus": 1, "steps": max(3, min(args.steps, 10)), "warmup": args.warmup,
             "ms_per_step": res["wavefront"]["ms_per_frame"], "higher_is_better": True, "scaling": "weak",
@@ -493,7 +498,7 @@ def run_large(args):
                        "triangles": int(info["n_tris"]), "bvh_nodes": int(info["n_nodes"]),
                        "device_bytes": int(info["device_bytes"]), "scene_setup_s": setup_s},
             "wavefront": res["wavefront"], "megakernel": res["megakernel"], "hybrid": res["hybrid"],
-            "two_level": ires,
+            "two_level": two_level,
             "wf_over_mk_speedup": res["megakernel"]["ms_per_frame"] / res["wavefront"]["ms_per_frame"]}
     print(json.dumps(line), flush=True)
 

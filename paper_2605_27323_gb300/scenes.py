@@ -275,10 +275,10 @@ def instanced_spheres_scene(seed: int = 0, n_spheres=200, level=4, ground_quads=
 
 
 def instanced_terrain_scene(seed: int = 0, grid=2048, n_spheres=5000, level=2, n_lights=64, width=3840,
-                            height=2160, extent=200.0, relief=12.0):
-    """The terrain recipe with real instancing: the heightfield as one mesh, one level-2 icosphere
-    mesh placed by n_spheres instances (uniform scale, translation, one of 253 materials each) and
-    one light quad mesh placed by n_lights instances."""
+                            height=2160, extent=200.0, relief=12.0, tiles=1):
+    """The terrain recipe with real instancing: the heightfield as one mesh (or tiles x tiles meshes
+    of contiguous quads), one level-2 icosphere mesh placed by n_spheres instances (uniform scale,
+    translation, one of 253 materials each) and one light quad mesh placed by n_lights instances."""
     rng = np.random.default_rng(seed)
     h = fbm(rng)
     scale = (grid - 1) / (2 * extent)
@@ -298,10 +298,23 @@ def instanced_terrain_scene(seed: int = 0, grid=2048, n_spheres=5000, level=2, n
     smat = rng.integers(0, n_sph_mats, size=n_spheres)
     hh = 4.0
     LV, LT = quad((-hh, 0.0, -hh), (hh, 0.0, -hh), (hh, 0.0, hh), (-hh, 0.0, hh))
-    meshes = [(GV, GT, np.full(len(GT), ground_mat)), (S, ST, np.zeros(len(ST))), (LV, LT, np.full(len(LT), light_mat))]
-    im, ix, imat = [0], [_xform()], [NO_MATERIAL]
+    meshes = [(S, ST, np.zeros(len(ST))), (LV, LT, np.full(len(LT), light_mat))]
+    im, ix, imat = [], [], []
+    # terrain tiles: quads (i, j) with i, j in a tile's range; both triangles of a quad stay together
+    n = grid - 1
+    qi = np.concatenate([np.arange(n * n), np.arange(n * n)]) % n          # quad column of each triangle
+    qj = np.concatenate([np.arange(n * n), np.arange(n * n)]) // n         # quad row
+    edges = np.linspace(0, n, tiles + 1).round().astype(int)
+    for tj in range(tiles):
+        for ti in range(tiles):
+            sel = np.flatnonzero((qi >= edges[ti]) & (qi < edges[ti + 1]) & (qj >= edges[tj]) & (qj < edges[tj + 1]))
+            used, inv = np.unique(GT[sel].ravel(), return_inverse=True)
+            meshes.append((GV[used], inv.reshape(-1, 3), np.full(len(sel), ground_mat)))
+            im.append(len(meshes) - 1)
+            ix.append(_xform())
+            imat.append(NO_MATERIAL)
     for k in range(n_spheres):
-        im.append(1)
+        im.append(0)
         ix.append(_xform(radii[k], (cx[k], cy[k], cz[k])))
         imat.append(smat[k])
     side = int(round(np.sqrt(n_lights)))
@@ -309,7 +322,7 @@ def instanced_terrain_scene(seed: int = 0, grid=2048, n_spheres=5000, level=2, n
         i, j = k % side, k // side
         x = -0.8 * extent + 1.6 * extent * (i + 0.5) / side
         z = -0.8 * extent + 1.6 * extent * (j + 0.5) / side
-        im.append(2)
+        im.append(1)
         ix.append(_xform(1.0, (x, 60.0, z)))
         imat.append(NO_MATERIAL)
     types = np.concatenate([types, [LAMBERT, LAMBERT]])
