@@ -11,6 +11,7 @@ the device.  Prints one JSON line (rank 0).
   python bench.py --workload batch      # 64 scenes in one persistent launch vs 64 renders
   python bench.py --workload large      # ~10M-triangle scene, 3840x2160, 4 spp, depth 8
   python bench.py --workload diff       # inverse rendering, 512x512, 64 spp, 256 materials
+  python bench.py --workload instanced  # the 1080p scene as a two-level (instanced) scene vs flat
 Under torchrun (N > 1) each rank renders its own frames (seed offset by rank, no collective on the
 data path: weak scaling); the barrier and max-over-ranks timing are the only communication.
 """
@@ -579,6 +580,54 @@ def run_diff(args):
     print(json.dumps(line), flush=True)
 
 
+def run_instanced(args):
+    """The 1080p procedural scene as a two-level scene (one icosphere mesh placed by 200 randomly
+    rotated, scaled instances; the ground and the light quads as meshes; 1,155,088 placed
+    triangles, 1 spp, depth 5) against the same recipe flattened into one BVH: wavefront and
+    megakernel frames, device-timed, L2 flushed between frames."""
+    import torch
+
+    import paper_2605_27323_gb300 as pt
+    from paper_2605_27323_gb300 import scenes
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    res = {}
+    for name, sc in (("two_level", scenes.instanced_spheres_scene(seed=0)),
+                     ("flat", scenes.spheres_scene(seed=0))):
+        g = pt.Scene.from_dict(sc)
+        cam, spp, depth = sc["camera"], sc["spp"], sc["max_depth"]
+        r = {}
+        for mode in ("wavefront", "megakernel"):
+            for k in range(args.warmup):
+                g.render(cam, spp, depth, 100 + k, mode=mode)
+            ms, rays = [], []
+            for k in range(args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.render(cam, spp, depth, k, mode=mode)
+                e1.record(stream)
+                st = g.stats()
+                ms.append(e0.elapsed_time(e1))
+                rays.append(st["extension_rays"] + st["shadow_rays"])
+                flush.fill_(k & 0xFF)
+            r[mode] = {"ms_per_frame": float(np.mean(ms)), "mrays_s": float(np.sum(rays) / (np.sum(ms) * 1e-3) / 1e6)}
+        info = g.info()
+        r["device_bytes"] = int(info["device_bytes"])
+        r["triangles"] = int(info["n_tris"])
+        res[name] = r
+        del g
+    line = {"metric": "Mrays/s and ms/frame, 1080p procedural scene as a two-level (instanced) scene",
+            "value": res["two_level"]["wavefront"]["mrays_s"], "unit": "Mrays/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["two_level"]["wavefront"]["ms_per_frame"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "200 rotated, scaled instances of one level-4 icosphere mesh + 256x256-quad ground "
+                                   "mesh + 8 light-quad instances, 1920x1080, 1 spp, depth 5",
+                       "l2": "flushed between frames (256 MiB write)"},
+            "two_level": res["two_level"], "flat": res["flat"],
+            "two_level_over_flat_time": res["two_level"]["wavefront"]["ms_per_frame"] / res["flat"]["wavefront"]["ms_per_frame"]}
+    print(json.dumps(line), flush=True)
+
+
 def run_batch(args):
     """64 procedural scenes (lognormal triangle counts in [1k, 2M], resolutions from {256^2, 512^2,
     1280x720, 1920x1080}, spp from {1, 4, 16}, depth 5): one persistent batched wavefront (autotuned
@@ -671,7 +720,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="frame", choices=["frame", "batch", "large", "diff"])
+    ap.add_argument("--workload", default="frame", choices=["frame", "batch", "large", "diff", "instanced"])
     ap.add_argument("--sort", default="none", choices=["none", "type", "material"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -688,6 +737,9 @@ def main():
         return
     if args.workload == "diff":
         run_diff(args)
+        return
+    if args.workload == "instanced":
+        run_instanced(args)
         return
     run_gpu(args)
 

@@ -62,6 +62,7 @@ struct Builder {
     const std::vector<Box>* tri_box;
     const std::vector<float>* cen;   // 3 per triangle
     uint32_t* idx;
+    uint32_t max_leaf = kMaxLeaf;
 
     void bounds(uint32_t first, uint32_t count, Box& b, Box& cb) const {
         b.reset();
@@ -86,7 +87,7 @@ struct Builder {
         return mid;
     }
 
-    // Binned SAH: returns the split position, or 0 when a leaf is cheaper (count <= kMaxLeaf).
+    // Binned SAH: returns the split position, or 0 when a leaf is cheaper (count <= max_leaf).
     uint32_t sah_split(uint32_t first, uint32_t count, const Box& b, const Box& cb) const {
         float best_cost = std::numeric_limits<float>::infinity();
         int best_axis = -1, best_bin = -1;
@@ -131,7 +132,7 @@ struct Builder {
         float area = b.area();
         float leaf_cost = (float)count;
         float split_cost = area > 0.f ? kTravCost + best_cost / area : std::numeric_limits<float>::infinity();
-        if (count <= kMaxLeaf && leaf_cost <= split_cost) return 0;
+        if (count <= max_leaf && leaf_cost <= split_cost) return 0;
         if (best_axis < 0) return median_split(first, count, cb);
         float lo = cb.lo[best_axis], scale = kBins / (cb.hi[best_axis] - cb.lo[best_axis]);
         uint32_t* mid = std::partition(idx + first, idx + first + count, [&](uint32_t t) {
@@ -153,7 +154,7 @@ struct Builder {
         if (count <= 1) {
             mid = 0;
         } else if (depth >= kMedianDepth) {
-            mid = count <= kMaxLeaf ? 0 : median_split(first, count, cb);
+            mid = count <= max_leaf ? 0 : median_split(first, count, cb);
         } else {
             mid = sah_split(first, count, b, cb);
         }
@@ -205,7 +206,12 @@ float f32_bits(uint32_t u) {
 
 }  // namespace
 
-bool build_bvh(const float* verts, const uint32_t* tris, uint32_t n_tris, BvhOut& out, std::string& err) {
+bool build_bvh(const float* verts, const uint32_t* tris, uint32_t n_tris, BvhOut& out, std::string& err,
+               uint32_t max_leaf) {
+    if (max_leaf < 1 || max_leaf > kMaxLeaf) {
+        err = "max_leaf must be in [1, 8]";
+        return false;
+    }
     out.nodes.clear();
     out.order.clear();
     out.depth = 0;
@@ -227,7 +233,7 @@ bool build_bvh(const float* verts, const uint32_t* tris, uint32_t n_tris, BvhOut
     std::vector<BNode> bn;
     bn.reserve(2 * (size_t)n_tris + 1);
     if (n_tris > 0) {
-        Builder B{&tri_box, &cen, idx.data()};
+        Builder B{&tri_box, &cen, idx.data(), max_leaf};
         B.build(bn, 0, n_tris, 0);
     }
     // Convert: GPU nodes are the internal build nodes in depth-first order; a leaf lives in its

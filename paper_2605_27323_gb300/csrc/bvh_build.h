@@ -15,6 +15,9 @@ struct BvhOut {
 
 // verts: n_verts x 3; tris: n_tris x 3 indices (already validated).  Returns false with a message
 // when the input cannot be encoded.
-bool build_bvh(const float* verts, const uint32_t* tris, uint32_t n_tris, BvhOut& out, std::string& err);
+// max_leaf: most primitives per leaf (1 for the top level of a two-level scene, so that each
+// instance's box is tested in its parent before the ray is transformed).
+bool build_bvh(const float* verts, const uint32_t* tris, uint32_t n_tris, BvhOut& out, std::string& err,
+               uint32_t max_leaf = 8);
 
 }  // namespace pt

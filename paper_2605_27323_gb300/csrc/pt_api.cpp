@@ -6,7 +6,6 @@
 #include <cuda_runtime_api.h>
 
 #include <algorithm>
-#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -388,7 +387,8 @@ pt_status run_wavefront(pt_scene* sc, const pt::DevCamera& cam, const pt::Render
             if (o.hybrid_threshold && b + 1 < p.max_depth) {
                 // hybrid: finish the remaining bounces in one kernel if few paths are left
                 const uint32_t thr = (uint32_t)std::min<uint64_t>(o.hybrid_threshold, 0xFFFFFFFFull);
-                pt::Launch lf = launch_for(sc, pt::K_FINISH, 128, 128, st, std::min<uint64_t>(n, thr));
+                pt::Launch lf = launch_for(sc, sc->instanced ? pt::K_FINISH_INST : pt::K_FINISH, 128, 128, st,
+                                           std::min<uint64_t>(n, thr));
                 PT_TRY(sc->ev_begin(ST_MEGA, st, ev));
                 PT_CUDA(pt::launch_finish(lf, ds, p, w, (int)((b + 1) & 1u), b + 1, thr, sc->finish_claim()));
                 PT_TRY(sc->ev_end(ev, st));
@@ -750,7 +750,8 @@ pt_status render_impl(pt_scene* sc, const pt_camera* cam, uint32_t spp, uint32_t
             pt::Launch l = launch_for(sc, pt::K_MEGA, o.block_size, 128, st, n_paths);
             PT_CUDA(pt::launch_megakernel(l, sc->view(), dc, p, n_paths, outL, img, o.d_path_sig, sc->rays()));
         } else {
-            pt::Launch l = launch_for(sc, pt::K_MEGA_REGEN, o.block_size ? std::min<uint32_t>(o.block_size, 128) : 128, 128,
+            pt::Launch l = launch_for(sc, sc->instanced ? pt::K_MEGA_REGEN_INST : pt::K_MEGA_REGEN,
+                                      o.block_size ? std::min<uint32_t>(o.block_size, 128) : 128, 128,
                                       st, n_paths);
             PT_CUDA(pt::launch_megakernel_regen(l, sc->view(), dc, p, n_paths, outL, img, o.d_path_sig, sc->rays(),
                                                 sc->next_path()));
@@ -1030,7 +1031,6 @@ pt_status pt_scene_create_instanced(uint32_t n_meshes, const float* const* verts
     // bottom level: one BVH per mesh, nodes and triangle records concatenated (refs relocated)
     std::vector<float> nodes, trec;
     std::vector<uint32_t> node_base(n_meshes), rec_base(n_meshes);
-    std::vector<std::array<double, 6>> mesh_box(n_meshes);
     for (uint32_t m = 0; m < n_meshes; ++m) {
         pt::BvhOut bvh;
         std::string err;
@@ -1054,7 +1054,6 @@ pt_status pt_scene_create_instanced(uint32_t n_meshes, const float* const* verts
             }
             nodes.insert(nodes.end(), f, f + 16);
         }
-        std::array<double, 6> box = {1e300, 1e300, 1e300, -1e300, -1e300, -1e300};
         for (uint32_t k = 0; k < n_tris[m]; ++k) {
             const uint32_t i = bvh.order[k];
             const float* pa = verts[m] + 3 * (size_t)tris[m][3 * (size_t)i];
@@ -1064,26 +1063,28 @@ pt_status pt_scene_create_instanced(uint32_t n_meshes, const float* const* verts
             const float r[12] = {pa[0], pa[1], pa[2], bits(i), pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2], bits(mat),
                                  pc[0] - pa[0], pc[1] - pa[1], pc[2] - pa[2], bits(mats[mat].emission > 0.f ? 1u : 0u)};
             trec.insert(trec.end(), r, r + 12);
-            for (const float* p : {pa, pb, pc})
-                for (int c = 0; c < 3; ++c) {
-                    box[c] = std::min(box[c], (double)p[c]);
-                    box[3 + c] = std::max(box[3 + c], (double)p[c]);
-                }
         }
-        mesh_box[m] = box;
     }
-    // top level: the instances' world boxes (the 8 transformed corners of the mesh box, padded a
-    // few ulps outward), built as degenerate triangles (lo, hi, hi) so the same builder applies
+    // top level: the instances' world boxes -- the bounds of the mesh's vertices placed in the world
+    // (tighter than the placed corners of the object box when the instance rotates), padded a few
+    // ulps outward -- built as degenerate triangles (lo, hi, hi) so the same builder applies
+    std::vector<std::vector<uint32_t>> used(n_meshes);       // vertices referenced by each mesh
+    for (uint32_t m = 0; m < n_meshes; ++m) {
+        std::vector<char> mark(n_verts[m], 0);
+        for (uint64_t k = 0; k < 3ull * n_tris[m]; ++k) mark[tris[m][k]] = 1;
+        for (uint32_t v = 0; v < n_verts[m]; ++v)
+            if (mark[v]) used[m].push_back(v);
+    }
     std::vector<float> ibox(6 * (size_t)n_instances);
     std::vector<uint32_t> itri(3 * (size_t)n_instances);
     for (uint32_t i = 0; i < n_instances; ++i) {
         const pt_instance& I = instances[i];
-        const auto& b = mesh_box[I.mesh];
         double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-        for (int corner = 0; corner < 8; ++corner) {
-            const double p[3] = {corner & 1 ? b[3] : b[0], corner & 2 ? b[4] : b[1], corner & 4 ? b[5] : b[2]};
+        for (uint32_t v : used[I.mesh]) {
+            const float* p = verts[I.mesh] + 3 * (size_t)v;
             for (int r = 0; r < 3; ++r) {
-                const double w = I.xform[4 * r] * p[0] + I.xform[4 * r + 1] * p[1] + I.xform[4 * r + 2] * p[2] + I.xform[4 * r + 3];
+                const double w = I.xform[4 * r] * (double)p[0] + I.xform[4 * r + 1] * (double)p[1] +
+                                 I.xform[4 * r + 2] * (double)p[2] + I.xform[4 * r + 3];
                 lo[r] = std::min(lo[r], w);
                 hi[r] = std::max(hi[r], w);
             }
@@ -1101,7 +1102,7 @@ pt_status pt_scene_create_instanced(uint32_t n_meshes, const float* const* verts
     }
     pt::BvhOut top;
     std::string err;
-    if (!pt::build_bvh(ibox.data(), itri.data(), n_instances, top, err))
+    if (!pt::build_bvh(ibox.data(), itri.data(), n_instances, top, err, 1))
         return bail(fail(PT_ERR_INVALID_ARG, "top-level BVH build: %s", err.c_str()));
     std::vector<uint32_t> prim_base(n_instances);
     {
@@ -1111,20 +1112,22 @@ pt_status pt_scene_create_instanced(uint32_t n_meshes, const float* const* verts
             acc += n_tris[instances[i].mesh];
         }
     }
-    // instance records in top-level leaf order
-    std::vector<float> irec(24 * (size_t)n_instances);
+    // instance records in top-level leaf order, 128 bytes: i0..i2 world-to-object rows (A | b),
+    // i3 = (mesh root node, first triangle id, material word, -), i4..i6 object-to-world rows of R;
+    // the first 64 bytes are all that taking a ray into the instance reads
+    std::vector<float> irec(32 * (size_t)n_instances, 0.f);
     for (uint32_t k = 0; k < n_instances; ++k) {
         const uint32_t i = top.order[k];
         const pt_instance& I = instances[i];
-        float* r = &irec[24 * (size_t)k];
+        float* r = &irec[32 * (size_t)k];
         for (int q = 0; q < 12; ++q) r[q] = (float)inv[12 * (size_t)i + q];
-        for (int row = 0; row < 3; ++row)
-            for (int c = 0; c < 3; ++c) r[12 + 4 * row + c] = I.xform[4 * row + c];
         uint32_t mw = 0;
         if (I.material != PT_NO_MATERIAL) mw = (I.material + 1u) | (mats[I.material].emission > 0.f ? 0x80000000u : 0u);
-        r[15] = bits(node_base[I.mesh]);
-        r[19] = bits(prim_base[i]);
-        r[23] = bits(mw);
+        r[12] = bits(node_base[I.mesh]);
+        r[13] = bits(prim_base[i]);
+        r[14] = bits(mw);
+        for (int row = 0; row < 3; ++row)
+            for (int c = 0; c < 3; ++c) r[16 + 4 * row + c] = I.xform[4 * row + c];
     }
     // lights: every instance's emissive triangles in the world, ascending triangle id
     std::vector<float> lrec;

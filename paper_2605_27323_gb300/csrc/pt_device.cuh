@@ -401,14 +401,14 @@ __device__ __forceinline__ Vertex shade_vertex(const DevScene& s, const RenderPa
     if (INST) {
         // two-level scene: the mesh's object-space edges taken to the world by the instance's
         // rotation/scale rows; the instance may replace the material
-        const float4* ip = s.inst + 6 * (size_t)inst;
-        const float4 m0 = __ldg(ip + 3), m1 = __ldg(ip + 4), m2 = __ldg(ip + 5);
+        const float4* ip = s.inst + 8 * (size_t)inst;
+        const float4 i3 = __ldg(ip + 3), m0 = __ldg(ip + 4), m1 = __ldg(ip + 5), m2 = __ldg(ip + 6);
         const float3 e1 = xyz(t1), e2 = xyz(t2);
         const float3 E1 = f3(dot(xyz(m0), e1), dot(xyz(m1), e1), dot(xyz(m2), e1));
         const float3 E2 = f3(dot(xyz(m0), e2), dot(xyz(m1), e2), dot(xyz(m2), e2));
         ng = normalize(cross(E1, E2));
-        V.prim += __float_as_uint(m1.w);
-        const uint32_t mw = __float_as_uint(m2.w);
+        V.prim += __float_as_uint(i3.y);
+        const uint32_t mw = __float_as_uint(i3.z);
         if (mw != 0u) {
             V.mat = (mw & 0x7FFFFFFFu) - 1u;
             is_light = (mw >> 31) != 0u;

@@ -12,7 +12,8 @@ namespace pt {
 // path of its warp finishes.  The per-path arithmetic is that of mk_path, so images are identical.
 template <bool SIG, bool MIS, bool INST>
 // Register cap for 8 resident blocks of 128: occupancy outweighs the spills (measured 3.96 -> 3.11 ms
-// per 1080p frame against the uncapped 107 registers).
+// per 1080p frame against the uncapped 107 registers; for two-level scenes a cap of 6 blocks with
+// fewer spills measured slower too, 5.49 -> 6.07 ms).
 __global__ void __launch_bounds__(128, 8) k_megakernel_regen(DevScene s, DevCamera c, RenderParams p, uint64_t n_paths,
                                                           float* __restrict__ out_L, float* __restrict__ img,
                                                           uint32_t* __restrict__ sig,
@@ -207,6 +208,8 @@ int occupancy_mega(int which, int block) {
     cudaError_t e = cudaErrorInvalidValue;
     switch (which) {
         case K_MEGA_REGEN: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_megakernel_regen<false, false, false>, block, 0); break;
+        case K_MEGA_REGEN_INST: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_megakernel_regen<false, true, true>, block, 0); break;
+        case K_FINISH_INST: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_finish<false, true, true>, block, 0); break;
         case K_FINISH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_finish<false, false, false>, block, 0); break;
         default: return 0;
     }

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) k_sort_keys(Src src, WfBuffers w, int in,
             const DevScene s = src.scene(src.sid_from_ray(w.q_d[in][j].w, base, __float_as_uint(w.q_o[in][j].w)));
             uint32_t m = __float_as_uint(__ldg(s.tris + 3 * (size_t)tri + 1).w);
             if (INST) {        // an instance may replace the mesh's material
-                const uint32_t mw = __float_as_uint(__ldg(s.inst + 6 * (size_t)w.hit_inst[j] + 5).w);
+                const uint32_t mw = __float_as_uint(__ldg(s.inst + 8 * (size_t)w.hit_inst[j] + 3).z);
                 if (mw != 0u) m = (mw & 0x7FFFFFFFu) - 1u;
             }
             key = mode == 1u ? __float_as_uint(__ldg(reinterpret_cast<const float*>(s.mats + m))) : m;

@@ -36,7 +36,7 @@ __device__ __forceinline__ float3 ray_rcp(float3 d) {
     float x = fabsf(d.x) > 1e-20f ? d.x : copysignf(1e-20f, d.x);
     float y = fabsf(d.y) > 1e-20f ? d.y : copysignf(1e-20f, d.y);
     float z = fabsf(d.z) > 1e-20f ? d.z : copysignf(1e-20f, d.z);
-    return f3(1.0f / x, 1.0f / y, 1.0f / z);
+    return f3(__frcp_rn(x), __frcp_rn(y), __frcp_rn(z));   // correctly rounded, as 1.0f / x
 }
 
 // Slab test of one box against [0, tmax]; returns whether it is hit and the entry distance.
@@ -206,13 +206,13 @@ struct InstRay {
 };
 
 __device__ __forceinline__ InstRay instance_ray(const DevScene& s, uint32_t k, float3 o, float3 d) {
-    const float4* p = s.inst + 6 * (size_t)k;
-    const float4 a0 = __ldg(p), a1 = __ldg(p + 1), a2 = __ldg(p + 2);
+    const float4* p = s.inst + 8 * (size_t)k;
+    const float4 a0 = __ldg(p), a1 = __ldg(p + 1), a2 = __ldg(p + 2), a3 = __ldg(p + 3);
     InstRay r;
     r.o = f3(__fadd_rn(dot(xyz(a0), o), a0.w), __fadd_rn(dot(xyz(a1), o), a1.w), __fadd_rn(dot(xyz(a2), o), a2.w));
     r.d = f3(dot(xyz(a0), d), dot(xyz(a1), d), dot(xyz(a2), d));
-    r.root = __float_as_uint(__ldg(p + 3).w);
-    r.prim_base = __float_as_uint(__ldg(p + 4).w);
+    r.root = __float_as_uint(a3.x);
+    r.prim_base = __float_as_uint(a3.y);
     return r;
 }
 

@@ -28,10 +28,10 @@ struct DevScene {
     uint32_t n_mats;
     uint32_t* status;                      // device status word (atomicOr of fault bits)
     // two-level scenes: `nodes`/`tris` hold every mesh's BVH and object-space triangles, `tlas` the
-    // top-level BVH over the instances, `inst` 6 float4 per instance in top-level leaf order:
-    //   i0..i2 = world-to-object rows (A | b), i3..i5 = object-to-world rotation/scale rows with
-    //   w = (mesh root node, first triangle id of the instance, material word); the material word
-    //   is 0 (the mesh's materials) or (material + 1) | (material emitted at creation) << 31.
+    // top-level BVH over the instances, `inst` 8 float4 (128 bytes) per instance in top-level leaf
+    // order: i0..i2 = world-to-object rows (A | b), i3 = (mesh root node, first triangle id of the
+    // instance, material word, -), i4..i6 = object-to-world rotation/scale rows; the material word
+    // is 0 (the mesh's materials) or (material + 1) | (material emitted at creation) << 31.
     const float4* __restrict__ tlas = nullptr;
     const float4* __restrict__ inst = nullptr;
 };
