@@ -45,6 +45,22 @@ BYTES_PER_UNIT = {
 }
 
 
+def rank_seed(step: int, rank: int) -> int:
+    """Seed of a step on a rank: every rank renders its own frames (weak scaling, no data exchange)."""
+    return step + rank * 1_000_000
+
+
+def reduce_over_ranks(total_ms: float, total_rays: float, device) -> tuple:
+    """Job time = the slowest rank's, job rays = the sum over ranks (the only communication)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    r = torch.tensor([total_rays], device=device, dtype=torch.float64)
+    dist.all_reduce(r, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(r.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -250,13 +266,13 @@ def run_gpu(args):
         return ev, ev_mk, ev_bw, s_wf, s_mk, s_bw
 
     for w in range(args.warmup):
-        step(10_000 + w + rank * 1_000_000, False)
+        step(rank_seed(10_000 + w, rank), False)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clocks = Clocks(local) if rank == 0 else None
     torch.cuda.synchronize()
-    recs = [step(s + rank * 1_000_000, True) for s in range(args.steps)]
+    recs = [step(rank_seed(s, rank), True) for s in range(args.steps)]
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -271,11 +287,7 @@ def run_gpu(args):
     total_ms = float(np.sum(step_ms))
     total_rays = float(np.sum(wf_rays) + np.sum(mk_rays) + np.sum(mk_rays))
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        r_ = torch.tensor([total_rays], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(r_, op=torch.distributed.ReduceOp.SUM)
-        total_ms, total_rays = float(t.item()), float(r_.item())
+        total_ms, total_rays = reduce_over_ranks(total_ms, total_rays, "cuda")
     value = total_rays / (total_ms * 1e-3) / 1e6
 
     # stage times from the library's events on the launch stream (timed region); the adjoint's
