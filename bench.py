@@ -699,20 +699,25 @@ def run_batch(args):
     small = [i for i, (c, s_) in enumerate(zip(cams, spps)) if c["width"] * c["height"] * s_ <= (1 << 20)]
     sg, sc_, ss, so = [gs[i] for i in small], [cams[i] for i in small], [spps[i] for i in small], [outs[i] for i in small]
 
-    def batched_small(k):
-        pt.render_batch(sg, sc_, ss, depth, k, outs=so, **kw)
-
     def separate_small(k):
         for i, (g, c, s_) in enumerate(zip(sg, sc_, ss)):
             g.render(c, s_, depth, k, out=so[i], mode="wavefront")
 
     small_res = None
     if small:
+        # the small renders as a batch of their own, with the autotuner's choice for that batch
+        best_s = pt.autotune_batch(sg, sc_, ss, depth, 0, outs=so)
+        kw_s = dict(queue_capacity=best_s["queue_capacity"], block_size=best_s["block_size"], sort=int(best_s["sort"]))
+
+        def batched_small(k):
+            pt.render_batch(sg, sc_, ss, depth, k, outs=so, **kw_s)
+
         batched_small(0)
         separate_small(0)
         bs_ms, ss_ms = timed(batched_small, steps), timed(separate_small, steps)
         small_res = {"scenes": len(small), "paths": int(sum(c["width"] * c["height"] * s_ for c, s_ in zip(sc_, ss))),
-                     "batched_ms": bs_ms, "separate_ms": ss_ms, "batched_over_separate": ss_ms / bs_ms}
+                     "batched_ms": bs_ms, "separate_ms": ss_ms, "batched_over_separate": ss_ms / bs_ms,
+                     "autotuned": kw_s}
     line = {"metric": "batched wavefront vs 64 per-scene renders (Mrays/s)", "value": rays / (b_ms * 1e-3) / 1e6,
             "unit": "Mrays/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": b_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
