@@ -779,6 +779,26 @@ pt_status render_impl(pt_scene* sc, const pt_camera* cam, uint32_t spp, uint32_t
 
 }  // namespace
 
+namespace {
+
+// Material table and environment checks shared by both scene constructors.
+pt_status check_materials(const pt_material* mats, uint32_t n_mats, const float* env_radiance) {
+    for (uint32_t m = 0; m < n_mats; ++m) {
+        const pt_material& M = mats[m];
+        if (M.type > PT_MAT_DIELECTRIC) return fail(PT_ERR_INVALID_ARG, "material %u: unknown type %u", m, M.type);
+        if (!finite3(M.albedo) || M.albedo[0] < 0 || M.albedo[1] < 0 || M.albedo[2] < 0)
+            return fail(PT_ERR_INVALID_ARG, "material %u: albedo must be finite and >= 0", m);
+        if (!std::isfinite(M.emission) || M.emission < 0) return fail(PT_ERR_INVALID_ARG, "material %u: emission must be finite and >= 0", m);
+        if (!std::isfinite(M.roughness) || M.roughness < 0) return fail(PT_ERR_INVALID_ARG, "material %u: roughness must be finite and >= 0", m);
+        if (!std::isfinite(M.ior) || !(M.ior > 0)) return fail(PT_ERR_INVALID_ARG, "material %u: ior must be finite and > 0", m);
+    }
+    if (env_radiance && (!finite3(env_radiance) || env_radiance[0] < 0 || env_radiance[1] < 0 || env_radiance[2] < 0))
+        return fail(PT_ERR_INVALID_ARG, "env_radiance must be finite and >= 0");
+    return PT_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* pt_status_string(pt_status s) {
@@ -814,17 +834,7 @@ pt_status pt_scene_create(const float* verts, uint32_t n_verts, const uint32_t* 
         if (tris[i] >= n_verts) return fail(PT_ERR_INVALID_ARG, "triangle %llu references vertex %u >= n_verts", (unsigned long long)(i / 3), tris[i]);
     for (uint32_t i = 0; i < n_tris; ++i)
         if (tri_material[i] >= n_mats) return fail(PT_ERR_INVALID_ARG, "triangle %u has material %u >= n_mats", i, tri_material[i]);
-    for (uint32_t m = 0; m < n_mats; ++m) {
-        const pt_material& M = mats[m];
-        if (M.type > PT_MAT_DIELECTRIC) return fail(PT_ERR_INVALID_ARG, "material %u: unknown type %u", m, M.type);
-        if (!finite3(M.albedo) || M.albedo[0] < 0 || M.albedo[1] < 0 || M.albedo[2] < 0)
-            return fail(PT_ERR_INVALID_ARG, "material %u: albedo must be finite and >= 0", m);
-        if (!std::isfinite(M.emission) || M.emission < 0) return fail(PT_ERR_INVALID_ARG, "material %u: emission must be finite and >= 0", m);
-        if (!std::isfinite(M.roughness) || M.roughness < 0) return fail(PT_ERR_INVALID_ARG, "material %u: roughness must be finite and >= 0", m);
-        if (!std::isfinite(M.ior) || !(M.ior > 0)) return fail(PT_ERR_INVALID_ARG, "material %u: ior must be finite and > 0", m);
-    }
-    if (env_radiance && (!finite3(env_radiance) || env_radiance[0] < 0 || env_radiance[1] < 0 || env_radiance[2] < 0))
-        return fail(PT_ERR_INVALID_ARG, "env_radiance must be finite and >= 0");
+    PT_TRY(check_materials(mats, n_mats, env_radiance));
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
     pt_scene* sc = new (std::nothrow) pt_scene();
@@ -959,17 +969,7 @@ pt_status pt_scene_create_instanced(uint32_t n_meshes, const float* const* verts
         total_records += n_tris[m];
     }
     if (total_records >= (1u << 28)) return fail(PT_ERR_INVALID_ARG, "the meshes hold >= 2^28 triangles");
-    for (uint32_t m = 0; m < n_mats; ++m) {
-        const pt_material& M = mats[m];
-        if (M.type > PT_MAT_DIELECTRIC) return fail(PT_ERR_INVALID_ARG, "material %u: unknown type %u", m, M.type);
-        if (!finite3(M.albedo) || M.albedo[0] < 0 || M.albedo[1] < 0 || M.albedo[2] < 0)
-            return fail(PT_ERR_INVALID_ARG, "material %u: albedo must be finite and >= 0", m);
-        if (!std::isfinite(M.emission) || M.emission < 0) return fail(PT_ERR_INVALID_ARG, "material %u: emission must be finite and >= 0", m);
-        if (!std::isfinite(M.roughness) || M.roughness < 0) return fail(PT_ERR_INVALID_ARG, "material %u: roughness must be finite and >= 0", m);
-        if (!std::isfinite(M.ior) || !(M.ior > 0)) return fail(PT_ERR_INVALID_ARG, "material %u: ior must be finite and > 0", m);
-    }
-    if (env_radiance && (!finite3(env_radiance) || env_radiance[0] < 0 || env_radiance[1] < 0 || env_radiance[2] < 0))
-        return fail(PT_ERR_INVALID_ARG, "env_radiance must be finite and >= 0");
+    PT_TRY(check_materials(mats, n_mats, env_radiance));
     // instance transforms and their inverses (FP64)
     std::vector<double> inv(12 * (size_t)n_instances);
     uint64_t total_prims = 0;
