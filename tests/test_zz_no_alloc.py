@@ -65,7 +65,7 @@ def test_static_scratch_rejects_what_it_cannot_hold():
     c = make_camera(sc["camera"])
     o = make_opts()
     out = torch.zeros((2, 2, 3), device="cuda")
-    # one pixel's samples must fit the array: 200,000 x 176 B > 32 MiB
+    # one pixel's samples must fit the array: 200,000 x 180 B > 32 MiB
     assert lib.pt_render_wavefront_static(g.h, C.byref(c), 200_000, 4, 0, C.byref(o), C.c_void_p(out.data_ptr()),
                                           stream) == 1
     assert b"static scratch" in lib.pt_last_error()
