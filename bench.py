@@ -163,9 +163,16 @@ def cpu_baseline(sc, budget_s=12.0, threads=None):
     _, rays = osc.render_pixels(cam, 1, sc["max_depth"], 0, pix, rr_start=3, n_threads=threads)
     dt = time.perf_counter() - t0
     total = int(rays[0] + rays[1])
+    # the same oracle on one core, on 1/64 of that sample
+    pix1 = pix[::64]
+    t0 = time.perf_counter()
+    _, rays1 = osc.render_pixels(cam, 1, sc["max_depth"], 0, pix1, rr_start=3, n_threads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": total / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
             "sample": f"{n} evenly strided pixels of the 1920x1080 frame, 1 spp, depth 5 ({total} rays, "
-                      f"{dt:.1f} s, FP64, OpenMP)", "ms_per_frame_extrapolated": dt * 1e3 * n_pix / n}
+                      f"{dt:.1f} s, FP64, OpenMP)", "ms_per_frame_extrapolated": dt * 1e3 * n_pix / n,
+            "single_core": {"value": float(rays1[0] + rays1[1]) / dt1 / 1e6, "unit": "Mrays/s",
+                            "sample": f"{len(pix1)} of those pixels"}}
 
 
 def run_reference(args):
