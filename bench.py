@@ -23,6 +23,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -36,7 +37,7 @@ WORKLOAD = ("procedural spheres scene: 200 level-4 icospheres + 256x256-quad gro
             "step = wavefront frame + megakernel frame + adjoint pass")
 KERNEL_SOURCES = ["paper_2605_27323_gb300/csrc/pt_k_wave.cu", "paper_2605_27323_gb300/csrc/pt_common.cuh",
                   "paper_2605_27323_gb300/csrc/pt_device.cuh", "paper_2605_27323_gb300/csrc/pt_trace.cuh"]
-# Algorithmic bytes per unit of each stage (queue/state traffic, "Roofline").
+# Algorithmic bytes per unit of each stage: the queue and path-state records it must read and write.
 BYTES_PER_UNIT = {
     "extend": 40,      # per extension ray: ray o|id + d|flags (32 B) read, hit record (8 B) written
     "shadow": 80,      # per shadow ray: o|tmax + d|id (32 B) + contribution (16 B) read, L rw (32 B)
@@ -101,7 +102,8 @@ class Clocks:
 
     def __init__(self, index: int):
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(os.environ.get("PT_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"clocks_bench_{os.getpid()}.csv")
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
