@@ -96,3 +96,68 @@ def test_no_cpu_fallback_in_product_path():
             if f.endswith((".py", ".cu", ".cpp", ".h", ".cuh")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_struct_layouts_match_a_compiled_header(tmp_path):
+    """sizeof and offsetof of every ABI struct, from a C program compiled against include/pt.h,
+    against the ctypes mirrors."""
+    fields = {"pt_material": ("Material", ["type", "albedo", "emission", "roughness", "ior", "flags"]),
+              "pt_camera": ("Camera", ["eye", "target", "up", "vfov_deg", "width", "height"]),
+              "pt_render_opts": ("RenderOpts", ["mode", "rr_start", "rr_fixed", "sort_mode", "block_size", "flags",
+                                                "queue_capacity", "d_path_sig", "hybrid_threshold"]),
+              "pt_instance": ("Instance", ["xform", "mesh", "material", "reserved"]),
+              "pt_stats": ("Stats", ["extension_rays", "shadow_rays", "paths", "bounces", "status", "active",
+                                     "ms_raygen", "ms_adjoint", "launches_extend", "launches_total", "ms_total"])}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pt.h"', "int main(void) {"]
+    for cname, (_, fs) in fields.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in fs:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            a, b, c = line.split()
+            got[(a, b)] = int(c)
+    for cname, (pyname, fs) in fields.items():
+        cls = getattr(capi, pyname)
+        assert C.sizeof(cls) == got[(cname, "size")], cname
+        for f in fs:
+            assert getattr(cls, f).offset == got[(cname, f)], (cname, f)
+
+
+def test_instanced_scene_validation_on_host():
+    lib = capi.load()
+    h = C.c_void_p()
+    # no meshes / no instances are rejected before any CUDA call
+    assert lib.pt_scene_create_instanced(0, None, None, None, None, None, None, 0, None, 0, None, None,
+                                         C.byref(h)) == 1
+    assert b"mesh" in lib.pt_last_error()
+    import numpy as np
+    v = np.zeros((3, 3), np.float32)
+    t = np.array([[0, 1, 2]], np.uint32)
+    m = np.zeros(1, np.uint32)
+    vp = (C.c_void_p * 1)(v.ctypes.data)
+    tp = (C.c_void_p * 1)(t.ctypes.data)
+    mp = (C.c_void_p * 1)(m.ctypes.data)
+    nv = (C.c_uint32 * 1)(3)
+    nt = (C.c_uint32 * 1)(1)
+    mats = (capi.Material * 1)()
+    mats[0].ior = 1.5
+    inst = (capi.Instance * 1)()
+    inst[0].mesh = 3                                      # out of range
+    assert lib.pt_scene_create_instanced(1, vp, nv, tp, nt, mp, inst, 1, mats, 1, None, None, C.byref(h)) == 1
+    assert b"mesh 3" in lib.pt_last_error()
+    inst[0].mesh = 0
+    inst[0].material = 7                                  # out of range
+    assert lib.pt_scene_create_instanced(1, vp, nv, tp, nt, mp, inst, 1, mats, 1, None, None, C.byref(h)) == 1
+    assert b"material 7" in lib.pt_last_error()
+    inst[0].material = capi.NO_MATERIAL                   # identity not set: the zero transform is singular
+    assert lib.pt_scene_create_instanced(1, vp, nv, tp, nt, mp, inst, 1, mats, 1, None, None, C.byref(h)) == 1
+    assert b"singular" in lib.pt_last_error()
+    assert h.value is None
