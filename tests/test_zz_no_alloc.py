@@ -51,6 +51,30 @@ def test_static_scratch_render_equals_pt_render_on_two_calls():
         assert float(out.mean()) > 0
 
 
+def test_static_scratch_handles_estimator_variants_and_two_level_scenes():
+    """The same entry point with MIS and the Halton jitter, on a two-level (instanced) scene."""
+    import torch
+
+    import paper_2605_27323_gb300 as pt
+    from paper_2605_27323_gb300 import capi, scenes
+    from paper_2605_27323_gb300.tracer import make_camera, make_opts
+
+    lib = capi.load()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    sc = scenes.instanced_spheres_scene(seed=3, n_spheres=25, level=3, ground_quads=32, extent=15.0, width=200,
+                                        height=120, n_materials=12)
+    g = pt.Scene.from_dict(sc)
+    cam = sc["camera"]
+    ref = g.render(cam, 8, 6, 4, mode="wavefront", mis=True, sampler="halton")
+    out = torch.full_like(ref, float("nan"))
+    c = make_camera(cam)
+    o = make_opts(mode="wavefront", mis=True, sampler="halton")
+    st = lib.pt_render_wavefront_static(g.h, C.byref(c), 8, 6, 4, C.byref(o), C.c_void_p(out.data_ptr()), stream)
+    assert st == 0, lib.pt_last_error()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+
+
 def test_static_scratch_rejects_what_it_cannot_hold():
     import torch
 
