@@ -34,11 +34,22 @@ __global__ void __launch_bounds__(256) k_raygen(Src src, uint64_t base, uint32_t
         w.counts[0] = n;
         w.counts[1] = 0u;
         w.counts[2] = 0u;
+        w.counts[4] = 0u;
+        w.counts[5] = 0u;
         if (wave_base_dev) *wave_base_dev = base;
     }
 }
 
 // Extend: closest hit of every active ray (scene-intersection stage); hit records per queue slot.
+// Warp-granular dynamic work: each warp claims the next 32 queue slots with one atomic, so warps
+// that drew cheap rays take more batches and the grid ends together (a static grid-stride split
+// leaves the SMs waiting on the warps that drew the longest rays).
+__device__ __forceinline__ uint32_t warp_claim32(uint32_t* counter) {
+    uint32_t b = 0u;
+    if (lane_id() == 0u) b = atomicAdd(counter, 32u);
+    return __shfl_sync(0xFFFFFFFFu, b, 0);
+}
+
 template <class Src, bool INST>
 __global__ void __launch_bounds__(256) k_extend(Src src, WfBuffers w, int in) {
     const uint32_t n = min(w.counts[0], w.capacity);
@@ -46,8 +57,9 @@ __global__ void __launch_bounds__(256) k_extend(Src src, WfBuffers w, int in) {
     const float4* __restrict__ qo = w.q_o[in];
     const float4* __restrict__ qd = w.q_d[in];
     float2* __restrict__ hit = w.hit;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    for (uint32_t b0 = warp_claim32(&w.counts[4]); b0 < n; b0 = warp_claim32(&w.counts[4])) {
+        const uint32_t j = b0 + lane_id();
+        if (j >= n) continue;
         float4 o4 = qo[j], d4 = qd[j];
         Hit h = trace_closest<INST>(src.scene(src.sid_from_ray(d4.w, base, __float_as_uint(o4.w))), xyz(o4), xyz(d4));
         hit[j] = make_float2(h.t, __uint_as_float(h.tri));
@@ -220,8 +232,9 @@ template <class Src, bool SIG, bool INST>
 __global__ void __launch_bounds__(256) k_shadow(Src src, WfBuffers w, uint32_t b) {
     const uint32_t n = min(w.counts[2], w.capacity);
     const uint64_t base = src.base();
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    for (uint32_t b0 = warp_claim32(&w.counts[5]); b0 < n; b0 = warp_claim32(&w.counts[5])) {
+        const uint32_t j = b0 + lane_id();
+        if (j >= n) continue;
         const float4 so = w.s_o[j], sd = w.s_d[j], sc = w.s_c[j];
         const uint32_t pid = __float_as_uint(sd.w);
         const bool occ = trace_any<INST>(src.scene(src.sid_from_shadow(sc.w, base, pid)), xyz(so), xyz(sd), so.w);
@@ -243,6 +256,8 @@ __global__ void k_prepare(WfBuffers w, uint32_t b) {
     w.counts[0] = w.counts[1];
     w.counts[1] = 0u;
     w.counts[2] = 0u;
+    w.counts[4] = 0u;      // the extend and shadow stages' work counters
+    w.counts[5] = 0u;
 }
 
 // ================================================================== accumulation
