@@ -1299,7 +1299,9 @@ pt_status pt_render_backward(pt_scene* sc, const pt_camera* cam, uint32_t spp, u
     PT_TRY(sc->ev_begin(ST_ADJOINT, st, ev));
     if (o.mode == PT_MODE_MEGAKERNEL) {
         pt::Launch l = launch_for(sc, pt::K_ADJOINT, o.block_size, 128, st, n_paths);
-        PT_CUDA(pt::launch_adjoint(l, sc->view(), dc, p, n_paths, grad, d_grad_albedo, d_grad_emission, max_depth));
+        // the counters were zeroed above; the regenerating megakernel's path counter is free here
+        PT_CUDA(pt::launch_adjoint(l, sc->view(), dc, p, n_paths, grad, d_grad_albedo, d_grad_emission, max_depth,
+                                   sc->next_path()));
         sc->launches += 1;
     } else {
         // wavefront replay: the forward stages with record-writing shading, then one reverse pass per wave

@@ -25,6 +25,15 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool want) {
     return base + (uint32_t)__popc(mask & ((1u << lane_id()) - 1u));
 }
 
+// Warp-granular dynamic work: each warp claims the next 32 queue slots with one atomic, so warps
+// that drew cheap rays take more batches and the grid ends together (a static grid-stride split
+// leaves the SMs waiting on the warps that drew the longest rays).
+__device__ __forceinline__ uint32_t warp_claim32(uint32_t* counter) {
+    uint32_t b = 0u;
+    if (lane_id() == 0u) b = atomicAdd(counter, 32u);
+    return __shfl_sync(0xFFFFFFFFu, b, 0);
+}
+
 __device__ __forceinline__ void warp_add_u64(unsigned long long* dst, unsigned long long v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
     if (lane_id() == 0 && v) atomicAdd(dst, v);

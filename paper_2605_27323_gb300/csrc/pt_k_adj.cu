@@ -91,8 +91,9 @@ template <bool INST>
 __global__ void __launch_bounds__(256) k_shadow_adj(SingleSrc src, WfBuffers w, AdjBuffers a, uint32_t b) {
     const uint32_t n = min(w.counts[2], w.capacity);
     const size_t cap = w.capacity;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    for (uint32_t b0 = warp_claim32(&w.counts[5]); b0 < n; b0 = warp_claim32(&w.counts[5])) {
+        const uint32_t j = b0 + lane_id();
+        if (j >= n) continue;
         const float4 so = w.s_o[j], sd = w.s_d[j];
         if (!trace_any<INST>(src.s, xyz(so), xyz(sd), so.w)) {
             const uint32_t pid = __float_as_uint(sd.w);
@@ -109,20 +110,27 @@ __global__ void __launch_bounds__(256) k_shadow_adj(SingleSrc src, WfBuffers w, 
 //   d/d emission(m_b) += delta . tp_b                (emission counted at b)
 //   d/d emission(light material) += delta . tp_b * f_b G A   (visible NEE)
 // Loops are warp-uniform so that the per-vertex adds can be aggregated across the warp.
+// Warps claim 32 consecutive paths at a time from a 64-bit device counter (zero at launch), as the
+// wavefront stages claim queue slots.
+__device__ __forceinline__ uint64_t warp_claim32_u64(unsigned long long* counter) {
+    unsigned long long b = 0ull;
+    if (lane_id() == 0u) b = atomicAdd(counter, 32ull);
+    return __shfl_sync(0xFFFFFFFFu, b, 0);
+}
+
 template <int MAXD, bool INST>
 __global__ void __launch_bounds__(256) k_adjoint(DevScene s, DevCamera c, RenderParams p, uint64_t n_paths,
                                                  const float* __restrict__ grad, float* __restrict__ g_alb,
-                                                 float* __restrict__ g_em, int smem) {
+                                                 float* __restrict__ g_em, int smem,
+                                                 unsigned long long* __restrict__ claim) {
     extern __shared__ float acc[];
     if (smem)
         for (uint32_t k = threadIdx.x; k < 4 * s.n_mats; k += blockDim.x) acc[k] = 0.f;
     __syncthreads();
-    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const float3 env = f3(s.env_r, s.env_g, s.env_b);
     const float inv_spp = 1.0f / (float)p.spp;
     AdjRec rec[MAXD];
-    for (uint64_t base = warp * 32; base < n_paths; base += n_warps * 32) {
+    for (uint64_t base = warp_claim32_u64(claim); base < n_paths; base = warp_claim32_u64(claim)) {
         const uint64_t i = base + lane_id();
         int nv = 0;
         bool end_miss = false;
@@ -299,11 +307,11 @@ __global__ void __launch_bounds__(256) k_adjoint_reverse(DevScene s, RenderParam
 // ------------------------------------------------------------------ launchers
 cudaError_t launch_adjoint(const Launch& l, const DevScene& s, const DevCamera& c, const RenderParams& p,
                            uint64_t n_paths, const float* grad_img, float* g_albedo, float* g_emission,
-                           uint32_t max_depth_cap) {
+                           uint32_t max_depth_cap, unsigned long long* claim) {
     size_t smem_bytes = sizeof(float) * 4 * (size_t)s.n_mats;
     int smem = smem_bytes <= 32 * 1024 ? 1 : 0;
     size_t sb = smem ? smem_bytes : 0;
-#define PT_ADJ(D, I) k_adjoint<D, I><<<l.grid, l.block, sb, l.st>>>(s, c, p, n_paths, grad_img, g_albedo, g_emission, smem)
+#define PT_ADJ(D, I) k_adjoint<D, I><<<l.grid, l.block, sb, l.st>>>(s, c, p, n_paths, grad_img, g_albedo, g_emission, smem, claim)
     // two-level scenes: one instantiation (the record array sized for the deepest paths)
     if (s.tlas) PT_ADJ(32, true);
     else if (max_depth_cap <= 8) PT_ADJ(8, false);

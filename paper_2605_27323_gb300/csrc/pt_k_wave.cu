@@ -41,15 +41,6 @@ __global__ void __launch_bounds__(256) k_raygen(Src src, uint64_t base, uint32_t
 }
 
 // Extend: closest hit of every active ray (scene-intersection stage); hit records per queue slot.
-// Warp-granular dynamic work: each warp claims the next 32 queue slots with one atomic, so warps
-// that drew cheap rays take more batches and the grid ends together (a static grid-stride split
-// leaves the SMs waiting on the warps that drew the longest rays).
-__device__ __forceinline__ uint32_t warp_claim32(uint32_t* counter) {
-    uint32_t b = 0u;
-    if (lane_id() == 0u) b = atomicAdd(counter, 32u);
-    return __shfl_sync(0xFFFFFFFFu, b, 0);
-}
-
 template <class Src, bool INST>
 __global__ void __launch_bounds__(256) k_extend(Src src, WfBuffers w, int in) {
     const uint32_t n = min(w.counts[0], w.capacity);

@@ -67,10 +67,11 @@ cudaError_t launch_accumulate(const Launch& l, const float* L, uint32_t stride, 
 cudaError_t launch_finish(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w, int in,
                           uint32_t b0, uint32_t threshold, unsigned long long* claim);
 
-// Path-replay adjoint (one thread per path).  grad_img is H x W x 3.
+// Path-replay adjoint (one thread per path).  grad_img is H x W x 3; `claim` is a device counter
+// that must be zero at launch (warps take paths from it).
 cudaError_t launch_adjoint(const Launch& l, const DevScene& s, const DevCamera& c, const RenderParams& p,
                            uint64_t n_paths, const float* grad_img, float* g_albedo, float* g_emission,
-                           uint32_t max_depth_cap);
+                           uint32_t max_depth_cap, unsigned long long* claim);
 
 // Wavefront adjoint: shading that writes per-vertex records, the shadow stage that marks visible
 // NEE samples, and the reverse pass over one wave's paths.
