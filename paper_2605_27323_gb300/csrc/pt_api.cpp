@@ -303,8 +303,22 @@ pt_status check_opts(const pt_render_opts& o) {
     return PT_OK;
 }
 
+// The two-level instantiation of a wavefront stage (its register count, hence its occupancy, differs).
+int stage_kernel(const pt_scene* sc, int kernel) {
+    if (!sc->instanced) return kernel;
+    switch (kernel) {
+        case pt::K_EXTEND: return pt::K_EXTEND_INST;
+        case pt::K_SHADE: return pt::K_SHADE_INST;
+        case pt::K_SHADOW: return pt::K_SHADOW_INST;
+        case pt::K_SHADE_ADJ: return pt::K_SHADE_ADJ_INST;
+        case pt::K_SHADOW_ADJ: return pt::K_SHADOW_ADJ_INST;
+        default: return kernel;
+    }
+}
+
 pt::Launch launch_for(const pt_scene* sc, int kernel, uint32_t block_opt, uint32_t def_block, cudaStream_t st,
                       uint64_t work_upper) {
+    kernel = stage_kernel(sc, kernel);
     pt::Launch l;
     l.block = block_opt ? (int)block_opt : (int)def_block;
     int per = blocks_per_sm(kernel, l.block);
@@ -357,7 +371,6 @@ pt_status run_wavefront(pt_scene* sc, const pt::DevCamera& cam, const pt::Render
         pt::RenderParams p = p0;
         p.path_begin = w0;
         size_t ev = 0;
-        pt::Launch lr = launch_for(sc, pt::K_EXTEND, 0, 256, st, n);
         PT_TRY(sc->ev_begin(ST_RAYGEN, st, ev));
         PT_CUDA(pt::launch_raygen(simple_launch(sc, st, n), cam, p, n, w));
         PT_TRY(sc->ev_end(ev, st));
@@ -395,7 +408,6 @@ pt_status run_wavefront(pt_scene* sc, const pt::DevCamera& cam, const pt::Render
                 sc->launches += 2;
             }
         }
-        (void)lr;
         PT_TRY(sc->ev_begin(ST_REDUCE, st, ev));
         if (accum)
             PT_CUDA(pt::launch_accumulate(simple_launch(sc, st, n / p.spp), reinterpret_cast<const float*>(w.L), 4,

@@ -354,6 +354,8 @@ int occupancy_adj(int which, int block) {
         case K_ADJOINT: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adjoint<16, false>, block, 16 * 1024); break;
         case K_SHADE_ADJ: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade_adj<false>, block, 0); break;
         case K_SHADOW_ADJ: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shadow_adj<false>, block, 0); break;
+        case K_SHADE_ADJ_INST: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shade_adj<true>, block, 0); break;
+        case K_SHADOW_ADJ_INST: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_shadow_adj<true>, block, 0); break;
         default: return 0;
     }
     if (e != cudaSuccess) {

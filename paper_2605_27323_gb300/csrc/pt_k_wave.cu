@@ -41,8 +41,10 @@ __global__ void __launch_bounds__(256) k_raygen(Src src, uint64_t base, uint32_t
 }
 
 // Extend: closest hit of every active ray (scene-intersection stage); hit records per queue slot.
+// Single-level: registers capped for 6 resident blocks of 256 (extend 2.73 -> 2.68 ms per 1080p
+// step against 5 blocks); the two-level variant measured slower under that cap and keeps its own.
 template <class Src, bool INST>
-__global__ void __launch_bounds__(256) k_extend(Src src, WfBuffers w, int in) {
+__global__ void __launch_bounds__(256, INST ? 1 : 6) k_extend(Src src, WfBuffers w, int in) {
     const uint32_t n = min(w.counts[0], w.capacity);
     const uint64_t base = src.base();
     const float4* __restrict__ qo = w.q_o[in];
@@ -490,6 +492,9 @@ int occupancy_wave(int which, int block) {
         case K_EXTEND_BATCH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend<TableSrc, false>, block, 0); break;
         case K_SHADE_BATCH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (k_shade<TableSrc, false, false>), block, 0); break;
         case K_SHADOW_BATCH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (k_shadow<TableSrc, false, false>), block, 0); break;
+        case K_EXTEND_INST: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend<SingleSrc, true>, block, 0); break;
+        case K_SHADE_INST: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (k_shade<SingleSrc, false, true>), block, 0); break;
+        case K_SHADOW_INST: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (k_shadow<SingleSrc, false, true>), block, 0); break;
         default: return 0;
     }
     if (e != cudaSuccess) {

@@ -145,6 +145,9 @@ extern "C" pt_status pt_render_wavefront_static(pt_scene* scene, const pt_camera
     }
     const int block = o.block_size ? (int)o.block_size : 256;
     auto persistent = [&](int which) {
+        if (ds.tlas)   // the two-level instantiations have their own register counts
+            which = which == pt::K_EXTEND ? pt::K_EXTEND_INST : which == pt::K_SHADE ? pt::K_SHADE_INST
+                  : which == pt::K_SHADOW ? pt::K_SHADOW_INST : which;
         pt::Launch l;
         l.block = block;
         l.grid = std::max(1, sms * pt::max_blocks_per_sm(which, block));
