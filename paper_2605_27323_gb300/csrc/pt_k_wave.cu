@@ -41,10 +41,11 @@ __global__ void __launch_bounds__(256) k_raygen(Src src, uint64_t base, uint32_t
 }
 
 // Extend: closest hit of every active ray (scene-intersection stage); hit records per queue slot.
-// Single-level: registers capped for 6 resident blocks of 256 (extend 2.73 -> 2.68 ms per 1080p
-// step against 5 blocks); the two-level variant measured slower under that cap and keeps its own.
+// Registers capped for 6 resident blocks of 256 single-level (extend 2.73 -> 2.68 ms per 1080p step
+// against 5 blocks) and 4 two-level (64 registers; 6 blocks measured slower, and without a bound
+// ptxas takes 78 registers, leaving 3 blocks: 2.89 -> 3.00 ms per two-level frame).
 template <class Src, bool INST>
-__global__ void __launch_bounds__(256, INST ? 1 : 6) k_extend(Src src, WfBuffers w, int in) {
+__global__ void __launch_bounds__(256, INST ? 4 : 6) k_extend(Src src, WfBuffers w, int in) {
     const uint32_t n = min(w.counts[0], w.capacity);
     const uint64_t base = src.base();
     const float4* __restrict__ qo = w.q_o[in];
