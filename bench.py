@@ -85,8 +85,8 @@ def load_peaks():
 
 
 def load_traffic(kernel: str):
-    """Per-unit DRAM bytes of `kernel` from the committed ncu summary, if it was taken on the
-    current kernel sources."""
+    """The committed ncu figures of `kernel` (per-unit DRAM bytes and a few unit utilisations), if
+    they were taken on the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -94,7 +94,7 @@ def load_traffic(kernel: str):
     e = d.get(kernel)
     if not e or e.get("kernel_hash") != kernel_hash():
         return None
-    return float(e["dram_bytes_per_unit"])
+    return e
 
 
 class Clocks:
@@ -329,7 +329,9 @@ def run_gpu(args):
     tr = load_traffic(dom)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src,
-                "traffic": (tr * units[dom] / launches[dom]) if tr is not None else None,
+                "traffic": (float(tr["dram_bytes_per_unit"]) * units[dom] / launches[dom]) if tr else None,
+                # what does bound it: ncu's unit utilisations for the same kernel sources
+                "ncu_counters": tr.get("counters") if tr else None,
                 "algorithmic_bytes_per_launch": alg_bytes / launches[dom],
                 "avg_launch_ms": stage[dom] / launches[dom],
                 "share_of_step_kernel_time": {k: round(v, 4) for k, v in shares.items()}}

@@ -167,10 +167,11 @@ __device__ __forceinline__ bool trace_any_plain(const DevScene& s, float3 o, flo
             float t0, t1;
             bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tmax, t0);
             bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tmax, t1);
-            if (h0 && h1) {
-                if (sp < kStack) stack_ref[sp++] = r.y;
+            if (h0 && h1) {       // nearer child first: an occluder near the origin ends the walk sooner
+                const bool first0 = t0 <= t1;
+                if (sp < kStack) stack_ref[sp++] = first0 ? r.y : r.x;
                 else atomicOr(s.status, ST_TRAVERSAL);
-                ref = r.x;
+                ref = first0 ? r.x : r.y;
                 if (++steps < kMaxSteps) continue;
             } else if (h0 || h1) {
                 ref = h0 ? r.x : r.y;
@@ -294,10 +295,11 @@ __device__ __forceinline__ bool blas_any(const DevScene& s, const InstRay& r, fl
             float t0, t1;
             bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, r.o, id, tmax, t0);
             bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, r.o, id, tmax, t1);
-            if (h0 && h1) {
-                if (sp < kStack) stack_ref[sp++] = c.y;
+            if (h0 && h1) {       // nearer child first, as in the single-level walk
+                const bool first0 = t0 <= t1;
+                if (sp < kStack) stack_ref[sp++] = first0 ? c.y : c.x;
                 else atomicOr(s.status, ST_TRAVERSAL);
-                ref = c.x;
+                ref = first0 ? c.x : c.y;
                 if (++steps < kMaxSteps) continue;
             } else if (h0 || h1) {
                 ref = h0 ? c.x : c.y;
@@ -398,10 +400,11 @@ __device__ __forceinline__ bool trace_any_inst(const DevScene& s, float3 o, floa
             float t0, t1;
             bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tmax, t0);
             bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tmax, t1);
-            if (h0 && h1) {
-                if (sp < kStack) stack_ref[sp++] = c.y;
+            if (h0 && h1) {       // nearer child first, as in the single-level walk
+                const bool first0 = t0 <= t1;
+                if (sp < kStack) stack_ref[sp++] = first0 ? c.y : c.x;
                 else atomicOr(s.status, ST_TRAVERSAL);
-                ref = c.x;
+                ref = first0 ? c.x : c.y;
                 if (++steps < kMaxSteps) continue;
             } else if (h0 || h1) {
                 ref = h0 ? c.x : c.y;
