@@ -355,9 +355,13 @@ def run_gpu(args):
     hyb_thr = min(hyb, key=hyb.get)
     # estimator variants (not in the step): MIS, and the Halton (2,3) + Cranley-Patterson jitter
     variants = {}
+    # (and the two integrators without the per-stage timing events the step records: those cost
+    # the wavefront about 2 us per stage boundary)
     for name, kw in (("mis_wavefront", dict(mode="wavefront", mis=True)),
                      ("mis_megakernel", dict(mode="megakernel", mis=True)),
-                     ("halton_wavefront", dict(mode="wavefront", sampler="halton"))):
+                     ("halton_wavefront", dict(mode="wavefront", sampler="halton")),
+                     ("wavefront_no_stage_events", dict(mode="wavefront", sort=args.sort)),
+                     ("megakernel_no_stage_events", dict(mode="megakernel"))):
         g.render(cam, spp, depth, 900, rr_start=3, **kw)
         ms = []
         for k in range(max(3, args.steps // 2)):
@@ -371,6 +375,19 @@ def run_gpu(args):
         st_v = g.stats()
         variants[name] = {"ms_per_frame": float(np.mean(ms)),
                           "mrays_s": (st_v["extension_rays"] + st_v["shadow_rays"]) / (float(np.mean(ms)) * 1e-3) / 1e6}
+    variants["wf_over_mk_no_stage_events"] = (variants["megakernel_no_stage_events"]["ms_per_frame"] /
+                                              variants["wavefront_no_stage_events"]["ms_per_frame"])
+    # the adjoint's one-thread-per-path replay (mode="megakernel"), not in the step
+    ms = []
+    for k in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.backward(cam, spp, depth, 930 + k, grad, rr_start=3, mode="megakernel")
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        flush.fill_(k & 0xFF)
+    variants["adjoint_one_thread_per_path"] = {"ms_per_pass": float(np.mean(ms[1:]))}
     out = None
     if rank == 0:
         e2e = measure_e2e(g, cam, spp, depth, grad, args, wf_opts, mk_opts) if world == 1 else None
