@@ -167,21 +167,24 @@ struct pt_scene {
     uint32_t last_mode = 0;
     uint64_t last_paths = 0;
     uint32_t launches = 0;     // kernel launches issued by the last call
-    // profiling: event pairs recorded on the launch stream
+    // profiling: stage intervals between events recorded on the launch stream.  Consecutive stages
+    // share the event between them (one record per stage boundary: each record costs the stream a
+    // couple of microseconds).  A stage's end is recorded when the next stage begins, another
+    // stage ends, or the call finishes, so a bookkeeping launch between two stages counts toward
+    // the earlier one.
     struct Ev {
         int stage;
-        cudaEvent_t a, b;
+        int a, b;      // indices into ev_pool; -1: not recorded
     };
     std::vector<Ev> events;
-    size_t ev_used = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0, pool_used = 0;
+    long ev_pending = -1;     // the stage whose end is still to be recorded
     bool profiling = false;
     std::mutex mu;
 
     ~pt_scene() {
-        for (Ev& e : events) {
-            cudaEventDestroy(e.a);
-            cudaEventDestroy(e.b);
-        }
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     }
 
     pt::DevScene view() const {
@@ -218,22 +221,47 @@ struct pt_scene {
         return PT_OK;
     }
 
+    void ev_reset(bool on) {
+        profiling = on;
+        ev_used = 0;
+        pool_used = 0;
+        ev_pending = -1;
+    }
+    pt_status ev_record(cudaStream_t st, int& slot) {
+        if (pool_used == ev_pool.size()) {
+            cudaEvent_t e = nullptr;
+            PT_CUDA(cudaEventCreate(&e));
+            ev_pool.push_back(e);
+        }
+        slot = (int)pool_used++;
+        PT_CUDA(cudaEventRecord(ev_pool[slot], st));
+        return PT_OK;
+    }
     pt_status ev_begin(int stage, cudaStream_t st, size_t& idx) {
         if (!profiling) return PT_OK;
-        if (ev_used == events.size()) {
-            Ev e{stage, nullptr, nullptr};
-            PT_CUDA(cudaEventCreate(&e.a));
-            PT_CUDA(cudaEventCreate(&e.b));
-            events.push_back(e);
+        int e = -1;
+        PT_TRY(ev_record(st, e));
+        if (ev_pending >= 0) {
+            events[ev_pending].b = e;
+            ev_pending = -1;
         }
+        if (ev_used == events.size()) events.push_back(Ev{stage, -1, -1});
         idx = ev_used++;
-        events[idx].stage = stage;
-        PT_CUDA(cudaEventRecord(events[idx].a, st));
+        events[idx] = Ev{stage, e, -1};
         return PT_OK;
     }
     pt_status ev_end(size_t idx, cudaStream_t st) {
         if (!profiling) return PT_OK;
-        PT_CUDA(cudaEventRecord(events[idx].b, st));
+        PT_TRY(ev_flush(st));
+        ev_pending = (long)idx;
+        return PT_OK;
+    }
+    pt_status ev_flush(cudaStream_t st) {
+        if (!profiling || ev_pending < 0) return PT_OK;
+        int e = -1;
+        PT_TRY(ev_record(st, e));
+        events[ev_pending].b = e;
+        ev_pending = -1;
         return PT_OK;
     }
 };
@@ -718,8 +746,7 @@ pt_status render_impl(pt_scene* sc, const pt_camera* cam, uint32_t spp, uint32_t
         img = sc->img_stage.as<float>();
     }
     const uint32_t count = sample_offset + spp;
-    sc->profiling = (o.flags & PT_FLAG_PROFILE) != 0;
-    sc->ev_used = 0;
+    sc->ev_reset((o.flags & PT_FLAG_PROFILE) != 0);
     sc->last_stream = st;
     sc->last_mode = o.mode;
     sc->last_paths = n_paths;
@@ -782,6 +809,7 @@ pt_status render_impl(pt_scene* sc, const pt_camera* cam, uint32_t spp, uint32_t
     } else {
         PT_TRY(run_wavefront(sc, dc, p, o, n_paths, img, d_path_L_or_null, o.d_path_sig, st, accum, count));
     }
+    PT_TRY(sc->ev_flush(st));
     if (host_out) {
         PT_CUDA(cudaMemcpyAsync(d_out_rgb, img, n_pixels * 12, cudaMemcpyDeviceToHost, st));
         PT_CUDA(cudaStreamSynchronize(st));
@@ -1289,8 +1317,7 @@ pt_status pt_render_backward(pt_scene* sc, const pt_camera* cam, uint32_t spp, u
         PT_CUDA(cudaMemcpyAsync(sc->grad_stage.p, d_grad_rgb, n_pixels * 12, cudaMemcpyHostToDevice, st));
         grad = sc->grad_stage.as<float>();
     }
-    sc->profiling = (o.flags & PT_FLAG_PROFILE) != 0;
-    sc->ev_used = 0;
+    sc->ev_reset((o.flags & PT_FLAG_PROFILE) != 0);
     sc->last_stream = st;
     sc->last_mode = 2;
     sc->last_paths = n_paths;
@@ -1362,6 +1389,7 @@ pt_status pt_render_backward(pt_scene* sc, const pt_camera* cam, uint32_t spp, u
         }
     }
     PT_TRY(sc->ev_end(ev, st));
+    PT_TRY(sc->ev_flush(st));
     return PT_OK;
 }
 
@@ -1448,7 +1476,9 @@ pt_status pt_get_stats(pt_scene* sc, pt_stats* out) {
         uint32_t n_ext = 0, n_shd = 0;
         for (size_t i = 0; i < sc->ev_used; ++i) {
             float t = 0.f;
-            PT_CUDA(cudaEventElapsedTime(&t, sc->events[i].a, sc->events[i].b));
+            const auto& e = sc->events[i];
+            if (e.a < 0 || e.b < 0) continue;      // a call that failed before the stage ended
+            PT_CUDA(cudaEventElapsedTime(&t, sc->ev_pool[e.a], sc->ev_pool[e.b]));
             ms[sc->events[i].stage] += t;
             if (sc->events[i].stage == ST_EXTEND) ++n_ext;
             if (sc->events[i].stage == ST_SHADOW) ++n_shd;
