@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(256, 3) k_shade_adj(SingleSrc src, WfBuffers w
 template <bool INST>
 __global__ void __launch_bounds__(256) k_shadow_adj(SingleSrc src, WfBuffers w, AdjBuffers a, uint32_t b) {
     const uint32_t n = min(w.counts[2], w.capacity);
+    if (n == 0u) return;
     const size_t cap = w.capacity;
     for (uint32_t b0 = warp_claim32(&w.counts[5]); b0 < n; b0 = warp_claim32(&w.counts[5])) {
         const uint32_t j = b0 + lane_id();

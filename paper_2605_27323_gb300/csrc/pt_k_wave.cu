@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(256) k_raygen(Src src, uint64_t base, uint32_t
 template <class Src, bool INST>
 __global__ void __launch_bounds__(256, INST ? 4 : 6) k_extend(Src src, WfBuffers w, int in) {
     const uint32_t n = min(w.counts[0], w.capacity);
+    if (n == 0u) return;       // an emptied queue: no claims (the same for every thread)
     const uint64_t base = src.base();
     const float4* __restrict__ qo = w.q_o[in];
     const float4* __restrict__ qd = w.q_d[in];
@@ -225,6 +226,7 @@ __global__ void __launch_bounds__(256, 3) k_shade(Src src, WfBuffers w, int in, 
 template <class Src, bool SIG, bool INST>
 __global__ void __launch_bounds__(256) k_shadow(Src src, WfBuffers w, uint32_t b) {
     const uint32_t n = min(w.counts[2], w.capacity);
+    if (n == 0u) return;
     const uint64_t base = src.base();
     for (uint32_t b0 = warp_claim32(&w.counts[5]); b0 < n; b0 = warp_claim32(&w.counts[5])) {
         const uint32_t j = b0 + lane_id();
