@@ -377,17 +377,6 @@ def run_gpu(args):
                           "mrays_s": (st_v["extension_rays"] + st_v["shadow_rays"]) / (float(np.mean(ms)) * 1e-3) / 1e6}
     variants["wf_over_mk_no_stage_events"] = (variants["megakernel_no_stage_events"]["ms_per_frame"] /
                                               variants["wavefront_no_stage_events"]["ms_per_frame"])
-    # the adjoint's one-thread-per-path replay (mode="megakernel"), not in the step
-    ms = []
-    for k in range(3):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        g.backward(cam, spp, depth, 930 + k, grad, rr_start=3, mode="megakernel")
-        e1.record(stream)
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
-        flush.fill_(k & 0xFF)
-    variants["adjoint_one_thread_per_path"] = {"ms_per_pass": float(np.mean(ms[1:]))}
     out = None
     if rank == 0:
         e2e = measure_e2e(g, cam, spp, depth, grad, args, wf_opts, mk_opts) if world == 1 else None
@@ -604,6 +593,15 @@ def run_diff(args):
     st = g.stats()
     rays_fwd = st["extension_rays"] + st["shadow_rays"]
     alb_err = float((alb.detach() - alb_t)[lam].abs().mean())
+    # the adjoint's one-thread-per-path replay (mode="megakernel") on the same gradient, for comparison
+    grad_img = torch.ones_like(target) * (1.0 / target.numel())
+    g.backward(cam, spp, depth, 1, grad_img, mode="megakernel", **kw)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.backward(cam, spp, depth, 2, grad_img, mode="megakernel", **kw)
+    e1.record(stream)
+    e1.synchronize()
+    bwd_mk = e0.elapsed_time(e1)
     line = {"metric": "inverse-rendering step: backward/forward time ratio (512x512, 64 spp, depth 6, 256 materials)",
             "value": float(np.median(bwd) / np.median(fwd)), "unit": "ratio", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(np.mean(tot)), "higher_is_better": False, "scaling": "weak",
@@ -613,6 +611,7 @@ def run_diff(args):
                                    "(seed 7); Adam on albedo and emission",
                        "paths": n_paths, "l2": "inputs (scene, queues, records) exceed L2; no flush"},
             "forward_ms": float(np.median(fwd)), "backward_ms": float(np.median(bwd)),
+            "backward_one_thread_per_path_ms": bwd_mk,
             "forward_mrays_s": rays_fwd / (np.median(fwd) * 1e-3) / 1e6,
             "loss_first": losses[0], "loss_last": losses[-1],
             "lambert_albedo_mean_abs_error": {"start": alb_err0, "end": alb_err,
