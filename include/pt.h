@@ -110,7 +110,11 @@ typedef struct {
     uint32_t status;            /* device status word: 0 or a pt_status */
     uint64_t active[64];        /* wavefront: active paths entering each bounce (all waves) */
     /* PT_FLAG_PROFILE: total milliseconds per stage of the last profiled call, and launches
-       (ms_megakernel includes the hybrid continuation kernel of a wavefront render) */
+       (ms_megakernel includes the hybrid continuation kernel of a wavefront render).  A stage's
+       interval runs from an event recorded before its first launch to the event that starts the
+       next stage (or ends the call): consecutive stages share one event, and bookkeeping launches
+       and launch gaps between two stages count toward the earlier one.  ms_adjoint spans the
+       whole backward pass, which contains its replay's stages. */
     float ms_raygen, ms_extend, ms_sort, ms_shade, ms_shadow, ms_reduce, ms_megakernel, ms_adjoint;
     uint32_t launches_extend, launches_shadow, launches_total;
     float ms_total;
@@ -196,7 +200,8 @@ pt_status pt_render_progressive(pt_scene* scene, const pt_camera* cam, uint32_t 
  * replay: PT_MODE_WAVEFRONT (default) re-runs the wavefront stages with shading that writes a
  * 64-byte record per path and vertex into a library workspace (waves are sized to keep it under
  * 8 GiB), then walks each path's records backward; PT_MODE_MEGAKERNEL replays each path in one
- * thread with the records in thread-local memory.  d_grad_albedo (device n_mats x 3) and
+ * thread with the records in thread-local memory, and a thread whose path is done takes the next
+ * one.  d_grad_albedo (device n_mats x 3) and
  * d_grad_emission (device n_mats) are ACCUMULATED into (the caller zeroes them).  max_depth <= 32
  * (else PT_ERR_UNSUPPORTED). */
 pt_status pt_render_backward(pt_scene* scene, const pt_camera* cam, uint32_t spp, uint32_t max_depth,
