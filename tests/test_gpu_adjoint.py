@@ -152,11 +152,12 @@ def test_autograd_l2_loss_against_hidden_target(pt, torch):
     assert float(A.grad.abs().sum()) > 0
 
 
-@pytest.mark.parametrize("spp,depth,rr", [(4, 6, 0.0), (1, 12, 0.8)])
+@pytest.mark.parametrize("spp,depth,rr", [(4, 6, 0.0), (1, 12, 0.8), (2, 24, 0.9), (3, 32, 0.95)])
 def test_wavefront_and_megakernel_replays_agree(pt, torch, spp, depth, rr):
     """The two replays of the adjoint (wavefront stages writing vertex records, and one thread per
-    path with thread-local records) compute the same gradients; only the order of the FP32 atomic
-    additions differs."""
+    path with thread-local records and path regeneration) compute the same gradients; only the
+    order of the FP32 atomic additions differs.  Depths 12, 24 and 32 take the 16- and 32-vertex
+    record arrays of the one-thread-per-path replay."""
     sc = _c5_scene()
     cam = dict(sc["camera"], width=160, height=90)
     g = pt.Scene.from_dict(sc)
