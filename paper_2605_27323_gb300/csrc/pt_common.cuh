@@ -67,7 +67,7 @@ struct LogRec {   // event list with two diagnostic numbers per event (testing a
 // One whole path (Sec. 2.2 steps 1-5) in registers: the body of the megakernel.
 template <class Rec, bool MIS, bool INST>
 __device__ __forceinline__ float3 mk_path(const DevScene& s, const DevCamera& c, const RenderParams& p, uint64_t path,
-                                          Rec& rec, unsigned long long& n_ext, unsigned long long& n_shd) {
+                                          Rec& rec, uint32_t& n_ext, uint32_t& n_shd) {
     const float3 env = f3(s.env_r, s.env_g, s.env_b);
     const uint32_t pixel = (uint32_t)(path / p.spp);
     const uint32_t sample = p.sample_offset + (uint32_t)(path - (uint64_t)pixel * p.spp);
@@ -118,8 +118,8 @@ __device__ __forceinline__ float3 mk_path(const DevScene& s, const DevCamera& c,
 template <bool SIG, bool MIS, bool INST>
 __device__ __forceinline__ bool mk_bounce(const DevScene& s, const RenderParams& p, float3 env, uint32_t key,
                                           uint32_t& b, float3& o, float3& d, float3& tp, bool& prev_delta,
-                                          float& prev_pdf, float3& L, uint32_t& sg, unsigned long long& n_ext,
-                                          unsigned long long& n_shd) {
+                                          float& prev_pdf, float3& L, uint32_t& sg, uint32_t& n_ext,
+                                          uint32_t& n_shd) {
     ++n_ext;
     Hit h = trace_closest<INST>(s, o, d);
     if (h.tri == kMiss) {

@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(128, 8) k_megakernel_regen(DevScene s, DevCame
                                                           uint32_t* __restrict__ sig,
                                                           unsigned long long* __restrict__ rays,
                                                           unsigned long long* __restrict__ next_path) {
-    unsigned long long n_ext = 0, n_shd = 0;
+    uint32_t n_ext = 0, n_shd = 0;
     const float3 env = f3(s.env_r, s.env_g, s.env_b);
     bool active = false, exhausted = false;
     uint64_t i = 0;
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(128, 8) k_finish(SingleSrc src, WfBuffers w, i
     const DevScene& s = src.s;
     const RenderParams& p = src.p;
     const float3 env = f3(s.env_r, s.env_g, s.env_b);
-    unsigned long long n_ext = 0, n_shd = 0;
+    uint32_t n_ext = 0, n_shd = 0;
     bool active = false, exhausted = false;
     uint32_t pid = 0, key = 0, b = 0, sg = 0;
     uint64_t path = 0;
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(128, 8) k_finish(SingleSrc src, WfBuffers w, i
         if (!__any_sync(0xFFFFFFFFu, active)) break;
         if (active) {
             const uint32_t bb = b;
-            const unsigned long long shd0 = n_shd;
+            const uint32_t shd0 = n_shd;
             atomicAdd(&h_s[bb & 63u], 1u);
             const bool end = mk_bounce<SIG, MIS, INST>(s, p, env, key, b, o, d, tp, prev_delta, prev_pdf, L, sg, n_ext, n_shd);
             if (n_shd != shd0) atomicAdd(&h_s[64u + (bb & 63u)], 1u);

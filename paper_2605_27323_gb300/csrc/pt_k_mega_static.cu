@@ -9,7 +9,7 @@ template <bool SIG, bool MIS, bool INST>
 __global__ void __launch_bounds__(256) k_megakernel(DevScene s, DevCamera c, RenderParams p, uint64_t n_paths,
                                                     float* __restrict__ out_L, float* __restrict__ img,
                                                     uint32_t* __restrict__ sig, unsigned long long* __restrict__ rays) {
-    unsigned long long n_ext = 0, n_shd = 0;
+    uint32_t n_ext = 0, n_shd = 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_paths; i += stride) {
         const uint64_t path = p.path_begin + i;
@@ -44,7 +44,7 @@ __global__ void k_debug_paths(DevScene s, DevCamera c, RenderParams p, const uns
                               uint32_t* __restrict__ n_ev, float* __restrict__ out_L) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    unsigned long long a = 0, b = 0;
+    uint32_t a = 0, b = 0;
     LogRec r;
     r.ev_u = ev_u + (size_t)i * 2 * kMaxEvents;
     r.ev_f = ev_f + (size_t)i * 2 * kMaxEvents;
