@@ -43,7 +43,17 @@ BYTES_PER_UNIT = {
     "shadow": 80,      # per shadow ray: o|tmax + d|id (32 B) + contribution (16 B) read, L rw (32 B)
     "shade": 184,      # per active path: ray+tp (48) + hit (8) + L rw (32) + next ray (48) + shadow (48)
     "megakernel": 12,  # per path: radiance written (scene reads amortise to ~0 per path)
+    "raygen": 64,      # per path: ray + throughput (48 B) and radiance (16 B) written
+    "reduce": 16,      # per path: radiance read (the image, 12 B per pixel, is added per pixel)
 }
+
+
+def wavefront_frame_bytes(st: dict, n_paths: int, n_pixels: int) -> float:
+    """Algorithmic bytes of one wavefront frame from its device counts: every stage's per-unit
+    bytes times the units it processed (extension rays = paths entering each bounce)."""
+    ext = float(sum(st["active"]))
+    return (ext * (BYTES_PER_UNIT["extend"] + BYTES_PER_UNIT["shade"]) + st["shadow_rays"] * BYTES_PER_UNIT["shadow"]
+            + n_paths * (BYTES_PER_UNIT["raygen"] + BYTES_PER_UNIT["reduce"]) + n_pixels * 12)
 
 
 def rank_seed(step: int, rank: int) -> int:
@@ -339,6 +349,12 @@ def run_gpu(args):
 
     wf_frame = float(np.mean(wf_ms))
     mk_frame = float(np.mean(mk_ms))
+    wf_bytes = float(np.mean([wavefront_frame_bytes(r[3], n_paths, W * H) for r in recs]))
+    wf_bpr = wf_bytes / float(np.mean(wf_rays))
+    wf_roof = {"bound": "hbm", "algorithmic_bytes_per_frame": wf_bytes, "bytes_per_ray": wf_bpr,
+               "achieved": wf_bytes / (wf_frame * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+               "frac": wf_bytes / (wf_frame * 1e-3) / 1e9 / peak,
+               "mrays_s_bound": peak * 1e9 / wf_bpr / 1e6}
     # the paper's megakernel layout (one thread per path over all paths), timed apart from the step
     st_ms = []
     for s_ in range(max(3, args.steps // 2)):
@@ -388,9 +404,14 @@ def run_gpu(args):
                        "triangles": int(g.info()["n_tris"]), "sort": args.sort,
                        "l2": "flushed between steps (256 MiB write), outside the timed events"},
             "wavefront": {"mrays_s": float(np.sum(wf_rays)) / (np.sum(wf_ms) * 1e-3) / 1e6, "ms_per_frame": wf_frame,
-                          "rays_per_frame": float(np.mean(wf_rays))},
+                          "ms_per_frame_median": float(np.median(wf_ms)), "rays_per_frame": float(np.mean(wf_rays)),
+                          "mpaths_s": n_paths / (wf_frame * 1e-3) / 1e6},
             "megakernel": {"mrays_s": float(np.sum(mk_rays)) / (np.sum(mk_ms) * 1e-3) / 1e6,
-                           "ms_per_frame": mk_frame, "rays_per_frame": float(np.mean(mk_rays))},
+                           "ms_per_frame": mk_frame, "ms_per_frame_median": float(np.median(mk_ms)),
+                           "rays_per_frame": float(np.mean(mk_rays)), "mpaths_s": n_paths / (mk_frame * 1e-3) / 1e6},
+            # the whole wavefront frame against HBM: every stage's algorithmic bytes (queue and
+            # state traffic) over the frame time; its bound in rays/s is peak / (bytes per ray)
+            "wavefront_frame_roofline": wf_roof,
             "hybrid": {"ms_per_frame": hyb[hyb_thr], "threshold": hyb_thr, "sweep_ms": hyb,
                        "wavefront_over_hybrid": wf_frame / hyb[hyb_thr],
                        "note": "wavefront frame whose remaining bounces run in one persistent kernel once at "

@@ -57,6 +57,11 @@ def test_numbers_hang_together(line):
     cam_px = line["config"]["resolution"][0] * line["config"]["resolution"][1]
     assert e["h2d_bytes_per_step"] == cam_px * 12                 # the gradient image
     assert e["d2h_bytes_per_step"] >= 2 * cam_px * 12             # both images (+ the gradients)
+    f = line["wavefront_frame_roofline"]
+    assert f["unit"] == "GB/s" and 0.0 < f["frac"] < 1.0 and abs(f["frac"] - f["achieved"] / f["peak"]) < 1e-9
+    assert f["bytes_per_ray"] > 40 and f["mrays_s_bound"] > wf["mrays_s"]
+    px = line["config"]["resolution"][0] * line["config"]["resolution"][1] * line["config"]["spp"]
+    assert abs(wf["mpaths_s"] - px / (wf["ms_per_frame"] * 1e-3) / 1e6) <= 1e-6 * wf["mpaths_s"]
     c = line["cpu_baseline"]
     assert c["kind"] == "oracle" and c["cores"] >= 1 and c["value"] > 0 and c["unit"] == line["unit"]
     assert line["clocks"]["sm_mhz"] > 0
