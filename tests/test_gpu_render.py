@@ -175,8 +175,12 @@ def test_wavefront_sort_and_waves_are_bitwise_identical(pt, torch):
     cam = sc["camera"]
     g = pt.Scene.from_dict(sc)
     ref = g.render(cam, 4, 8, 3, mode="wavefront").cpu().numpy()
+    # waves of 8, 36 and 124 paths: fewer paths than a warp, and a warp's claim past the end of
+    # the queue in the traversal stages
     for kw in ({"sort": "type"}, {"sort": "material"}, {"queue_capacity": 4 * 1000},
-               {"queue_capacity": 4 * 777, "sort": "material", "block_size": 128}, {"mode": "megakernel"},
+               {"queue_capacity": 4 * 777, "sort": "material", "block_size": 128},
+               {"queue_capacity": 8}, {"queue_capacity": 36}, {"queue_capacity": 124, "hybrid": 20},
+               {"mode": "megakernel"},
                {"mode": "megakernel", "block_size": 64}, {"mode": "megakernel", "mk_static": True},
                {"mode": "megakernel", "mk_static": True, "block_size": 96}):
         kw.setdefault("mode", "wavefront")
