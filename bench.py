@@ -180,11 +180,21 @@ def cpu_baseline(sc, budget_s=12.0, threads=None):
     t0 = time.perf_counter()
     _, rays1 = osc.render_pixels(cam, 1, sc["max_depth"], 0, pix1, rr_start=3, n_threads=1)
     dt1 = time.perf_counter() - t0
+    # and on the small box workload (128^2 pixels, 16 spp, depth 8), whole frame
+    from paper_2605_27323_gb300 import scenes
+    box = scenes.box_scene(seed=0, width=128, height=128)
+    obox = oracle.Scene.from_dict(box)
+    t0 = time.perf_counter()
+    _, rays_b = obox.render_pixels(box["camera"], 16, 8, 0, np.arange(128 * 128, dtype=np.uint32), rr_start=3,
+                                   n_threads=threads)
+    dt_b = time.perf_counter() - t0
     return {"value": total / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
             "sample": f"{n} evenly strided pixels of the 1920x1080 frame, 1 spp, depth 5 ({total} rays, "
                       f"{dt:.1f} s, FP64, OpenMP)", "ms_per_frame_extrapolated": dt * 1e3 * n_pix / n,
             "single_core": {"value": float(rays1[0] + rays1[1]) / dt1 / 1e6, "unit": "Mrays/s",
-                            "sample": f"{len(pix1)} of those pixels"}}
+                            "sample": f"{len(pix1)} of those pixels"},
+            "box_128x128_16spp": {"value": float(rays_b[0] + rays_b[1]) / dt_b / 1e6, "unit": "Mrays/s",
+                                  "ms_per_frame": dt_b * 1e3}}
 
 
 def run_reference(args):
