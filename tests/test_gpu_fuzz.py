@@ -85,3 +85,27 @@ def test_random_scene_invariants(torch, seed):
     assert (same & ~close).sum() <= 1e-3 * same.sum(), (seed, np.flatnonzero(same & ~close)[:5])
     assert not np.any(same & ~near), (seed, np.flatnonzero(same & ~near)[:5])
     assert same.mean() >= 0.98, (seed, same.mean())
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_scene_as_instances_and_adjoint_replays(torch, seed):
+    """The same soup cut into exactly placed instances renders bit for bit like the flat soup (the
+    transforms are sign flips times powers of two), in both integrators; and the two replays of
+    the adjoint (wavefront records, one thread per path) give the same gradients up to the order
+    of their float-atomic sums."""
+    import paper_2605_27323_gb300 as pt
+    sc, spp, depth, opts = _case(seed)
+    cam = sc["camera"]
+    flat = pt.Scene.from_dict(sc)
+    inst = pt.Scene.from_dict(scenes.split_as_instances(sc, 2 + seed % 5, seed=seed))
+    for mode in ("wavefront", "megakernel"):
+        a = flat.render(cam, spp, depth, seed, mode=mode, sig=True, **opts)
+        b = inst.render(cam, spp, depth, seed, mode=mode, sig=True, **opts)
+        assert np.array_equal(a["img"].cpu().numpy(), b["img"].cpu().numpy()), (seed, mode)
+        assert np.array_equal(a["sig"].cpu().numpy(), b["sig"].cpu().numpy()), (seed, mode)
+    rng = np.random.default_rng(seed)
+    delta = torch.from_numpy(rng.uniform(0.0, 1.0, size=(cam["height"], cam["width"], 3)).astype(np.float32)).cuda()
+    ga_w, ge_w = flat.backward(cam, spp, depth, seed, delta, mode="wavefront", **opts)
+    ga_m, ge_m = flat.backward(cam, spp, depth, seed, delta, mode="megakernel", **opts)
+    assert torch.allclose(ga_w, ga_m, rtol=1e-4, atol=1e-6 * float(ga_m.abs().max()) + 1e-30), seed
+    assert torch.allclose(ge_w, ge_m, rtol=1e-4, atol=1e-6 * float(ge_m.abs().max()) + 1e-30), seed
