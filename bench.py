@@ -403,6 +403,28 @@ def run_gpu(args):
                           "mrays_s": (st_v["extension_rays"] + st_v["shadow_rays"]) / (float(np.mean(ms)) * 1e-3) / 1e6}
     variants["wf_over_mk_no_stage_events"] = (variants["megakernel_no_stage_events"]["ms_per_frame"] /
                                               variants["wavefront_no_stage_events"]["ms_per_frame"])
+    # the wavefront's advantage against the maximum depth (the paper expects it to grow with depth,
+    # as compaction leaves ever fewer active paths per bounce); frames without stage events
+    # (and the hybrid, which finishes the sparse late bounces in one kernel)
+    depth_sweep = {}
+    for dmax in (1, 2, 3, 5, 8, 12, 16):
+        row = {}
+        for name, kw in (("wavefront", dict(mode="wavefront")), ("megakernel", dict(mode="megakernel")),
+                         ("hybrid", dict(mode="wavefront", hybrid=hyb_thr))):
+            g.render(cam, spp, dmax, 950, rr_start=3, **kw)
+            ms = []
+            for k in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.render(cam, spp, dmax, 960 + k, rr_start=3, **kw)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                flush.fill_(k & 0xFF)
+            row[name + "_ms"] = float(np.mean(ms))
+        row["wf_over_mk"] = row["megakernel_ms"] / row["wavefront_ms"]
+        row["hybrid_over_mk"] = row["megakernel_ms"] / row["hybrid_ms"]
+        depth_sweep[str(dmax)] = row
     out = None
     if rank == 0:
         e2e = measure_e2e(g, cam, spp, depth, grad, args, wf_opts, mk_opts) if world == 1 else None
@@ -427,6 +449,7 @@ def run_gpu(args):
                        "note": "wavefront frame whose remaining bounces run in one persistent kernel once at "
                                "most `threshold` paths are active; same image; not in the step"},
             "estimator_variants": variants,
+            "depth_sweep": depth_sweep,
             "megakernel_static": {"ms_per_frame": float(np.mean(st_ms)),
                                   "mrays_s": float(np.mean(mk_rays)) / (float(np.mean(st_ms)) * 1e-3) / 1e6,
                                   "note": "one thread per path over all paths (the paper's layout); not in the step"},
