@@ -51,58 +51,105 @@ def _p(a):
     return a.ctypes.data_as(C.c_void_p)
 
 
+def build_variant(replacements, out_dir: str, name: str = "liboracle_variant.so") -> str:
+    """Compile a copy of oracle.c with textual replacements [(old, new), ...] into out_dir (testing
+    aid: the pins must fail on an oracle with a planted mistake).  Each `old` must occur exactly once."""
+    src = open(_SRC).read()
+    for old, new in replacements:
+        if src.count(old) != 1:
+            raise ValueError(f"planted change does not match exactly once: {old!r}")
+        src = src.replace(old, new)
+    os.makedirs(out_dir, exist_ok=True)
+    c_path = os.path.join(out_dir, name.replace(".so", ".c"))
+    with open(c_path, "w") as f:
+        f.write(src)
+    out = os.path.join(out_dir, name)
+    subprocess.run(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                    "-fno-fast-math", "-Wall", "-Wno-unused-function", c_path, "-o", out, "-lm"], check=True)
+    return out
+
+
+class use_library:
+    """Context manager: route every call of this module to another build of the oracle (a variant
+    from build_variant); the default library is restored on exit."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        with _lock:
+            self._saved = _lib
+            _lib = _load(self.path)
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        with _lock:
+            _lib = self._saved
+        return False
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = C.CDLL(_LIB_PATH)
-            vp, u32, u64, i64, i32, f32, f64 = (C.c_void_p, C.c_uint32, C.c_uint64, C.c_int64,
-                                                C.c_int, C.c_float, C.c_double)
-            L.or_pcg_hash.restype = u32
-            L.or_pcg_hash.argtypes = [u32]
-            L.or_path_key.restype = u32
-            L.or_path_key.argtypes = [u64, u32, u32]
-            L.or_u01.restype = f64
-            L.or_u01.argtypes = [u32, u32, u32]
-            L.or_u01_batch.argtypes = [u64, vp, vp, vp, vp, i64, vp]
-            L.or_radical_inverse24.restype = u32
-            L.or_radical_inverse24.argtypes = [u32, u32]
-            L.or_pixel_jitter_batch.argtypes = [u32, u64, vp, vp, i64, vp]
-            L.or_scene_create.restype = vp
-            L.or_scene_create.argtypes = [vp, i64, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp]
-            L.or_scene_destroy.argtypes = [vp]
-            L.or_scene_create_corners.restype = vp
-            L.or_scene_create_corners.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp, vp, vp]
-            L.or_scene_set_materials.argtypes = [vp, vp, vp]
-            L.or_scene_n_lights.restype = i64
-            L.or_scene_n_lights.argtypes = [vp]
-            L.or_scene_light_area.restype = f64
-            L.or_scene_light_area.argtypes = [vp]
-            L.or_intersect_batch.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp, vp]
-            L.or_occluded_batch.argtypes = [vp, vp, vp, vp, i64, i32, vp]
-            L.or_bsdf_eval.argtypes = [u32, vp, f64, vp, vp, vp, vp]
-            L.or_bsdf_sample.restype = i32
-            L.or_bsdf_sample.argtypes = [u32, vp, f64, f64, vp, vp, vp, f64, f64, f64, vp, vp, vp]
-            L.or_onb.argtypes = [vp, vp, vp]
-            L.or_bsdf_pdf.restype = f64
-            L.or_bsdf_pdf.argtypes = [u32, f64, vp, vp, vp]
-            L.or_fresnel_dielectric.restype = f64
-            L.or_fresnel_dielectric.argtypes = [f64, f64, f64]
-            L.or_ggx_D.restype = f64
-            L.or_ggx_D.argtypes = [f64, f64]
-            L.or_ggx_G1.restype = f64
-            L.or_ggx_G1.argtypes = [f64, f64]
-            L.or_render_paths.argtypes = [vp, vp, vp, vp, f32, u32, u32, u32, u32, u64, u32, f64, u32, i32,
-                                          vp, i64, i32, vp, vp, i32, vp, vp, vp, vp]
-            L.or_render_pixels.argtypes = [vp, vp, vp, vp, f32, u32, u32, u32, u32, u64, u32, f64, u32, i32,
-                                           vp, i64, i32, vp, vp]
-            L.or_trace_rays.argtypes = [vp, vp, vp, vp, i64, u32, u32, f64, u32, i32, i32, vp, vp, i32, vp, vp]
-            L.or_trace_path_events.argtypes = [vp, vp, vp, vp, f32, u32, u32, u32, u32, u64, u32, f64, u32, vp, i64, vp,
-                                               vp, vp, vp]
-            L.or_max_tangents.restype = i32
-            _lib = L
+            _lib = _load(_LIB_PATH)
     return _lib
+
+
+def _load(path: str):
+    """Open one build of the oracle and declare its C signatures."""
+    L = C.CDLL(path)
+    vp, u32, u64, i64, i32, f32, f64 = (C.c_void_p, C.c_uint32, C.c_uint64, C.c_int64,
+                                        C.c_int, C.c_float, C.c_double)
+    L.or_pcg_hash.restype = u32
+    L.or_pcg_hash.argtypes = [u32]
+    L.or_path_key.restype = u32
+    L.or_path_key.argtypes = [u64, u32, u32]
+    L.or_u01.restype = f64
+    L.or_u01.argtypes = [u32, u32, u32]
+    L.or_u01_batch.argtypes = [u64, vp, vp, vp, vp, i64, vp]
+    L.or_radical_inverse24.restype = u32
+    L.or_radical_inverse24.argtypes = [u32, u32]
+    L.or_pixel_jitter_batch.argtypes = [u32, u64, vp, vp, i64, vp]
+    L.or_scene_create.restype = vp
+    L.or_scene_create.argtypes = [vp, i64, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp]
+    L.or_scene_destroy.argtypes = [vp]
+    L.or_scene_create_corners.restype = vp
+    L.or_scene_create_corners.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp, vp, vp]
+    L.or_scene_set_materials.argtypes = [vp, vp, vp]
+    L.or_scene_n_lights.restype = i64
+    L.or_scene_n_lights.argtypes = [vp]
+    L.or_scene_light_area.restype = f64
+    L.or_scene_light_area.argtypes = [vp]
+    L.or_intersect_batch.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp, vp]
+    L.or_occluded_batch.argtypes = [vp, vp, vp, vp, i64, i32, vp]
+    L.or_bsdf_eval.argtypes = [u32, vp, f64, vp, vp, vp, vp]
+    L.or_bsdf_sample.restype = i32
+    L.or_bsdf_sample.argtypes = [u32, vp, f64, f64, vp, vp, vp, f64, f64, f64, vp, vp, vp]
+    L.or_onb.argtypes = [vp, vp, vp]
+    L.or_bsdf_pdf.restype = f64
+    L.or_bsdf_pdf.argtypes = [u32, f64, vp, vp, vp]
+    L.or_fresnel_dielectric.restype = f64
+    L.or_fresnel_dielectric.argtypes = [f64, f64, f64]
+    L.or_ggx_D.restype = f64
+    L.or_ggx_D.argtypes = [f64, f64]
+    L.or_ggx_G1.restype = f64
+    L.or_ggx_G1.argtypes = [f64, f64]
+    L.or_render_paths.argtypes = [vp, vp, vp, vp, f32, u32, u32, u32, u32, u64, u32, f64, u32, i32,
+                                  vp, i64, i32, vp, vp, i32, vp, vp, vp, vp]
+    L.or_render_pixels.argtypes = [vp, vp, vp, vp, f32, u32, u32, u32, u32, u64, u32, f64, u32, i32,
+                                   vp, i64, i32, vp, vp]
+    L.or_trace_rays.argtypes = [vp, vp, vp, vp, i64, u32, u32, f64, u32, i32, i32, vp, vp, i32, vp, vp]
+    L.or_trace_path_events.argtypes = [vp, vp, vp, vp, f32, u32, u32, u32, u32, u64, u32, f64, u32, vp, i64, vp,
+                                       vp, vp, vp]
+    L.or_max_tangents.restype = i32
+    L.or_camera_rays.argtypes = [vp, vp, vp, f32, u32, u32, vp, vp, vp, i64, vp, vp]
+    L.or_pick_light_batch.argtypes = [vp, vp, i64, vp]
+    L.or_scene_light_tris.argtypes = [vp, vp]
+    return L
 
 
 # ---------------------------------------------------------------- random numbers
@@ -143,6 +190,18 @@ def u01(seed, pixel, sample, bounce, dim) -> np.ndarray:
     out = np.empty(px.shape, np.float64)
     lib().or_u01_batch(seed, _p(px), _p(sm), _p(bo), _p(dm), px.size, _p(out))
     return out
+
+
+def camera_rays(cam: dict, pixel, u0, u1):
+    """The ray-generation step for explicit pixels and sub-pixel offsets: (origins, unit directions)."""
+    px = _f(pixel, np.uint32).reshape(-1)
+    a = _f(np.broadcast_to(u0, px.shape), np.float64)
+    b = _f(np.broadcast_to(u1, px.shape), np.float64)
+    o, d = np.empty((px.size, 3)), np.empty((px.size, 3))
+    lib().or_camera_rays(_p(_f(cam["eye"], np.float32)), _p(_f(cam["target"], np.float32)),
+                         _p(_f(cam["up"], np.float32)), float(cam["vfov_deg"]), int(cam["width"]),
+                         int(cam["height"]), _p(px), _p(a), _p(b), px.size, _p(o), _p(d))
+    return o, d
 
 
 # ---------------------------------------------------------------- BSDFs (pins)
@@ -254,6 +313,21 @@ class Scene:
     @property
     def light_area(self) -> float:
         return float(lib().or_scene_light_area(self.h))
+
+    def pick_light(self, u) -> np.ndarray:
+        """Light index drawn by each uniform (the NEE light pick on its own)."""
+        uu = _f(u, np.float64).reshape(-1)
+        out = np.empty(uu.size, np.int64)
+        lib().or_pick_light_batch(self.h, _p(uu), uu.size, _p(out))
+        return out
+
+    @property
+    def light_tris(self) -> np.ndarray:
+        """Triangle id of each light, in light-index order."""
+        out = np.empty(max(self.n_lights, 0), np.int64)
+        if out.size:
+            lib().or_scene_light_tris(self.h, _p(out))
+        return out
 
     def set_materials(self, albedo, emission):
         a = _f(albedo, np.float32).reshape(-1, 3)

@@ -40,8 +40,12 @@
  * Parity pins (tests/test_oracle_*.py): BVH closest hit == brute force; closed-form
  * intersections; Lambert/GGX/dielectric identities (reciprocity, sampled-weight == f cos/pdf,
  * normalisation, R + T = 1, Schlick and Fresnel limits); white-furnace series; the
- * differential-area-to-rectangle form factor; a glass-in-furnace identity; dual numbers ==
- * central finite differences of the oracle itself and == the furnace derivative series.
+ * differential-area-to-rectangle form factor, also with the rectangle light cut into triangles of
+ * very unequal area; the pinhole camera's geometry (centre ray at the target, half-angles vfov/2
+ * and atan(tan(vfov/2) W/H), square pixels, row 0 at the top, +x to the right); light picks
+ * counted against area / total area; a glass-in-furnace identity; dual numbers == central finite
+ * differences of the oracle itself and == the furnace derivative series.  The camera and
+ * light-pick pins are also run on copies of this file with planted mistakes, which must fail them.
  */
 #include <math.h>
 #include <stdint.h>
@@ -832,6 +836,16 @@ static int64_t pick_light(const or_scene* s, double u) {
     return lo;
 }
 
+/* The light-pick step on its own: out[i] = light index drawn by uniform u[i]. */
+void or_pick_light_batch(const or_scene* s, const double* u, int64_t n, int64_t* out) {
+    for (int64_t i = 0; i < n; ++i) out[i] = s->n_lights > 0 ? pick_light(s, u[i]) : -1;
+}
+
+/* Triangle id of each light, in light-index order (n_lights entries). */
+void or_scene_light_tris(const or_scene* s, int64_t* out) {
+    for (int64_t j = 0; j < s->n_lights; ++j) out[j] = s->light_tri[j];
+}
+
 /* One path from ray (o, d).  Adds radiance into L (dual), counts rays, writes the branch
  * signature.  Follows the steps of Sec. 2.2 with NEE (Sec. 3) and Russian roulette (Sec. 3.1). */
 static void trace(const or_scene* s, v3 o, v3 d, uint32_t key, const ropts* op, const dirs_t* dr,
@@ -969,6 +983,19 @@ static void camera_ray(const ocam* c, uint32_t pixel, double u0, double u1, v3* 
     double sy = ((double)y + u1) / (double)c->H;
     *o = c->eye;
     *d = nrm(sub(add(scl(c->u, (2.0 * sx - 1.0) * c->tw), scl(c->v, (1.0 - 2.0 * sy) * c->th)), c->w));
+}
+
+/* The ray-generation step on its own, for explicit (pixel, u0, u1): o_out, d_out are n x 3. */
+void or_camera_rays(const float* eye, const float* target, const float* up, float vfov_deg, uint32_t W, uint32_t H,
+                    const uint32_t* pixel, const double* u0, const double* u1, int64_t n, double* o_out,
+                    double* d_out) {
+    ocam cam = make_cam(eye, target, up, vfov_deg, W, H);
+    for (int64_t i = 0; i < n; ++i) {
+        v3 o, d;
+        camera_ray(&cam, pixel[i], u0[i], u1[i], &o, &d);
+        o_out[3 * i] = o.x; o_out[3 * i + 1] = o.y; o_out[3 * i + 2] = o.z;
+        d_out[3 * i] = d.x; d_out[3 * i + 1] = d.y; d_out[3 * i + 2] = d.z;
+    }
 }
 
 static int nthreads(int want) {

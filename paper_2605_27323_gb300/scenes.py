@@ -555,14 +555,26 @@ def furnace_sphere(albedo=0.5, emission=1.0, level=3, radius=1.0):
     return _scene(b, mats, (0.0, 0.0, 0.0), camera=cam)
 
 
-def rect_over_plane(albedo=0.7, emission=5.0, half_w=0.5, half_h=0.8, height=1.0, plane_half=10.0):
+def rect_over_plane(albedo=0.7, emission=5.0, half_w=0.5, half_h=0.8, height=1.0, plane_half=10.0, fan=None):
     """Lambert plane y=0 (large) under a parallel emitting rectangle at y=height facing down,
-    centred over the origin with half-sizes (half_w along x, half_h along z)."""
+    centred over the origin with half-sizes (half_w along x, half_h along z).
+
+    fan=(fx, fz): the rectangle is cut into six triangles of very unequal area instead of two equal
+    ones -- a fan around the interior point (fx * half_w, height, fz * half_h) through the four
+    corners and the midpoints of the -z and +x edges.  The emitting region, hence the irradiance of
+    the plane, is the same."""
     b = _Builder()
     b.add(*quad((-plane_half, 0, plane_half), (plane_half, 0, plane_half), (plane_half, 0, -plane_half),
                 (-plane_half, 0, -plane_half)), 0)
-    b.add(*quad((-half_w, height, -half_h), (half_w, height, -half_h), (half_w, height, half_h),
-                (-half_w, height, half_h)), 1)
+    corners = [(-half_w, height, -half_h), (half_w, height, -half_h), (half_w, height, half_h),
+               (-half_w, height, half_h)]
+    if fan is None:
+        b.add(*quad(*corners), 1)
+    else:
+        ring = [corners[0], (0.0, height, -half_h), corners[1], (half_w, height, 0.0), corners[2], corners[3]]
+        V = np.array([(fan[0] * half_w, height, fan[1] * half_h)] + ring, np.float64)
+        T = np.array([[0, 1 + k, 1 + (k + 1) % len(ring)] for k in range(len(ring))], np.int64)
+        b.add(V, T, 1)
     mats = _materials([LAMBERT, LAMBERT], [[albedo] * 3, [0.0] * 3], [0.0, emission], [0.5, 0.5], [1.5, 1.5])
     return _scene(b, mats, (0.0, 0.0, 0.0))
 
