@@ -98,7 +98,7 @@ typedef struct {
                                    paths of a wave are active entering a bounce, one persistent kernel
                                    finishes them all in registers (the megakernel's loop body) instead
                                    of running the remaining bounces as wavefront stages -- the hybrid of
-                                   the paper's future work (Sec. 5).  Decided on the device, so the
+                                   the paper's future work (Sec. 6.1).  Decided on the device, so the
                                    image is unchanged.  0 = off.  Ignored by the other entry points. */
 } pt_render_opts;
 
@@ -234,12 +234,17 @@ pt_status pt_trace_closest(pt_scene* scene, const float* d_rays, uint32_t n, flo
  * library do it -- an application whose own memory manager owns the whole device, or a real-time
  * loop that cannot absorb the implicit synchronisation of cudaMalloc/cudaFree.  Its queues live in
  * one 32 MiB file-scope device array that every GPU loading libpt.so holds until the process exits;
- * frames are rendered in waves of whole pixels that fit it (about 190,000 paths per wave), with the
+ * frames are rendered in waves of whole pixels that fit it (about 186,000 paths per wave), with the
  * same kernels and random numbers, so the image equals pt_render's.  Arguments as for pt_render,
  * except: d_out_rgb (and opts->d_path_sig, if set) must be device memory (nothing is staged), there
- * is no per-path output, opts->queue_capacity is ignored, and pt_get_stats does not report this call.
+ * is no per-path output, and of opts only rr_start, rr_fixed, sort_mode, block_size, d_path_sig and
+ * the flags PT_FLAG_HALTON and PT_FLAG_MIS are used (queue_capacity and the other flags are
+ * ignored).  Device-side faults of the call (the traversal step cap, a queue overflow) are recorded
+ * in a status word inside the array, which the call clears when it starts; they are not reported
+ * (pt_get_stats does not see this call and keeps describing the scene's last pt_render call).
  * Errors: PT_ERR_INVALID_ARG also when one pixel's spp samples need more than the array
- * (spp x 180 bytes > 32 MiB).  The first call on a device looks up the array's device address
+ * (spp x 180 bytes > 32 MiB), for opts->mode other than PT_MODE_WAVEFRONT and for a nonzero
+ * opts->hybrid_threshold.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share the
  * array and it keeps the last call's contents: each call clears its own counters, and calls that
  * overlap on the GPU (other streams or threads without ordering between them) race. */

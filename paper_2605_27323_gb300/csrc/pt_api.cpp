@@ -118,32 +118,10 @@ int blocks_per_sm(int which, int block) {
 
 enum Stage { ST_RAYGEN, ST_EXTEND, ST_SORT, ST_SHADE, ST_SHADOW, ST_REDUCE, ST_MEGA, ST_ADJOINT, ST_COUNT };
 
-// One device allocation carved into the wavefront arrays for `cap` paths (180 bytes each).
+// One device allocation carved into the wavefront arrays for `cap` paths (kWfBytesPerPath each).
 pt_status carve_wavefront(DevBuf& buf, uint64_t cap, pt::WfBuffers& w) {
-    size_t q = align256(cap * 16), h = align256(cap * 8), k = align256(cap * 4);
-    size_t total = 6 * q + h + 3 * k + align256(pt::kMaxSortKeys * 4) + 3 * q + q;
-    PT_TRY(buf.ensure(total));
-    char* base = buf.as<char>();
-    size_t off = 0;
-    auto take = [&](size_t n) {
-        char* r = base + off;
-        off += n;
-        return r;
-    };
-    for (int i = 0; i < 2; ++i) {
-        w.q_o[i] = reinterpret_cast<float4*>(take(q));
-        w.q_d[i] = reinterpret_cast<float4*>(take(q));
-        w.q_tp[i] = reinterpret_cast<float4*>(take(q));
-    }
-    w.hit = reinterpret_cast<float2*>(take(h));
-    w.hit_inst = reinterpret_cast<uint32_t*>(take(k));
-    w.keys = reinterpret_cast<uint32_t*>(take(k));
-    w.perm = reinterpret_cast<uint32_t*>(take(k));
-    w.bucket = reinterpret_cast<uint32_t*>(take(align256(pt::kMaxSortKeys * 4)));
-    w.s_o = reinterpret_cast<float4*>(take(q));
-    w.s_d = reinterpret_cast<float4*>(take(q));
-    w.s_c = reinterpret_cast<float4*>(take(q));
-    w.L = reinterpret_cast<float4*>(take(q));
+    PT_TRY(buf.ensure(pt::wavefront_bytes(cap)));
+    pt::carve_wavefront_at(buf.as<char>(), cap, w);
     return PT_OK;
 }
 

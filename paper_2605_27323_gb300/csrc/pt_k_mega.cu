@@ -1,6 +1,6 @@
 // pt_k_mega.cu -- the persistent megakernel with path regeneration (Sec. 2.2: one thread traces one
 // path to termination; a lane whose path ended claims the next one), and the hybrid continuation
-// kernel that finishes a wavefront's last sparse bounces with the same bounce function (Sec. 5).
+// kernel that finishes a wavefront's last sparse bounces with the same bounce function (Sec. 6.1).
 #include "pt_common.cuh"
 
 namespace pt {
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(128, 8) k_megakernel_regen(DevScene s, DevCame
 }
 
 
-// ---- hybrid wavefront / megakernel (the hybrid of the paper's future work, Sec. 5): once the
+// ---- hybrid wavefront / megakernel (the hybrid of the paper's future work, Sec. 6.1): once the
 // active count entering a bounce is at most `threshold`, one persistent kernel finishes every
 // remaining path in registers (the megakernel's loop body, lanes claiming queue entries as they
 // free up) instead of running the remaining bounces as sparse wavefront stages.  The decision is

@@ -6,10 +6,10 @@
 // The array is kStaticScratchBytes (32 MiB) and lives on every GPU that loads this library until
 // the process exits.  Frames larger than one array's worth of paths are rendered in waves of whole
 // pixels.  Every call shares the array: it keeps the previous call's contents, this file clears the
-// counters that must start at zero on every call, and calls that overlap on the GPU (other streams,
-// other threads) race on it.  The first call on a device looks up the array's device address with
-// cudaGetSymbolAddress (the host-side name is only a stand-in); make that first call before any
-// stream capture.  Nothing here calls cudaMalloc, cudaFree or an allocating library routine.
+// counters and the call's status word that must start at zero on every call, and calls that overlap
+// on the GPU (other streams, other threads) race on it.  The first call on a device looks up the
+// array's device address with cudaGetSymbolAddress (the host-side name is only a stand-in); make
+// that first call before any stream capture.  Nothing here calls cudaMalloc, cudaFree or an allocating library routine.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,15 +30,14 @@ bool static_is_device_ptr(const void* p);
 namespace {
 
 constexpr size_t kStaticScratchBytes = 32ull << 20;
-constexpr size_t kBytesPerPath = 180;           // the wavefront's per-path queue records
+constexpr size_t kHeaderBytes = 256 + 8 * 128;  // counters (incl. this call's status word) and histories
+constexpr uint32_t kStatusWord = 16;            // counts[16]: device status word of this call
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 std::mutex g_mu;
 unsigned char* g_addr[kMaxDevices] = {};
-
-size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Device address of the array on `device` (which is current), looked up once per device.
 pt_status scratch_address(int device, unsigned char** out) {
@@ -59,10 +58,13 @@ pt_status scratch_address(int device, unsigned char** out) {
     return PT_OK;
 }
 
-// Paths one wave can hold after the fixed regions (counters, histories, sort buckets).
+// Paths one wave can hold: the largest capacity whose records (the allocating entry points' layout)
+// fit the array after the header.
 uint64_t wave_capacity() {
-    size_t fixed = a256(256) + a256(8 * 128) + a256(pt::kMaxSortKeys * 4) + 17 * 256;
-    return (kStaticScratchBytes - fixed) / kBytesPerPath;
+    const size_t avail = kStaticScratchBytes - kHeaderBytes;
+    uint64_t cap = avail / pt::kWfBytesPerPath;
+    while (cap > 0 && pt::wavefront_bytes(cap) > avail) --cap;
+    return cap;
 }
 
 pt_status cuda_fail(cudaError_t e, const char* what) {
@@ -85,6 +87,10 @@ extern "C" pt_status pt_render_wavefront_static(pt_scene* scene, const pt_camera
     int device = 0;
     pt_status s = pt::static_prepare(scene, cam, opts, &ds, &dc, &o, &device);
     if (s != PT_OK) return s;
+    if (o.mode != PT_MODE_WAVEFRONT)
+        return pt::static_set_error(PT_ERR_INVALID_ARG, "this entry point renders with the wavefront only (opts->mode)");
+    if (o.hybrid_threshold)
+        return pt::static_set_error(PT_ERR_INVALID_ARG, "this entry point has no hybrid continuation (opts->hybrid_threshold)");
     if (!pt::static_is_device_ptr(d_out_rgb))
         return pt::static_set_error(PT_ERR_INVALID_ARG, "d_out_rgb must be device memory (this call stages nothing)");
     if (o.d_path_sig && !pt::static_is_device_ptr(o.d_path_sig))
@@ -93,7 +99,7 @@ extern "C" pt_status pt_render_wavefront_static(pt_scene* scene, const pt_camera
     if (spp > cap_max) {
         char msg[200];
         std::snprintf(msg, sizeof msg, "spp %u needs %llu bytes per pixel; the static scratch holds %llu paths (%zu MiB)",
-                      spp, (unsigned long long)spp * kBytesPerPath, (unsigned long long)cap_max,
+                      spp, (unsigned long long)spp * pt::kWfBytesPerPath, (unsigned long long)cap_max,
                       kStaticScratchBytes >> 20);
         return pt::static_set_error(PT_ERR_INVALID_ARG, msg);
     }
@@ -104,38 +110,23 @@ extern "C" pt_status pt_render_wavefront_static(pt_scene* scene, const pt_camera
     const uint64_t n_paths = n_pixels * spp;
     const uint64_t cap = cap_max - cap_max % spp;
 
-    // carve the array: counters, histories, sort buckets, then the per-path records
+    // the array: counters and histories, then the wavefront records in the allocating layout
     pt::WfBuffers w{};
-    size_t off = 0;
-    auto take = [&](size_t n) {
-        unsigned char* r = base + off;
-        off += a256(n);
-        return r;
-    };
-    w.counts = reinterpret_cast<uint32_t*>(take(256));
-    w.hist = reinterpret_cast<unsigned long long*>(take(8 * 128));
-    w.bucket = reinterpret_cast<uint32_t*>(take(pt::kMaxSortKeys * 4));
-    for (int i = 0; i < 2; ++i) {
-        w.q_o[i] = reinterpret_cast<float4*>(take(cap * 16));
-        w.q_d[i] = reinterpret_cast<float4*>(take(cap * 16));
-        w.q_tp[i] = reinterpret_cast<float4*>(take(cap * 16));
-    }
-    w.hit = reinterpret_cast<float2*>(take(cap * 8));
-    w.hit_inst = reinterpret_cast<uint32_t*>(take(cap * 4));
-    w.keys = reinterpret_cast<uint32_t*>(take(cap * 4));
-    w.perm = reinterpret_cast<uint32_t*>(take(cap * 4));
-    w.s_o = reinterpret_cast<float4*>(take(cap * 16));
-    w.s_d = reinterpret_cast<float4*>(take(cap * 16));
-    w.s_c = reinterpret_cast<float4*>(take(cap * 16));
-    w.L = reinterpret_cast<float4*>(take(cap * 16));
-    if (off > kStaticScratchBytes) return pt::static_set_error(PT_ERR_UNSUPPORTED, "static scratch layout overflow");
+    w.counts = reinterpret_cast<uint32_t*>(base);
+    w.hist = reinterpret_cast<unsigned long long*>(base + 256);
+    const size_t used = kHeaderBytes + pt::carve_wavefront_at(reinterpret_cast<char*>(base) + kHeaderBytes, cap, w);
+    if (used > kStaticScratchBytes) return pt::static_set_error(PT_ERR_UNSUPPORTED, "static scratch layout overflow");
     w.sig = o.d_path_sig;
     w.capacity = (uint32_t)cap;
+    // faults of this call (traversal cap, queue overflow) go to a word of the array, not to the
+    // scene's status word, so pt_get_stats keeps describing the scene's last pt_render call
+    ds.status = w.counts + kStatusWord;
 
-    cudaError_t e = cudaMemsetAsync(base, 0, a256(256) + a256(8 * 128), st);   // counts and histories
+    cudaError_t e = cudaMemsetAsync(base, 0, kHeaderBytes, st);   // counters, status word, histories
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     if (max_depth == 0) {
         e = cudaMemsetAsync(d_out_rgb, 0, n_pixels * 12, st);
+        if (e == cudaSuccess && o.d_path_sig) e = cudaMemsetAsync(o.d_path_sig, 0, n_paths * 4, st);
         return e == cudaSuccess ? PT_OK : cuda_fail(e, "cudaMemsetAsync");
     }
     int sms = 1;
@@ -144,13 +135,17 @@ extern "C" pt_status pt_render_wavefront_static(pt_scene* scene, const pt_camera
         sms = 1;
     }
     const int block = o.block_size ? (int)o.block_size : 256;
-    auto persistent = [&](int which) {
-        if (ds.tlas)   // the two-level instantiations have their own register counts
-            which = which == pt::K_EXTEND ? pt::K_EXTEND_INST : which == pt::K_SHADE ? pt::K_SHADE_INST
-                  : which == pt::K_SHADOW ? pt::K_SHADOW_INST : which;
+    // resident blocks per SM of the three persistent stages, looked up once per call (the two-level
+    // instantiations have their own register counts)
+    const bool inst = ds.tlas != nullptr;
+    const int per_extend = pt::max_blocks_per_sm(inst ? pt::K_EXTEND_INST : pt::K_EXTEND, block);
+    const int per_shade = pt::max_blocks_per_sm(inst ? pt::K_SHADE_INST : pt::K_SHADE, block);
+    const int per_shadow = pt::max_blocks_per_sm(inst ? pt::K_SHADOW_INST : pt::K_SHADOW, block);
+    auto persistent = [&](int per, uint64_t work) {
         pt::Launch l;
         l.block = block;
-        l.grid = std::max(1, sms * pt::max_blocks_per_sm(which, block));
+        const uint64_t need = (work + block - 1) / block;
+        l.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sms * std::max(per, 1), need));
         l.st = st;
         return l;
     };
@@ -176,15 +171,15 @@ extern "C" pt_status pt_render_wavefront_static(pt_scene* scene, const pt_camera
     for (uint64_t w0 = 0; w0 < n_paths; w0 += cap) {
         const uint32_t n = (uint32_t)std::min<uint64_t>(cap, n_paths - w0);
         p.path_begin = w0;
+        const pt::Launch le = persistent(per_extend, n), ls = persistent(per_shade, n), lw = persistent(per_shadow, n);
         if ((e = pt::launch_raygen(plain(n), dc, p, n, w)) != cudaSuccess) return cuda_fail(e, "raygen");
         for (uint32_t b = 0; b < max_depth; ++b) {
             const int in = (int)(b & 1u);
-            if ((e = pt::launch_extend(persistent(pt::K_EXTEND), ds, w, in, p)) != cudaSuccess) return cuda_fail(e, "extend");
+            if ((e = pt::launch_extend(le, ds, w, in, p)) != cudaSuccess) return cuda_fail(e, "extend");
             if (n_keys && (e = pt::launch_sort(plain(n), ds, w, in, sort_mode, n_keys, p)) != cudaSuccess)
                 return cuda_fail(e, "sort");
-            if ((e = pt::launch_shade(persistent(pt::K_SHADE), ds, p, w, in, b, n_keys > 0)) != cudaSuccess)
-                return cuda_fail(e, "shade");
-            if ((e = pt::launch_shadow(persistent(pt::K_SHADOW), ds, p, w, b)) != cudaSuccess) return cuda_fail(e, "shadow");
+            if ((e = pt::launch_shade(ls, ds, p, w, in, b, n_keys > 0)) != cudaSuccess) return cuda_fail(e, "shade");
+            if ((e = pt::launch_shadow(lw, ds, p, w, b)) != cudaSuccess) return cuda_fail(e, "shadow");
             if ((e = pt::launch_prepare(st, w, b)) != cudaSuccess) return cuda_fail(e, "prepare");
         }
         if ((e = pt::launch_reduce(plain(n / spp), reinterpret_cast<const float*>(w.L), 4, w0 / spp, n / spp, spp,

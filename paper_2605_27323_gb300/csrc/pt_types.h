@@ -122,4 +122,44 @@ struct AdjBuffers {
 constexpr uint32_t kMaxSortKeys = 4096;
 constexpr uint32_t kMaxEvents = 64;     // event-log capacity per path (testing aid)
 
+// Device bytes of one wave's records per path: two ping-pong ray queues of three float4 arrays, the
+// hit record (float2), the hit instance, sort key and permutation (u32 each), the shadow queue (three
+// float4 arrays) and the radiance (float4).
+constexpr size_t kWfBytesPerPath = 2 * 3 * 16 + 8 + 3 * 4 + 3 * 16 + 16;
+static_assert(kWfBytesPerPath == 180, "wavefront record layout changed: update the documented sizes");
+
+inline size_t wf_align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Carve the wavefront arrays of `cap` paths (and the sort buckets) out of `base` (null: only count);
+// returns the bytes used.  The single layout of both the allocating entry points and the
+// allocation-free one.
+inline size_t carve_wavefront_at(char* base, uint64_t cap, WfBuffers& w) {
+    size_t off = 0;
+    auto take = [&](size_t n) {
+        char* r = base ? base + off : nullptr;
+        off += wf_align256(n);
+        return r;
+    };
+    for (int i = 0; i < 2; ++i) {
+        w.q_o[i] = reinterpret_cast<float4*>(take(cap * 16));
+        w.q_d[i] = reinterpret_cast<float4*>(take(cap * 16));
+        w.q_tp[i] = reinterpret_cast<float4*>(take(cap * 16));
+    }
+    w.hit = reinterpret_cast<float2*>(take(cap * 8));
+    w.hit_inst = reinterpret_cast<uint32_t*>(take(cap * 4));
+    w.keys = reinterpret_cast<uint32_t*>(take(cap * 4));
+    w.perm = reinterpret_cast<uint32_t*>(take(cap * 4));
+    w.bucket = reinterpret_cast<uint32_t*>(take(kMaxSortKeys * 4));
+    w.s_o = reinterpret_cast<float4*>(take(cap * 16));
+    w.s_d = reinterpret_cast<float4*>(take(cap * 16));
+    w.s_c = reinterpret_cast<float4*>(take(cap * 16));
+    w.L = reinterpret_cast<float4*>(take(cap * 16));
+    return off;
+}
+
+inline size_t wavefront_bytes(uint64_t cap) {
+    WfBuffers w{};
+    return carve_wavefront_at(nullptr, cap, w);
+}
+
 }  // namespace pt

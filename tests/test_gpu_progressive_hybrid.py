@@ -1,5 +1,5 @@
 """Progressive accumulation (the running average of the accumulation stage, Sec. 2.3) and the
-hybrid wavefront/megakernel render (the hybrid named as future work, Sec. 5).
+hybrid wavefront/megakernel render (the hybrid named as future work, Sec. 6.1).
 
 Progressive frames continue each pixel's FP32 sum in sample order, so frames of k1, k2, ... samples
 must give the one-call image of k1 + k2 + ... samples bit for bit, in both modes and across waves,

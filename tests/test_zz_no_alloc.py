@@ -97,3 +97,29 @@ def test_static_scratch_rejects_what_it_cannot_hold():
     assert lib.pt_render_wavefront_static(g.h, C.byref(c), 1, 4, 0, C.byref(o), host.ctypes.data_as(C.c_void_p),
                                           stream) == 1
     assert b"device memory" in lib.pt_last_error()
+    # the megakernel and the hybrid continuation are not part of this entry point
+    for kw in ({"mode": "megakernel"}, {"hybrid": 1000}):
+        assert lib.pt_render_wavefront_static(g.h, C.byref(c), 1, 4, 0, C.byref(make_opts(**kw)),
+                                              C.c_void_p(out.data_ptr()), stream) == 1, kw
+
+
+def test_static_scratch_depth_zero_clears_image_and_signatures():
+    """max_depth 0 renders black and zeroes the per-path signatures, as pt_render does."""
+    import torch
+
+    import paper_2605_27323_gb300 as pt
+    from paper_2605_27323_gb300 import capi
+    from paper_2605_27323_gb300.tracer import make_camera, make_opts
+
+    lib = capi.load()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    sc = _mixed_box(5, 3)
+    g = pt.Scene.from_dict(sc)
+    c = make_camera(sc["camera"])
+    out = torch.full((3, 5, 3), 7.0, device="cuda")
+    sig = torch.full((5 * 3 * 2,), -1, device="cuda", dtype=torch.int32)
+    o = make_opts(sig=sig)
+    assert lib.pt_render_wavefront_static(g.h, C.byref(c), 2, 0, 0, C.byref(o), C.c_void_p(out.data_ptr()),
+                                          stream) == 0, lib.pt_last_error()
+    torch.cuda.synchronize()
+    assert float(out.abs().sum()) == 0 and int(sig.abs().sum()) == 0
