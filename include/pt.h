@@ -78,11 +78,17 @@ enum {
     PT_FLAG_HALTON = 8u,        /* pixel jitter from the Halton sequence in bases 2 and 3 over the pixel's
                                    sample index with a per-pixel Cranley-Patterson rotation (Sec. 2.3),
                                    in 24-bit fixed point; default: the path's PCG uniforms */
-    PT_FLAG_MIS = 16u           /* combine next-event estimation and BSDF-sampled hits on listed lights
+    PT_FLAG_MIS = 16u,          /* combine next-event estimation and BSDF-sampled hits on listed lights
                                    with the power heuristic (Veach 1997) instead of leaving those hits
                                    to NEE; the expectation is unchanged, the variance on glossy surfaces
                                    and large lights is lower.  Gradients follow (the weights do not
                                    depend on albedo or emission). */
+    PT_FLAG_SHORT_STACK = 32u   /* pt_render / pt_render_progressive on single-level scenes: the BVH walks
+                                   of the extend and shadow stages, the megakernel and the hybrid
+                                   continuation keep the top 8 entries of their traversal stacks in shared
+                                   memory (per-warp short stacks, 64 bytes per thread), the rest in local
+                                   memory.  Same hits and images; slower than the default local-memory
+                                   stack on GB300, whose L1 already holds it.  Ignored elsewhere. */
 };
 
 typedef struct {

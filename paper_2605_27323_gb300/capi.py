@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "PT_OK", 1: "PT_ERR_INVALID_ARG", 2: "PT_ERR_OOM", 3: "PT_ERR
                 7: "PT_ERR_UNSUPPORTED"}
 MODE = {"megakernel": 0, "wavefront": 1}
 SORT = {"none": 0, "type": 1, "material": 2}
-FLAG_PROFILE, FLAG_NO_GRAPH, FLAG_MK_STATIC, FLAG_HALTON, FLAG_MIS = 1, 2, 4, 8, 16
+FLAG_PROFILE, FLAG_NO_GRAPH, FLAG_MK_STATIC, FLAG_HALTON, FLAG_MIS, FLAG_SHORT_STACK = 1, 2, 4, 8, 16, 32
 
 # Every function that include/pt.h declares (the symbol-export test checks this list against the
 # header and the shared object).

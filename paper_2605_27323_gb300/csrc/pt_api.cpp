@@ -309,6 +309,19 @@ pt_status check_opts(const pt_render_opts& o) {
     return PT_OK;
 }
 
+// The short-stack instantiation of a single-level stage (PT_FLAG_SHORT_STACK), whose occupancy
+// includes its shared-memory stacks.
+int short_stack_kernel(const pt_scene* sc, int kernel, bool on) {
+    if (!on || sc->instanced) return kernel;
+    switch (kernel) {
+        case pt::K_EXTEND: return pt::K_EXTEND_SS;
+        case pt::K_SHADOW: return pt::K_SHADOW_SS;
+        case pt::K_MEGA_REGEN: return pt::K_MEGA_REGEN_SS;
+        case pt::K_FINISH: return pt::K_FINISH_SS;
+        default: return kernel;
+    }
+}
+
 // The two-level instantiation of a wavefront stage (its register count, hence its occupancy, differs).
 int stage_kernel(const pt_scene* sc, int kernel) {
     if (!sc->instanced) return kernel;
@@ -383,7 +396,7 @@ pt_status run_wavefront(pt_scene* sc, const pt::DevCamera& cam, const pt::Render
         sc->launches += 1;
         for (uint32_t b = 0; b < p.max_depth; ++b) {
             const int in = (int)(b & 1u);
-            pt::Launch le = launch_for(sc, pt::K_EXTEND, o.block_size, 256, st, n);
+            pt::Launch le = launch_for(sc, short_stack_kernel(sc, pt::K_EXTEND, p.short_stack), o.block_size, 256, st, n);
             PT_TRY(sc->ev_begin(ST_EXTEND, st, ev));
             PT_CUDA(pt::launch_extend(le, ds, w, in, p));
             PT_TRY(sc->ev_end(ev, st));
@@ -397,7 +410,7 @@ pt_status run_wavefront(pt_scene* sc, const pt::DevCamera& cam, const pt::Render
             PT_TRY(sc->ev_begin(ST_SHADE, st, ev));
             PT_CUDA(pt::launch_shade(ls, ds, p, w, in, b, sorted));
             PT_TRY(sc->ev_end(ev, st));
-            pt::Launch lw = launch_for(sc, pt::K_SHADOW, o.block_size, 256, st, n);
+            pt::Launch lw = launch_for(sc, short_stack_kernel(sc, pt::K_SHADOW, p.short_stack), o.block_size, 256, st, n);
             PT_TRY(sc->ev_begin(ST_SHADOW, st, ev));
             PT_CUDA(pt::launch_shadow(lw, ds, p, w, b));
             PT_TRY(sc->ev_end(ev, st));
@@ -406,7 +419,8 @@ pt_status run_wavefront(pt_scene* sc, const pt::DevCamera& cam, const pt::Render
             if (o.hybrid_threshold && b + 1 < p.max_depth) {
                 // hybrid: finish the remaining bounces in one kernel if few paths are left
                 const uint32_t thr = (uint32_t)std::min<uint64_t>(o.hybrid_threshold, 0xFFFFFFFFull);
-                pt::Launch lf = launch_for(sc, sc->instanced ? pt::K_FINISH_INST : pt::K_FINISH, 128, 128, st,
+                pt::Launch lf = launch_for(sc, sc->instanced ? pt::K_FINISH_INST : short_stack_kernel(sc, pt::K_FINISH, p.short_stack),
+                                           128, 128, st,
                                            std::min<uint64_t>(n, thr));
                 PT_TRY(sc->ev_begin(ST_MEGA, st, ev));
                 PT_CUDA(pt::launch_finish(lf, ds, p, w, (int)((b + 1) & 1u), b + 1, thr, sc->finish_claim()));
@@ -741,6 +755,7 @@ pt_status render_impl(pt_scene* sc, const pt_camera* cam, uint32_t spp, uint32_t
     p.rr_fixed = o.rr_fixed;
     p.sampler = (o.flags & PT_FLAG_HALTON) ? pt::SAMPLER_HALTON_ID : 0u;
     p.mis = (o.flags & PT_FLAG_MIS) ? 1u : 0u;
+    p.short_stack = (o.flags & PT_FLAG_SHORT_STACK) ? 1u : 0u;
     p.sample_offset = sample_offset;
     if (max_depth == 0) {
         // every sample is black: the sums are unchanged and the image is sum / count
@@ -767,7 +782,8 @@ pt_status render_impl(pt_scene* sc, const pt_camera* cam, uint32_t spp, uint32_t
             pt::Launch l = launch_for(sc, pt::K_MEGA, o.block_size, 128, st, n_paths);
             PT_CUDA(pt::launch_megakernel(l, sc->view(), dc, p, n_paths, outL, img, o.d_path_sig, sc->rays()));
         } else {
-            pt::Launch l = launch_for(sc, sc->instanced ? pt::K_MEGA_REGEN_INST : pt::K_MEGA_REGEN,
+            pt::Launch l = launch_for(sc, sc->instanced ? pt::K_MEGA_REGEN_INST
+                                                        : short_stack_kernel(sc, pt::K_MEGA_REGEN, p.short_stack),
                                       o.block_size ? std::min<uint32_t>(o.block_size, 128) : 128, 128,
                                       st, n_paths);
             PT_CUDA(pt::launch_megakernel_regen(l, sc->view(), dc, p, n_paths, outL, img, o.d_path_sig, sc->rays(),

@@ -115,13 +115,14 @@ __device__ __forceinline__ float3 mk_path(const DevScene& s, const DevCamera& c,
 // One bounce of a path held in registers (extend, shade, shadow evaluation), the loop body of the
 // regenerating megakernel and of the wavefront's continuation kernel.  Returns true when the path
 // ends; otherwise the state has moved to bounce b + 1.
-template <bool SIG, bool MIS, bool INST>
+// SK: shared-memory short-stack entries of the walks (0: local stack; see trace_closest).
+template <bool SIG, bool MIS, bool INST, int SK = 0>
 __device__ __forceinline__ bool mk_bounce(const DevScene& s, const RenderParams& p, float3 env, uint32_t key,
                                           uint32_t& b, float3& o, float3& d, float3& tp, bool& prev_delta,
                                           float& prev_pdf, float3& L, uint32_t& sg, uint32_t& n_ext,
                                           uint32_t& n_shd) {
     ++n_ext;
-    Hit h = trace_closest<INST>(s, o, d);
+    Hit h = trace_closest<INST, SK>(s, o, d);
     if (h.tri == kMiss) {
         L = add_rn(L, mul_rn(tp, env));
         if (SIG) sg ^= sig_event(b, 0, kMiss);
@@ -135,7 +136,7 @@ __device__ __forceinline__ bool mk_bounce(const DevScene& s, const RenderParams&
         uint32_t vis = 0;
         if (V.cast) {
             ++n_shd;
-            vis = trace_any<INST>(s, V.s_o, V.s_d, V.s_tmax) ? 0u : 1u;
+            vis = trace_any<INST, SK>(s, V.s_o, V.s_d, V.s_tmax) ? 0u : 1u;
             if (vis) L = add_rn(L, V.contrib);
         }
         if (SIG) sg ^= sig_event(b, 1, (V.light_j << 2) | ((uint32_t)V.cast << 1) | vis);

@@ -10,7 +10,7 @@ namespace pt {
 // its camera ray to termination, one bounce per loop iteration; a lane whose path ended claims the
 // next path id (warp-aggregated atomic on a device counter) instead of idling until the longest
 // path of its warp finishes.  The per-path arithmetic is that of mk_path, so images are identical.
-template <bool SIG, bool MIS, bool INST>
+template <bool SIG, bool MIS, bool INST, int SK = 0>
 // Register cap for 8 resident blocks of 128: occupancy outweighs the spills (measured 3.96 -> 3.11 ms
 // per 1080p frame against the uncapped 107 registers; for two-level scenes a cap of 6 blocks with
 // fewer spills measured slower too, 5.49 -> 6.07 ms).
@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(128, 8) k_megakernel_regen(DevScene s, DevCame
         }
         if (!__any_sync(0xFFFFFFFFu, active)) break;
         if (active) {
-            const bool end = mk_bounce<SIG, MIS, INST>(s, p, env, key, b, o, d, tp, prev_delta, prev_pdf, L, sg, n_ext, n_shd);
+            const bool end = mk_bounce<SIG, MIS, INST, SK>(s, p, env, key, b, o, d, tp, prev_delta, prev_pdf, L, sg, n_ext,
+                                                         n_shd);
             if (end) {
                 if (out_L) {
                     out_L[3 * i] = L.x;
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(128, 8) k_megakernel_regen(DevScene s, DevCame
 // free up) instead of running the remaining bounces as sparse wavefront stages.  The decision is
 // taken on the device; k_finish_commit then empties the queue so the remaining stage launches find
 // no work.  The arithmetic per path is the same as in the wavefront stages, so images are identical.
-template <bool SIG, bool MIS, bool INST>
+template <bool SIG, bool MIS, bool INST, int SK = 0>
 __global__ void __launch_bounds__(128, 8) k_finish(SingleSrc src, WfBuffers w, int in, uint32_t b0, uint32_t threshold,
                                                   unsigned long long* __restrict__ claim) {
     __shared__ unsigned int h_s[128];     // [b]: extension rays, [64 + b]: shadow rays of bounce b
@@ -139,7 +140,8 @@ __global__ void __launch_bounds__(128, 8) k_finish(SingleSrc src, WfBuffers w, i
             const uint32_t bb = b;
             const uint32_t shd0 = n_shd;
             atomicAdd(&h_s[bb & 63u], 1u);
-            const bool end = mk_bounce<SIG, MIS, INST>(s, p, env, key, b, o, d, tp, prev_delta, prev_pdf, L, sg, n_ext, n_shd);
+            const bool end = mk_bounce<SIG, MIS, INST, SK>(s, p, env, key, b, o, d, tp, prev_delta, prev_pdf, L, sg, n_ext,
+                                                         n_shd);
             if (n_shd != shd0) atomicAdd(&h_s[64u + (bb & 63u)], 1u);
             if (end) {
                 w.L[pid] = f4(L, 0.f);
@@ -164,16 +166,21 @@ __global__ void k_finish_commit(WfBuffers w, uint32_t threshold, unsigned long l
 cudaError_t launch_megakernel_regen(const Launch& l, const DevScene& s, const DevCamera& c, const RenderParams& p,
                                     uint64_t n_paths, float* out_L, float* img, uint32_t* sig, unsigned long long* rays,
                                     unsigned long long* next_path) {
-#define PT_REGEN(S, M, I) k_megakernel_regen<S, M, I><<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays, next_path)
+    // PT_FLAG_SHORT_STACK: the single-level variants keep their top stack entries in shared memory
+    const size_t sm = stack_smem_bytes(kShortStack, l.block);
+#define PT_REGEN(S, M, I, K) k_megakernel_regen<S, M, I, K><<<l.grid, l.block, K ? sm : 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays, next_path)
     if (s.tlas) {            // two-level scenes: one variant, MIS decided at run time
-        if (sig) PT_REGEN(true, true, true);
-        else PT_REGEN(false, true, true);
+        if (sig) PT_REGEN(true, true, true, 0);
+        else PT_REGEN(false, true, true, 0);
+    } else if (p.short_stack) {
+        if (sig) PT_REGEN(true, true, false, kShortStack);
+        else PT_REGEN(false, true, false, kShortStack);
     } else if (p.mis) {
-        if (sig) PT_REGEN(true, true, false);
-        else PT_REGEN(false, true, false);
+        if (sig) PT_REGEN(true, true, false, 0);
+        else PT_REGEN(false, true, false, 0);
     } else {
-        if (sig) PT_REGEN(true, false, false);
-        else PT_REGEN(false, false, false);
+        if (sig) PT_REGEN(true, false, false, 0);
+        else PT_REGEN(false, false, false, 0);
     }
 #undef PT_REGEN
     return cudaGetLastError();
@@ -184,16 +191,20 @@ cudaError_t launch_megakernel_regen(const Launch& l, const DevScene& s, const De
 cudaError_t launch_finish(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w, int in,
                           uint32_t b0, uint32_t threshold, unsigned long long* claim) {
     SingleSrc src{s, DevCamera{}, p};
-#define PT_FIN(S, M, I) k_finish<S, M, I><<<l.grid, l.block, 0, l.st>>>(src, w, in, b0, threshold, claim)
+    const size_t sm = stack_smem_bytes(kShortStack, l.block);
+#define PT_FIN(S, M, I, K) k_finish<S, M, I, K><<<l.grid, l.block, K ? sm : 0, l.st>>>(src, w, in, b0, threshold, claim)
     if (s.tlas) {
-        if (w.sig) PT_FIN(true, true, true);
-        else PT_FIN(false, true, true);
+        if (w.sig) PT_FIN(true, true, true, 0);
+        else PT_FIN(false, true, true, 0);
+    } else if (p.short_stack) {
+        if (w.sig) PT_FIN(true, true, false, kShortStack);
+        else PT_FIN(false, true, false, kShortStack);
     } else if (p.mis) {
-        if (w.sig) PT_FIN(true, true, false);
-        else PT_FIN(false, true, false);
+        if (w.sig) PT_FIN(true, true, false, 0);
+        else PT_FIN(false, true, false, 0);
     } else {
-        if (w.sig) PT_FIN(true, false, false);
-        else PT_FIN(false, false, false);
+        if (w.sig) PT_FIN(true, false, false, 0);
+        else PT_FIN(false, false, false, 0);
     }
 #undef PT_FIN
     cudaError_t e = cudaGetLastError();
@@ -208,9 +219,17 @@ int occupancy_mega(int which, int block) {
     cudaError_t e = cudaErrorInvalidValue;
     switch (which) {
         case K_MEGA_REGEN: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_megakernel_regen<false, false, false>, block, 0); break;
+        case K_MEGA_REGEN_SS:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_megakernel_regen<false, true, false, kShortStack>, block,
+                                                              stack_smem_bytes(kShortStack, block));
+            break;
         case K_MEGA_REGEN_INST: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_megakernel_regen<false, true, true>, block, 0); break;
         case K_FINISH_INST: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_finish<false, true, true>, block, 0); break;
         case K_FINISH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_finish<false, false, false>, block, 0); break;
+        case K_FINISH_SS:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_finish<false, true, false, kShortStack>, block,
+                                                              stack_smem_bytes(kShortStack, block));
+            break;
         default: return 0;
     }
     if (e != cudaSuccess) {

@@ -44,7 +44,8 @@ __global__ void __launch_bounds__(256) k_raygen(Src src, uint64_t base, uint32_t
 // Registers capped for 6 resident blocks of 256 single-level (extend 2.73 -> 2.68 ms per 1080p step
 // against 5 blocks) and 4 two-level (64 registers; 6 blocks measured slower, and without a bound
 // ptxas takes 78 registers, leaving 3 blocks: 2.89 -> 3.00 ms per two-level frame).
-template <class Src, bool INST>
+// SK > 0: the walks keep their top SK stack entries in dynamic shared memory (single-level only).
+template <class Src, bool INST, int SK = 0>
 __global__ void __launch_bounds__(256, INST ? 4 : 6) k_extend(Src src, WfBuffers w, int in) {
     const uint32_t n = min(w.counts[0], w.capacity);
     if (n == 0u) return;       // an emptied queue: no claims (the same for every thread)
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(256, INST ? 4 : 6) k_extend(Src src, WfBuffers
         const uint32_t j = b0 + lane_id();
         if (j >= n) continue;
         float4 o4 = qo[j], d4 = qd[j];
-        Hit h = trace_closest<INST>(src.scene(src.sid_from_ray(d4.w, base, __float_as_uint(o4.w))), xyz(o4), xyz(d4));
+        Hit h = trace_closest<INST, SK>(src.scene(src.sid_from_ray(d4.w, base, __float_as_uint(o4.w))), xyz(o4), xyz(d4));
         hit[j] = make_float2(h.t, __uint_as_float(h.tri));
         if (INST) w.hit_inst[j] = h.inst;
     }
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(256, 3) k_shade(Src src, WfBuffers w, int in, 
 
 // Shadow: any-hit test of each queued shadow ray; unoccluded contributions are added to the path.
 // At most one shadow ray per path per bounce, so the read-modify-write of L needs no atomics.
-template <class Src, bool SIG, bool INST>
+template <class Src, bool SIG, bool INST, int SK = 0>
 __global__ void __launch_bounds__(256) k_shadow(Src src, WfBuffers w, uint32_t b) {
     const uint32_t n = min(w.counts[2], w.capacity);
     if (n == 0u) return;
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(256) k_shadow(Src src, WfBuffers w, uint32_t b
         if (j >= n) continue;
         const float4 so = w.s_o[j], sd = w.s_d[j], sc = w.s_c[j];
         const uint32_t pid = __float_as_uint(sd.w);
-        const bool occ = trace_any<INST>(src.scene(src.sid_from_shadow(sc.w, base, pid)), xyz(so), xyz(sd), so.w);
+        const bool occ = trace_any<INST, SK>(src.scene(src.sid_from_shadow(sc.w, base, pid)), xyz(so), xyz(sd), so.w);
         if (!occ) {
             float3 L = add_rn(xyz(w.L[pid]), xyz(sc));
             w.L[pid] = f4(L, 0.f);
@@ -381,6 +382,8 @@ cudaError_t launch_raygen(const Launch& l, const DevCamera& c, const RenderParam
 cudaError_t launch_extend(const Launch& l, const DevScene& s, const WfBuffers& w, int in, const RenderParams& p) {
     SingleSrc src{s, DevCamera{}, p};
     if (s.tlas) k_extend<SingleSrc, true><<<l.grid, l.block, 0, l.st>>>(src, w, in);
+    else if (p.short_stack)
+        k_extend<SingleSrc, false, kShortStack><<<l.grid, l.block, stack_smem_bytes(kShortStack, l.block), l.st>>>(src, w, in);
     else k_extend<SingleSrc, false><<<l.grid, l.block, 0, l.st>>>(src, w, in);
     return cudaGetLastError();
 }
@@ -417,8 +420,14 @@ cudaError_t launch_shadow(const Launch& l, const DevScene& s, const RenderParams
         if (w.sig) k_shadow<SingleSrc, true, true><<<l.grid, l.block, 0, l.st>>>(src, w, bounce);
         else k_shadow<SingleSrc, false, true><<<l.grid, l.block, 0, l.st>>>(src, w, bounce);
     } else {
-        if (w.sig) k_shadow<SingleSrc, true, false><<<l.grid, l.block, 0, l.st>>>(src, w, bounce);
-        else k_shadow<SingleSrc, false, false><<<l.grid, l.block, 0, l.st>>>(src, w, bounce);
+        const size_t sm = stack_smem_bytes(kShortStack, l.block);
+        if (p.short_stack) {
+            if (w.sig) k_shadow<SingleSrc, true, false, kShortStack><<<l.grid, l.block, sm, l.st>>>(src, w, bounce);
+            else k_shadow<SingleSrc, false, false, kShortStack><<<l.grid, l.block, sm, l.st>>>(src, w, bounce);
+        } else {
+            if (w.sig) k_shadow<SingleSrc, true, false><<<l.grid, l.block, 0, l.st>>>(src, w, bounce);
+            else k_shadow<SingleSrc, false, false><<<l.grid, l.block, 0, l.st>>>(src, w, bounce);
+        }
     }
     return cudaGetLastError();
 }
@@ -488,10 +497,17 @@ cudaError_t launch_copy_L(const Launch& l, const float4* L4, uint64_t n, float* 
 int occupancy_wave(int which, int block) {
     int nb = 0;
     cudaError_t e = cudaErrorInvalidValue;
+    const size_t sm = stack_smem_bytes(kShortStack, block);   // the short-stack instantiations' shared stacks
     switch (which) {
         case K_EXTEND: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend<SingleSrc, false>, block, 0); break;
         case K_SHADE: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (k_shade<SingleSrc, false, false>), block, 0); break;
         case K_SHADOW: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (k_shadow<SingleSrc, false, false>), block, 0); break;
+        case K_EXTEND_SS:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend<SingleSrc, false, kShortStack>, block, sm);
+            break;
+        case K_SHADOW_SS:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (k_shadow<SingleSrc, false, false, kShortStack>), block, sm);
+            break;
         case K_EXTEND_BATCH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend<TableSrc, false>, block, 0); break;
         case K_SHADE_BATCH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (k_shade<TableSrc, false, false>), block, 0); break;
         case K_SHADOW_BATCH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (k_shadow<TableSrc, false, false>), block, 0); break;

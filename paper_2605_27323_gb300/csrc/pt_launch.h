@@ -100,6 +100,8 @@ int max_blocks_per_sm(int which, int block);   // which: 0 megakernel, 1 extend,
 enum { K_MEGA = 0, K_EXTEND = 1, K_SHADE = 2, K_SHADOW = 3, K_ADJOINT = 4, K_EXTEND_BATCH = 5, K_SHADE_BATCH = 6,
        K_SHADOW_BATCH = 7, K_SHADE_ADJ = 8, K_SHADOW_ADJ = 9,
        K_MEGA_REGEN = 10, K_FINISH = 11, K_MEGA_REGEN_INST = 12, K_FINISH_INST = 13,
-       K_EXTEND_INST = 14, K_SHADE_INST = 15, K_SHADOW_INST = 16, K_SHADE_ADJ_INST = 17, K_SHADOW_ADJ_INST = 18 };
+       K_EXTEND_INST = 14, K_SHADE_INST = 15, K_SHADOW_INST = 16, K_SHADE_ADJ_INST = 17, K_SHADOW_ADJ_INST = 18,
+       // the single-level instantiations whose walks keep a shared-memory short stack
+       K_EXTEND_SS = 19, K_SHADOW_SS = 20, K_MEGA_REGEN_SS = 21, K_FINISH_SS = 22 };
 
 }  // namespace pt

@@ -82,14 +82,92 @@ __device__ __forceinline__ void load_node(const float4* __restrict__ nodes, uint
     refs = make_uint2(__float_as_uint(n3.x), __float_as_uint(n3.y));
 }
 
+// ------------------------------------------------------------------ traversal stacks
+// The stack of deferred subtrees (far child and its entry distance) of the single-level walks.
+// LocalStack: kStack entries per thread in local memory (cached by L1).  ShortStack<K>: the top K
+// entries per thread in shared memory -- per-warp short stacks, 32 lanes side by side in each slot
+// row, so a warp's accesses of one slot hit 32 distinct banks -- and the entries below them in
+// local memory: a push onto a full shared slice first moves the slice's bottom entry to local
+// memory.  A kernel whose walks use ShortStack<K> is launched with K * 8 * blockDim.x bytes of
+// dynamic shared memory (stack_smem_bytes).  Both give the same traversal order, hence the same
+// hits.  `T` = false keeps subtree references only (any-hit walks need no distances).
+extern __shared__ uint32_t g_stack_smem[];
+
+template <bool T>
+struct LocalStack {
+    uint32_t ref[kStack];
+    float t[T ? kStack : 1];
+    int sp = 0;
+    __device__ __forceinline__ bool empty() const { return sp == 0; }
+    __device__ __forceinline__ bool push(uint32_t r, float tt) {
+        if (sp >= kStack) return false;
+        ref[sp] = r;
+        if (T) t[sp] = tt;
+        ++sp;
+        return true;
+    }
+    // pop the top entry: its distance (closest-hit walks); its reference follows with top_ref()
+    __device__ __forceinline__ float pop_t() { return t[--sp]; }
+    __device__ __forceinline__ uint32_t top_ref() const { return ref[sp]; }
+    __device__ __forceinline__ uint32_t pop_ref() { return ref[--sp]; }
+};
+
+template <int K, bool T>
+struct ShortStack {
+    static_assert(K > 0 && (K & (K - 1)) == 0, "the shared slice holds a power-of-two number of entries");
+    uint32_t lref[kStack];
+    float lt[T ? kStack : 1];
+    int sp = 0;      // entries on the stack
+    int base = 0;    // entries [0, base) in local memory, [base, sp) in shared memory
+    __device__ __forceinline__ static uint32_t slot(int i) { return (uint32_t)(i & (K - 1)) * blockDim.x + threadIdx.x; }
+    __device__ __forceinline__ static uint32_t tslot(int i) { return slot(i) + (uint32_t)K * blockDim.x; }
+    __device__ __forceinline__ bool empty() const { return sp == 0; }
+    __device__ __forceinline__ bool push(uint32_t r, float tt) {
+        if (sp >= kStack) return false;
+        if (sp < base) base = sp;              // popped into the local part: the shared slice is empty
+        if (sp - base == K) {                  // the shared slice is full: its bottom entry goes to local
+            lref[base] = g_stack_smem[slot(base)];
+            if (T) lt[base] = __uint_as_float(g_stack_smem[tslot(base)]);
+            ++base;
+        }
+        g_stack_smem[slot(sp)] = r;
+        if (T) g_stack_smem[tslot(sp)] = __float_as_uint(tt);
+        ++sp;
+        return true;
+    }
+    __device__ __forceinline__ float pop_t() {
+        --sp;
+        return sp >= base ? __uint_as_float(g_stack_smem[tslot(sp)]) : lt[sp];
+    }
+    __device__ __forceinline__ uint32_t top_ref() const { return sp >= base ? g_stack_smem[slot(sp)] : lref[sp]; }
+    __device__ __forceinline__ uint32_t pop_ref() {
+        --sp;
+        return sp >= base ? g_stack_smem[slot(sp)] : lref[sp];
+    }
+};
+
+// Shared-memory short-stack entries per thread of the single-level walks in the kernels that offer
+// it (extend, shadow, the regenerating megakernel, the hybrid continuation; PT_FLAG_SHORT_STACK).
+// 8 measured fastest of 4, 8 and 16 -- and the local stack faster than all three on GB300 (its top
+// entries stay in the 256 KB L1, while the short stack costs registers and L1 capacity).
+constexpr int kShortStack = 8;
+__host__ __device__ constexpr size_t stack_smem_bytes(int k, int block) { return (size_t)k * 8u * (size_t)block; }
+
+template <int SK, bool T>
+struct StackOf {
+    using type = ShortStack<SK, T>;
+};
+template <bool T>
+struct StackOf<0, T> {
+    using type = LocalStack<T>;
+};
+
 // Closest hit: one loop that takes a node step or a leaf step per iteration.
-__device__ __forceinline__ Hit trace_closest_plain(const DevScene& s, float3 o, float3 d) {
+template <class Stk>
+__device__ __forceinline__ Hit trace_closest_plain(const DevScene& s, float3 o, float3 d, Stk& stk) {
     float3 id = ray_rcp(d);
     float tbest = __int_as_float(0x7f800000);
     uint32_t best = kMiss, bprim = kMiss;
-    uint32_t stack_ref[kStack];
-    float stack_t[kStack];
-    int sp = 0;
     uint32_t ref = 0;          // the root is always an internal node
     uint32_t steps = 0;
     while (true) {
@@ -102,13 +180,7 @@ __device__ __forceinline__ Hit trace_closest_plain(const DevScene& s, float3 o, 
             bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tbest, t1);
             if (h0 && h1) {
                 bool first0 = t0 <= t1;
-                if (sp < kStack) {
-                    stack_ref[sp] = first0 ? r.y : r.x;
-                    stack_t[sp] = first0 ? t1 : t0;
-                    ++sp;
-                } else {
-                    atomicOr(s.status, ST_TRAVERSAL);
-                }
+                if (!stk.push(first0 ? r.y : r.x, first0 ? t1 : t0)) atomicOr(s.status, ST_TRAVERSAL);
                 ref = first0 ? r.x : r.y;
                 if (++steps < kMaxSteps) continue;
             } else if (h0 || h1) {
@@ -133,10 +205,9 @@ __device__ __forceinline__ Hit trace_closest_plain(const DevScene& s, float3 o, 
             break;
         }
         bool found = false;        // pop the next subtree whose entry is not beyond the best hit
-        while (sp > 0) {
-            --sp;
-            if (stack_t[sp] <= tbest * 1.0000005f) {
-                ref = stack_ref[sp];
+        while (!stk.empty()) {
+            if (stk.pop_t() <= tbest * 1.0000005f) {
+                ref = stk.top_ref();
                 found = true;
                 break;
             }
@@ -153,10 +224,9 @@ __device__ __forceinline__ Hit trace_closest_plain(const DevScene& s, float3 o, 
 }
 
 // Any hit with 0 < t < tmax.
-__device__ __forceinline__ bool trace_any_plain(const DevScene& s, float3 o, float3 d, float tmax) {
+template <class Stk>
+__device__ __forceinline__ bool trace_any_plain(const DevScene& s, float3 o, float3 d, float tmax, Stk& stk) {
     float3 id = ray_rcp(d);
-    uint32_t stack_ref[kStack];
-    int sp = 0;
     uint32_t ref = 0;
     uint32_t steps = 0;
     while (true) {
@@ -169,8 +239,7 @@ __device__ __forceinline__ bool trace_any_plain(const DevScene& s, float3 o, flo
             bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tmax, t1);
             if (h0 && h1) {       // nearer child first: an occluder near the origin ends the walk sooner
                 const bool first0 = t0 <= t1;
-                if (sp < kStack) stack_ref[sp++] = first0 ? r.y : r.x;
-                else atomicOr(s.status, ST_TRAVERSAL);
+                if (!stk.push(first0 ? r.y : r.x, 0.f)) atomicOr(s.status, ST_TRAVERSAL);
                 ref = first0 ? r.x : r.y;
                 if (++steps < kMaxSteps) continue;
             } else if (h0 || h1) {
@@ -189,8 +258,8 @@ __device__ __forceinline__ bool trace_any_plain(const DevScene& s, float3 o, flo
             atomicOr(s.status, ST_TRAVERSAL);
             return false;
         }
-        if (sp == 0) return false;
-        ref = stack_ref[--sp];
+        if (stk.empty()) return false;
+        ref = stk.pop_ref();
         ++steps;
     }
 }
@@ -430,16 +499,26 @@ __device__ __forceinline__ bool trace_any_inst(const DevScene& s, float3 o, floa
 // warp -- lanes that are not converged may pass different masks to the vote -- so one path in 33M
 // differed between the megakernel and the wavefront.)
 // INST selects the two-level traversal at compile time (kernels are instantiated both ways, so the
-// single-level kernels carry none of its registers).
-template <bool INST = false>
+// single-level kernels carry none of its registers).  SK > 0: the single-level walks keep their top
+// SK stack entries in shared memory (the kernel supplies stack_smem_bytes(SK, blockDim.x) of dynamic
+// shared memory); the two-level walks keep the local stack.
+template <bool INST = false, int SK = 0>
 __device__ __forceinline__ Hit trace_closest(const DevScene& s, float3 o, float3 d) {
-    if (INST) return trace_closest_inst(s, o, d);
-    return trace_closest_plain(s, o, d);
+    if constexpr (INST) {
+        return trace_closest_inst(s, o, d);
+    } else {
+        typename StackOf<SK, true>::type stk;
+        return trace_closest_plain(s, o, d, stk);
+    }
 }
-template <bool INST = false>
+template <bool INST = false, int SK = 0>
 __device__ __forceinline__ bool trace_any(const DevScene& s, float3 o, float3 d, float tmax) {
-    if (INST) return trace_any_inst(s, o, d, tmax);
-    return trace_any_plain(s, o, d, tmax);
+    if constexpr (INST) {
+        return trace_any_inst(s, o, d, tmax);
+    } else {
+        typename StackOf<SK, false>::type stk;
+        return trace_any_plain(s, o, d, tmax, stk);
+    }
 }
 
 }  // namespace pt

@@ -54,6 +54,7 @@ struct RenderParams {
     uint32_t sample_offset = 0;   // sample index of a pixel's first path (progressive accumulation)
     uint32_t sampler = 0;         // pixel jitter: 0 PCG uniforms, 1 Halton (2,3) + Cranley-Patterson
     uint32_t mis = 0;             // 1: NEE and BSDF-sampled light hits combined by the power heuristic
+    uint32_t short_stack = 0;     // 1: single-level walks keep their top stack entries in shared memory
 };
 
 enum : uint32_t { MAT_LAMBERT = 0, MAT_GGX = 1, MAT_DIELECTRIC = 2 };
