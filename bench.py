@@ -36,7 +36,14 @@ WORKLOAD = ("procedural spheres scene: 200 level-4 icospheres + 256x256-quad gro
             "8 emissive quads + constant environment, 1920x1080, 1 spp, max depth 5, roulette from bounce 3; "
             "step = wavefront frame + megakernel frame + adjoint pass")
 KERNEL_SOURCES = ["paper_2605_27323_gb300/csrc/pt_k_wave.cu", "paper_2605_27323_gb300/csrc/pt_common.cuh",
-                  "paper_2605_27323_gb300/csrc/pt_device.cuh", "paper_2605_27323_gb300/csrc/pt_trace.cuh"]
+                  "paper_2605_27323_gb300/csrc/pt_device.cuh", "paper_2605_27323_gb300/csrc/pt_trace.cuh",
+                  "paper_2605_27323_gb300/csrc/pt_k_mega.cu"]
+# Unit ceilings of the traversal kernels (per SM per cycle): 4 warp schedulers issue one warp
+# instruction each; the L1 data path moves 128 bytes.  A BVH node record is 64 bytes, a triangle
+# record 48 bytes.
+ISSUE_PER_SM_CLK = 4
+L1_BYTES_PER_SM_CLK = 128
+NODE_BYTES, TRI_BYTES = 64, 48
 # Algorithmic bytes per unit of each stage: the queue and path-state records it must read and write.
 BYTES_PER_UNIT = {
     "extend": 40,      # per extension ray: ray o|id + d|flags (32 B) read, hit record (8 B) written
@@ -54,6 +61,38 @@ def wavefront_frame_bytes(st: dict, n_paths: int, n_pixels: int) -> float:
     ext = float(sum(st["active"]))
     return (ext * (BYTES_PER_UNIT["extend"] + BYTES_PER_UNIT["shade"]) + st["shadow_rays"] * BYTES_PER_UNIT["shadow"]
             + n_paths * (BYTES_PER_UNIT["raygen"] + BYTES_PER_UNIT["reduce"]) + n_pixels * 12)
+
+
+def traversal_ceilings(units_per_launch: float, avg_launch_ms: float, nodes_per_unit: float, tris_per_unit: float,
+                       sms: int, sm_mhz: float, prof) -> dict:
+    """Fractions of the traversal kernels' real ceilings for one kernel.  traversal_fetch: the node
+    and triangle records its walks fetch (device-counted nodes and triangles per unit x 64 / 48 bytes)
+    against the L1 data path.  From the committed ncu counts of the same kernel sources (`prof`, or
+    None): issue -- its warp instructions against the issue rate of every scheduler; l2 -- its L2
+    bytes against the L2 peak; ncu_utilisation -- the L1 and issue utilisation ncu measured for the
+    frame's launches (L1 is limited by the number of divergent requests, not by bytes).  Achieved =
+    per-unit work x units per launch / the launch's live duration."""
+    t = avg_launch_ms * 1e-3
+    clk = sm_mhz * 1e6
+    l1_peak = sms * L1_BYTES_PER_SM_CLK * clk / 1e9
+    fetch_per_unit = NODE_BYTES * nodes_per_unit + TRI_BYTES * tris_per_unit
+    fetch = fetch_per_unit * units_per_launch / t / 1e9
+    out = {"traversal_fetch": {"bytes_per_unit": fetch_per_unit, "nodes_per_unit": nodes_per_unit,
+                               "tris_per_unit": tris_per_unit, "achieved": fetch, "peak": l1_peak, "unit": "GB/s",
+                               "frac": fetch / l1_peak, "peak_basis": f"{L1_BYTES_PER_SM_CLK} B/clk/SM x {sms} SMs x "
+                                                                      f"{sm_mhz:.0f} MHz"}}
+    if prof:
+        issue_peak = sms * ISSUE_PER_SM_CLK * clk / 1e9
+        inst = prof["inst_per_unit"] * units_per_launch / t / 1e9
+        out["issue"] = {"inst_per_unit": prof["inst_per_unit"], "achieved": inst, "peak": issue_peak,
+                        "unit": "G warp-inst/s", "frac": inst / issue_peak,
+                        "peak_basis": f"{ISSUE_PER_SM_CLK} warp-inst/clk/SM x {sms} SMs x {sm_mhz:.0f} MHz"}
+        l2 = prof["l2_bytes_per_unit"] * units_per_launch / t / 1e9
+        out["l2"] = {"bytes_per_unit": prof["l2_bytes_per_unit"], "achieved": l2, "peak": prof["l2_peak_gbs"],
+                     "unit": "GB/s", "frac": l2 / prof["l2_peak_gbs"], "peak_basis": "ncu lts__t_bytes peak_sustained"}
+        if "utilisation" in prof:
+            out["ncu_utilisation"] = prof["utilisation"]
+    return out
 
 
 def rank_seed(step: int, rank: int) -> int:
@@ -425,6 +464,36 @@ def run_gpu(args):
         row["wf_over_mk"] = row["megakernel_ms"] / row["wavefront_ms"]
         row["hybrid_over_mk"] = row["megakernel_ms"] / row["hybrid_ms"]
         depth_sweep[str(dmax)] = row
+    # traversal work per ray (device counters of the counting instantiations; outside the timed region):
+    # the wavefront's extend walks per extension ray, the megakernel's walks per path
+    g.render(cam, spp, depth, 0, mode="wavefront", rr_start=3, count_traversal=True)
+    cw = g.stats()
+    g.render(cam, spp, depth, 0, mode="megakernel", rr_start=3, count_traversal=True)
+    cm = g.stats()
+    trav = {"extension_ray": {"nodes": cw["nodes_closest"] / cw["extension_rays"],
+                              "tris": cw["tris_closest"] / cw["extension_rays"]},
+            "shadow_ray": {"nodes": cw["nodes_any"] / max(1, cw["shadow_rays"]),
+                           "tris": cw["tris_any"] / max(1, cw["shadow_rays"])},
+            "megakernel_counts_equal_wavefront": all(cw[k] == cm[k] for k in
+                                                     ("nodes_closest", "tris_closest", "nodes_any", "tris_any"))}
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    roofline["ceilings"] = {
+        "extend": traversal_ceilings(units["extend"] / launches["extend"], stage["extend"] / launches["extend"],
+                                     trav["extension_ray"]["nodes"], trav["extension_ray"]["tris"], sms, sm_mhz, tr),
+        "megakernel": traversal_ceilings(n_paths, stage["megakernel"] / args.steps,
+                                         (cm["nodes_closest"] + cm["nodes_any"]) / n_paths,
+                                         (cm["tris_closest"] + cm["tris_any"]) / n_paths, sms, sm_mhz,
+                                         load_traffic("megakernel"))}
+    roofline["traversal_per_ray"] = trav
+    # the batched (64 scenes) and inverse-rendering workloads, compact: the benchmark spec's >= 1.5x and
+    # <= 3x targets are measured in every default run
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        extra["inverse_rendering"] = measure_diff(3, 3)
+        torch.cuda.empty_cache()
+        extra["batch"] = measure_batch(3, 3)
+        torch.cuda.empty_cache()
     out = None
     if rank == 0:
         e2e = measure_e2e(g, cam, spp, depth, grad, args, wf_opts, mk_opts) if world == 1 else None
@@ -461,6 +530,7 @@ def run_gpu(args):
             "gpu_launches": int(gpu_launches),
             "paper_context": "paper: wavefront 1.16x over megakernel (73.6 vs 64.7 FPS, RTX 3060 Ti, Vulkan RT cores)",
         }
+        line.update(extra)
         if e2e:
             line["e2e"] = e2e
         if clk:
@@ -587,18 +657,20 @@ def run_large(args):
     print(json.dumps(line), flush=True)
 
 
-def run_diff(args):
+def measure_diff(steps: int, warmup: int, adam_steps: bool = True) -> dict:
     """Inverse rendering on the 256-material spheres scene (512x512, 64 spp, depth 6, fixed roulette
     0.9): each step renders the image with the current albedos and emissions, takes the L2 loss
     against a target rendered with hidden parameters (another seed), back-propagates through the
-    path-replay adjoint and applies an Adam update.  Reports forward and backward device times,
+    path-replay adjoint and applies an Adam update.  Returns forward and backward device times,
     their ratio, and the loss and parameter error along the way."""
     import torch
 
     import paper_2605_27323_gb300 as pt
     from paper_2605_27323_gb300 import scenes
+    t0 = time.perf_counter()
     sc = scenes.diff_scene(seed=0)
     g = pt.Scene.from_dict(sc)
+    setup_s = time.perf_counter() - t0
     cam, spp, depth = sc["camera"], sc["spp"], sc["max_depth"]
     W, H = cam["width"], cam["height"]
     kw = dict(rr_start=sc["rr_start"], rr_fixed=sc["rr_fixed"])
@@ -634,10 +706,10 @@ def run_diff(args):
 
     lam = torch.from_numpy(np.asarray(sc["mat_type"]) == scenes.LAMBERT).cuda()
     alb_err0 = float((alb.detach() - alb_t)[lam].abs().mean())
-    for w in range(args.warmup):
+    for w in range(warmup):
         step(50_000 + w)
     torch.cuda.synchronize()
-    recs = [step(s) for s in range(args.steps)]
+    recs = [step(s) for s in range(steps)]
     torch.cuda.synchronize()
     fwd = [r[0][0].elapsed_time(r[0][1]) for r in recs]
     bwd = [r[0][2].elapsed_time(r[0][3]) for r in recs]
@@ -656,20 +728,27 @@ def run_diff(args):
     e1.record(stream)
     e1.synchronize()
     bwd_mk = e0.elapsed_time(e1)
-    line = {"metric": "inverse-rendering step: backward/forward time ratio (512x512, 64 spp, depth 6, 256 materials)",
-            "value": float(np.median(bwd) / np.median(fwd)), "unit": "ratio", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": float(np.mean(tot)), "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "procedural spheres geometry, 256 shared materials, 512x512, 64 spp, depth 6, "
-                                   "roulette from bounce 3 with q = 0.9; L2 loss to a target from hidden parameters "
-                                   "(seed 7); Adam on albedo and emission",
-                       "paths": n_paths, "l2": "inputs (scene, queues, records) exceed L2; no flush"},
+    return {"workload": "procedural spheres geometry, 256 shared materials, 512x512, 64 spp, depth 6, roulette "
+                        "from bounce 3 with q = 0.9; L2 loss to a target from hidden parameters (seed 7); Adam on "
+                        "albedo and emission",
+            "paths": n_paths, "steps": steps, "warmup": warmup, "scene_setup_s": setup_s,
             "forward_ms": float(np.median(fwd)), "backward_ms": float(np.median(bwd)),
+            "bwd_over_fwd": float(np.median(bwd) / np.median(fwd)), "step_ms": float(np.mean(tot)),
             "backward_one_thread_per_path_ms": bwd_mk,
             "forward_mrays_s": rays_fwd / (np.median(fwd) * 1e-3) / 1e6,
             "loss_first": losses[0], "loss_last": losses[-1],
-            "lambert_albedo_mean_abs_error": {"start": alb_err0, "end": alb_err,
-                                              "steps": args.warmup + args.steps}}
+            "lambert_albedo_mean_abs_error": {"start": alb_err0, "end": alb_err, "steps": warmup + steps}}
+
+
+def run_diff(args):
+    d = measure_diff(args.steps, args.warmup)
+    line = {"metric": "inverse-rendering step: backward/forward time ratio (512x512, 64 spp, depth 6, 256 materials)",
+            "value": d["bwd_over_fwd"], "unit": "ratio", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": d["step_ms"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": d["workload"], "paths": d["paths"],
+                       "l2": "inputs (scene, queues, records) exceed L2; no flush"}}
+    line.update({k: v for k, v in d.items() if k not in ("workload", "paths", "steps", "warmup")})
     print(json.dumps(line), flush=True)
 
 
@@ -721,11 +800,13 @@ def run_instanced(args):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
+def measure_batch(steps: int, warmup: int) -> dict:
     """64 procedural scenes (lognormal triangle counts in [1k, 2M], resolutions from {256^2, 512^2,
     1280x720, 1920x1080}, spp from {1, 4, 16}, depth 5): one persistent batched wavefront (autotuned
     queue capacity, block size and sort granularity; CUDA-graph bounce loop) against 64 separate
-    pt_render calls producing the same images."""
+    pt_render calls producing the same images.  Also the renders of <= 1M paths (those that leave the
+    GPU underfilled on their own) as a batch of their own, and the ratio the whole mix could reach
+    if batching made those renders free (the large renders fill the GPU either way)."""
     import torch
 
     import paper_2605_27323_gb300 as pt
@@ -752,9 +833,9 @@ def run_batch(args):
     kw = dict(queue_capacity=best["queue_capacity"], block_size=best["block_size"], sort=int(best["sort"]))
     stream = torch.cuda.current_stream()
 
-    def timed(fn, steps):
+    def timed(fn, n):
         ms = []
-        for k in range(steps):
+        for k in range(n):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             fn(k)
@@ -770,13 +851,12 @@ def run_batch(args):
         for i, (g, c, s) in enumerate(zip(gs, cams, spps)):
             g.render(c, s, depth, k, out=outs[i], mode="wavefront")
 
-    for k in range(args.warmup):
+    for k in range(warmup):
         batched(100 + k)
         separate(100 + k)
-    steps = max(3, min(args.steps, 10))
+    steps = max(3, min(steps, 10))
     b_ms = timed(batched, steps)
     s_ms = timed(separate, steps)
-    # the renders small enough to leave the GPU underfilled on their own (<= 1M paths)
     small = [i for i, (c, s_) in enumerate(zip(cams, spps)) if c["width"] * c["height"] * s_ <= (1 << 20)]
     sg, sc_, ss, so = [gs[i] for i in small], [cams[i] for i in small], [spps[i] for i in small], [outs[i] for i in small]
 
@@ -786,7 +866,6 @@ def run_batch(args):
 
     small_res = None
     if small:
-        # the small renders as a batch of their own, with the autotuner's choice for that batch
         best_s = pt.autotune_batch(sg, sc_, ss, depth, 0, outs=so)
         kw_s = dict(queue_capacity=best_s["queue_capacity"], block_size=best_s["block_size"], sort=int(best_s["sort"]))
 
@@ -799,16 +878,27 @@ def run_batch(args):
         small_res = {"scenes": len(small), "paths": int(sum(c["width"] * c["height"] * s_ for c, s_ in zip(sc_, ss))),
                      "batched_ms": bs_ms, "separate_ms": ss_ms, "batched_over_separate": ss_ms / bs_ms,
                      "autotuned": kw_s}
-    line = {"metric": "batched wavefront vs 64 per-scene renders (Mrays/s)", "value": rays / (b_ms * 1e-3) / 1e6,
-            "unit": "Mrays/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": b_ms,
+    return {"workload": "64 procedural scenes, lognormal triangle counts in [1k, 2M], resolutions "
+                        "{256^2, 512^2, 1280x720, 1920x1080}, spp {1, 4, 16}, depth 5",
+            "triangles_total": int(sum(tris)), "triangles_min": int(min(tris)), "triangles_max": int(max(tris)),
+            "paths": int(paths), "rays": int(rays), "steps": steps, "autotuned": kw, "autotune_s": tune_s,
+            "scene_setup_s": setup_s, "batched_ms": b_ms, "batched_mrays_s": rays / (b_ms * 1e-3) / 1e6,
+            "separate_ms": s_ms, "separate_mrays_s": rays / (s_ms * 1e-3) / 1e6, "batched_over_separate": s_ms / b_ms,
+            "small_renders": small_res,
+            # Amdahl: the large renders fill the GPU on their own, so removing every per-launch and tail
+            # cost of the small renders (their whole separate time) bounds what batching can gain
+            "ratio_bound_if_small_renders_were_free": (s_ms / (s_ms - small_res["separate_ms"])) if small_res else None}
+
+
+def run_batch(args):
+    b = measure_batch(args.steps, args.warmup)
+    line = {"metric": "batched wavefront vs 64 per-scene renders (Mrays/s)", "value": b["batched_mrays_s"],
+            "unit": "Mrays/s", "n_gpus": 1, "steps": b["steps"], "warmup": args.warmup, "ms_per_step": b["batched_ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "64 procedural scenes, lognormal triangle counts in [1k, 2M], resolutions "
-                                   "{256^2, 512^2, 1280x720, 1920x1080}, spp {1, 4, 16}, depth 5",
-                       "triangles_total": int(sum(tris)), "triangles_min": int(min(tris)),
-                       "triangles_max": int(max(tris)), "paths": int(paths), "rays": int(rays),
-                       "autotuned": kw, "autotune_s": tune_s, "scene_setup_s": setup_s},
-            "separate_ms": s_ms, "separate_mrays_s": rays / (s_ms * 1e-3) / 1e6,
-            "batched_over_separate": s_ms / b_ms, "small_renders": small_res}
+            "config": {k: b[k] for k in ("workload", "triangles_total", "triangles_min", "triangles_max", "paths",
+                                         "rays", "autotuned", "autotune_s", "scene_setup_s")}}
+    line.update({k: b[k] for k in ("separate_ms", "separate_mrays_s", "batched_over_separate", "small_renders",
+                                   "ratio_bound_if_small_renders_were_free")})
     print(json.dumps(line), flush=True)
 
 
@@ -821,6 +911,7 @@ def main():
     ap.add_argument("--workload", default="frame", choices=["frame", "batch", "large", "diff", "instanced"])
     ap.add_argument("--sort", default="none", choices=["none", "type", "material"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and inverse-rendering summaries")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -83,12 +83,17 @@ enum {
                                    to NEE; the expectation is unchanged, the variance on glossy surfaces
                                    and large lights is lower.  Gradients follow (the weights do not
                                    depend on albedo or emission). */
-    PT_FLAG_SHORT_STACK = 32u   /* pt_render / pt_render_progressive on single-level scenes: the BVH walks
+    PT_FLAG_SHORT_STACK = 32u,  /* pt_render / pt_render_progressive on single-level scenes: the BVH walks
                                    of the extend and shadow stages, the megakernel and the hybrid
                                    continuation keep the top 8 entries of their traversal stacks in shared
                                    memory (per-warp short stacks, 64 bytes per thread), the rest in local
                                    memory.  Same hits and images; slower than the default local-memory
                                    stack on GB300, whose L1 already holds it.  Ignored elsewhere. */
+    PT_FLAG_COUNT_TRAVERSAL = 64u  /* pt_render / pt_render_progressive on single-level scenes without
+                                   d_path_sig: the extend and shadow stages and the regenerating
+                                   megakernel run instantiations that count the BVH nodes visited and the
+                                   triangles tested by every walk (pt_stats nodes_* / tris_*); the
+                                   production instantiations count nothing.  Same hits and images. */
 };
 
 typedef struct {
@@ -124,6 +129,9 @@ typedef struct {
     float ms_raygen, ms_extend, ms_sort, ms_shade, ms_shadow, ms_reduce, ms_megakernel, ms_adjoint;
     uint32_t launches_extend, launches_shadow, launches_total;
     float ms_total;
+    /* PT_FLAG_COUNT_TRAVERSAL: internal BVH nodes visited and triangles tested by the closest-hit
+       (extension) and any-hit (shadow) walks of the last call; 0 otherwise. */
+    uint64_t nodes_closest, tris_closest, nodes_any, tris_any;
 } pt_stats;
 
 typedef struct pt_scene pt_scene;

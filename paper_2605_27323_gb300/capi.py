@@ -18,7 +18,8 @@ STATUS_NAMES = {0: "PT_OK", 1: "PT_ERR_INVALID_ARG", 2: "PT_ERR_OOM", 3: "PT_ERR
                 7: "PT_ERR_UNSUPPORTED"}
 MODE = {"megakernel": 0, "wavefront": 1}
 SORT = {"none": 0, "type": 1, "material": 2}
-FLAG_PROFILE, FLAG_NO_GRAPH, FLAG_MK_STATIC, FLAG_HALTON, FLAG_MIS, FLAG_SHORT_STACK = 1, 2, 4, 8, 16, 32
+FLAG_PROFILE, FLAG_NO_GRAPH, FLAG_MK_STATIC, FLAG_HALTON, FLAG_MIS, FLAG_SHORT_STACK, FLAG_COUNT_TRAVERSAL = (
+    1, 2, 4, 8, 16, 32, 64)
 
 # Every function that include/pt.h declares (the symbol-export test checks this list against the
 # header and the shared object).
@@ -55,7 +56,8 @@ class Stats(C.Structure):
     _fields_ = [("extension_rays", u64), ("shadow_rays", u64), ("paths", u64), ("bounces", u32), ("status", u32),
                 ("active", u64 * 64), ("ms_raygen", f32), ("ms_extend", f32), ("ms_sort", f32), ("ms_shade", f32),
                 ("ms_shadow", f32), ("ms_reduce", f32), ("ms_megakernel", f32), ("ms_adjoint", f32),
-                ("launches_extend", u32), ("launches_shadow", u32), ("launches_total", u32), ("ms_total", f32)]
+                ("launches_extend", u32), ("launches_shadow", u32), ("launches_total", u32), ("ms_total", f32),
+                ("nodes_closest", u64), ("tris_closest", u64), ("nodes_any", u64), ("tris_any", u64)]
 
 
 class PtError(RuntimeError):

@@ -181,13 +181,15 @@ struct pt_scene {
         s.status = status.as<uint32_t>();
         s.tlas = instanced ? tlas.as<const float4>() : nullptr;
         s.inst = instanced ? inst.as<const float4>() : nullptr;
+        s.trav = trav();
         return s;
     }
     uint32_t* counts() const { return counters.as<uint32_t>(); }
     unsigned long long* hist() const { return reinterpret_cast<unsigned long long*>(counters.as<char>() + 256); }
     unsigned long long* rays() const { return hist() + 128; }
 
-    pt_status ensure_counters() { return counters.ensure(256 + 8 * 132); }
+    pt_status ensure_counters() { return counters.ensure(256 + 8 * 136); }
+    unsigned long long* trav() const { return hist() + 132; }   // 4 traversal counters
     unsigned long long* next_path() const { return hist() + 130; }
     unsigned long long* finish_claim() const { return hist() + 131; }
 
@@ -756,6 +758,7 @@ pt_status render_impl(pt_scene* sc, const pt_camera* cam, uint32_t spp, uint32_t
     p.sampler = (o.flags & PT_FLAG_HALTON) ? pt::SAMPLER_HALTON_ID : 0u;
     p.mis = (o.flags & PT_FLAG_MIS) ? 1u : 0u;
     p.short_stack = (o.flags & PT_FLAG_SHORT_STACK) ? 1u : 0u;
+    p.count_trav = (o.flags & PT_FLAG_COUNT_TRAVERSAL) ? 1u : 0u;
     p.sample_offset = sample_offset;
     if (max_depth == 0) {
         // every sample is black: the sums are unchanged and the image is sum / count
@@ -1444,9 +1447,9 @@ pt_status pt_get_stats(pt_scene* sc, pt_stats* out) {
     PT_TRY(set_device(sc));
     PT_CUDA(cudaStreamSynchronize(sc->last_stream));
     std::memset(out, 0, sizeof(*out));
-    std::vector<unsigned long long> h(130);
+    std::vector<unsigned long long> h(136);
     uint32_t status = 0;
-    PT_CUDA(cudaMemcpy(h.data(), sc->hist(), 130 * 8, cudaMemcpyDeviceToHost));
+    PT_CUDA(cudaMemcpy(h.data(), sc->hist(), 136 * 8, cudaMemcpyDeviceToHost));
     PT_CUDA(cudaMemcpy(&status, sc->status.p, 4, cudaMemcpyDeviceToHost));
     out->paths = sc->last_paths;
     out->launches_total = sc->launches;
@@ -1461,6 +1464,10 @@ pt_status pt_get_stats(pt_scene* sc, pt_stats* out) {
             if (h[b]) out->bounces = b + 1;
         }
     }
+    out->nodes_closest = h[132];
+    out->tris_closest = h[133];
+    out->nodes_any = h[134];
+    out->tris_any = h[135];
     out->status = status & pt::ST_TRAVERSAL ? PT_ERR_TRAVERSAL_LIMIT
                 : status & pt::ST_QUEUE     ? PT_ERR_QUEUE_OVERFLOW
                 : status & pt::ST_TIMEOUT   ? PT_ERR_TIMEOUT

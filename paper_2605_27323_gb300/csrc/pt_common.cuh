@@ -115,14 +115,15 @@ __device__ __forceinline__ float3 mk_path(const DevScene& s, const DevCamera& c,
 // One bounce of a path held in registers (extend, shade, shadow evaluation), the loop body of the
 // regenerating megakernel and of the wavefront's continuation kernel.  Returns true when the path
 // ends; otherwise the state has moved to bounce b + 1.
-// SK: shared-memory short-stack entries of the walks (0: local stack; see trace_closest).
-template <bool SIG, bool MIS, bool INST, int SK = 0>
+// SK: shared-memory short-stack entries of the walks (0: local stack; see trace_closest).  cc, ca:
+// traversal counters of the closest-hit and any-hit walks (NoCount: none).
+template <bool SIG, bool MIS, bool INST, int SK = 0, class C = NoCount>
 __device__ __forceinline__ bool mk_bounce(const DevScene& s, const RenderParams& p, float3 env, uint32_t key,
                                           uint32_t& b, float3& o, float3& d, float3& tp, bool& prev_delta,
                                           float& prev_pdf, float3& L, uint32_t& sg, uint32_t& n_ext,
-                                          uint32_t& n_shd) {
+                                          uint32_t& n_shd, C& cc, C& ca) {
     ++n_ext;
-    Hit h = trace_closest<INST, SK>(s, o, d);
+    Hit h = trace_closest<INST, SK>(s, o, d, cc);
     if (h.tri == kMiss) {
         L = add_rn(L, mul_rn(tp, env));
         if (SIG) sg ^= sig_event(b, 0, kMiss);
@@ -136,7 +137,7 @@ __device__ __forceinline__ bool mk_bounce(const DevScene& s, const RenderParams&
         uint32_t vis = 0;
         if (V.cast) {
             ++n_shd;
-            vis = trace_any<INST, SK>(s, V.s_o, V.s_d, V.s_tmax) ? 0u : 1u;
+            vis = trace_any<INST, SK>(s, V.s_o, V.s_d, V.s_tmax, ca) ? 0u : 1u;
             if (vis) L = add_rn(L, V.contrib);
         }
         if (SIG) sg ^= sig_event(b, 1, (V.light_j << 2) | ((uint32_t)V.cast << 1) | vis);
@@ -153,6 +154,27 @@ __device__ __forceinline__ bool mk_bounce(const DevScene& s, const RenderParams&
     prev_pdf = V.pdf;
     ++b;
     return false;
+}
+template <bool SIG, bool MIS, bool INST, int SK = 0>
+__device__ __forceinline__ bool mk_bounce(const DevScene& s, const RenderParams& p, float3 env, uint32_t key,
+                                          uint32_t& b, float3& o, float3& d, float3& tp, bool& prev_delta,
+                                          float& prev_pdf, float3& L, uint32_t& sg, uint32_t& n_ext,
+                                          uint32_t& n_shd) {
+    NoCount cc, ca;
+    return mk_bounce<SIG, MIS, INST, SK>(s, p, env, key, b, o, d, tp, prev_delta, prev_pdf, L, sg, n_ext, n_shd, cc,
+                                         ca);
+}
+
+// Counting instantiations: the warp's node and triangle counts added to s.trav[k], s.trav[k + 1]
+// (all 32 lanes call it, converged).
+template <class C>
+__device__ __forceinline__ void flush_count(const DevScene& s, const C& c, int k);
+template <>
+__device__ __forceinline__ void flush_count<NoCount>(const DevScene&, const NoCount&, int) {}
+template <>
+__device__ __forceinline__ void flush_count<TravCount>(const DevScene& s, const TravCount& c, int k) {
+    warp_add_u64(s.trav + k, c.nodes);
+    warp_add_u64(s.trav + k + 1, c.tris);
 }
 
 // ================================================================== wavefront stages

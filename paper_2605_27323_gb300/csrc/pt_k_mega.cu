@@ -1,6 +1,8 @@
 // pt_k_mega.cu -- the persistent megakernel with path regeneration (Sec. 2.2: one thread traces one
 // path to termination; a lane whose path ended claims the next one), and the hybrid continuation
 // kernel that finishes a wavefront's last sparse bounces with the same bounce function (Sec. 6.1).
+#include <type_traits>
+
 #include "pt_common.cuh"
 
 namespace pt {
@@ -10,7 +12,7 @@ namespace pt {
 // its camera ray to termination, one bounce per loop iteration; a lane whose path ended claims the
 // next path id (warp-aggregated atomic on a device counter) instead of idling until the longest
 // path of its warp finishes.  The per-path arithmetic is that of mk_path, so images are identical.
-template <bool SIG, bool MIS, bool INST, int SK = 0>
+template <bool SIG, bool MIS, bool INST, int SK = 0, bool CNT = false>
 // Register cap for 8 resident blocks of 128: occupancy outweighs the spills (measured 3.96 -> 3.11 ms
 // per 1080p frame against the uncapped 107 registers; for two-level scenes a cap of 6 blocks with
 // fewer spills measured slower too, 5.49 -> 6.07 ms).
@@ -20,6 +22,7 @@ __global__ void __launch_bounds__(128, 8) k_megakernel_regen(DevScene s, DevCame
                                                           unsigned long long* __restrict__ rays,
                                                           unsigned long long* __restrict__ next_path) {
     uint32_t n_ext = 0, n_shd = 0;
+    typename std::conditional<CNT, TravCount, NoCount>::type cc, ca;   // closest-hit / any-hit walks
     const float3 env = f3(s.env_r, s.env_g, s.env_b);
     bool active = false, exhausted = false;
     uint64_t i = 0;
@@ -60,7 +63,7 @@ __global__ void __launch_bounds__(128, 8) k_megakernel_regen(DevScene s, DevCame
         if (!__any_sync(0xFFFFFFFFu, active)) break;
         if (active) {
             const bool end = mk_bounce<SIG, MIS, INST, SK>(s, p, env, key, b, o, d, tp, prev_delta, prev_pdf, L, sg, n_ext,
-                                                         n_shd);
+                                                         n_shd, cc, ca);
             if (end) {
                 if (out_L) {
                     out_L[3 * i] = L.x;
@@ -78,6 +81,8 @@ __global__ void __launch_bounds__(128, 8) k_megakernel_regen(DevScene s, DevCame
     }
     warp_add_u64(rays, n_ext);
     warp_add_u64(rays + 1, n_shd);
+    flush_count(s, cc, 0);
+    flush_count(s, ca, 2);
 }
 
 
@@ -172,6 +177,9 @@ cudaError_t launch_megakernel_regen(const Launch& l, const DevScene& s, const De
     if (s.tlas) {            // two-level scenes: one variant, MIS decided at run time
         if (sig) PT_REGEN(true, true, true, 0);
         else PT_REGEN(false, true, true, 0);
+    } else if (p.count_trav && !sig) {
+        k_megakernel_regen<false, true, false, 0, true>
+            <<<l.grid, l.block, 0, l.st>>>(s, c, p, n_paths, out_L, img, sig, rays, next_path);
     } else if (p.short_stack) {
         if (sig) PT_REGEN(true, true, false, kShortStack);
         else PT_REGEN(false, true, false, kShortStack);

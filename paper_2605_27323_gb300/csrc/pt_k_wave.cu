@@ -5,6 +5,8 @@
 // step rotates the two-slot active count without a host round trip.  Grids are persistent (a
 // multiple of the SM count) and stride over the device-side count, so no host read-back or
 // indirect launch is needed.  Also the batched variants (many scenes, one wavefront).
+#include <type_traits>
+
 #include "pt_common.cuh"
 
 namespace pt {
@@ -45,7 +47,8 @@ __global__ void __launch_bounds__(256) k_raygen(Src src, uint64_t base, uint32_t
 // against 5 blocks) and 4 two-level (64 registers; 6 blocks measured slower, and without a bound
 // ptxas takes 78 registers, leaving 3 blocks: 2.89 -> 3.00 ms per two-level frame).
 // SK > 0: the walks keep their top SK stack entries in dynamic shared memory (single-level only).
-template <class Src, bool INST, int SK = 0>
+// CNT: count the walks' node visits and triangle tests into the scene's traversal counters.
+template <class Src, bool INST, int SK = 0, bool CNT = false>
 __global__ void __launch_bounds__(256, INST ? 4 : 6) k_extend(Src src, WfBuffers w, int in) {
     const uint32_t n = min(w.counts[0], w.capacity);
     if (n == 0u) return;       // an emptied queue: no claims (the same for every thread)
@@ -53,14 +56,17 @@ __global__ void __launch_bounds__(256, INST ? 4 : 6) k_extend(Src src, WfBuffers
     const float4* __restrict__ qo = w.q_o[in];
     const float4* __restrict__ qd = w.q_d[in];
     float2* __restrict__ hit = w.hit;
+    typename std::conditional<CNT, TravCount, NoCount>::type cnt;
     for (uint32_t b0 = warp_claim32(&w.counts[4]); b0 < n; b0 = warp_claim32(&w.counts[4])) {
         const uint32_t j = b0 + lane_id();
         if (j >= n) continue;
         float4 o4 = qo[j], d4 = qd[j];
-        Hit h = trace_closest<INST, SK>(src.scene(src.sid_from_ray(d4.w, base, __float_as_uint(o4.w))), xyz(o4), xyz(d4));
+        Hit h = trace_closest<INST, SK>(src.scene(src.sid_from_ray(d4.w, base, __float_as_uint(o4.w))), xyz(o4), xyz(d4),
+                                        cnt);
         hit[j] = make_float2(h.t, __uint_as_float(h.tri));
         if (INST) w.hit_inst[j] = h.inst;
     }
+    flush_count(src.scene(0), cnt, 0);
 }
 
 // Key sort before shading (counting sort): keys + block histograms, scan, scatter into `perm`.
@@ -224,17 +230,19 @@ __global__ void __launch_bounds__(256, 3) k_shade(Src src, WfBuffers w, int in, 
 
 // Shadow: any-hit test of each queued shadow ray; unoccluded contributions are added to the path.
 // At most one shadow ray per path per bounce, so the read-modify-write of L needs no atomics.
-template <class Src, bool SIG, bool INST, int SK = 0>
+template <class Src, bool SIG, bool INST, int SK = 0, bool CNT = false>
 __global__ void __launch_bounds__(256) k_shadow(Src src, WfBuffers w, uint32_t b) {
     const uint32_t n = min(w.counts[2], w.capacity);
     if (n == 0u) return;
     const uint64_t base = src.base();
+    typename std::conditional<CNT, TravCount, NoCount>::type cnt;
     for (uint32_t b0 = warp_claim32(&w.counts[5]); b0 < n; b0 = warp_claim32(&w.counts[5])) {
         const uint32_t j = b0 + lane_id();
         if (j >= n) continue;
         const float4 so = w.s_o[j], sd = w.s_d[j], sc = w.s_c[j];
         const uint32_t pid = __float_as_uint(sd.w);
-        const bool occ = trace_any<INST, SK>(src.scene(src.sid_from_shadow(sc.w, base, pid)), xyz(so), xyz(sd), so.w);
+        const bool occ =
+            trace_any<INST, SK>(src.scene(src.sid_from_shadow(sc.w, base, pid)), xyz(so), xyz(sd), so.w, cnt);
         if (!occ) {
             float3 L = add_rn(xyz(w.L[pid]), xyz(sc));
             w.L[pid] = f4(L, 0.f);
@@ -244,6 +252,7 @@ __global__ void __launch_bounds__(256) k_shadow(Src src, WfBuffers w, uint32_t b
             w.sig[base + pid] ^= sig_event(b, 1, (lj << 2) | 2u | (occ ? 0u : 1u));
         }
     }
+    flush_count(src.scene(0), cnt, 2);
 }
 
 // Prepare (Sec. 3.1): record this bounce's counts, promote the next count, reset the slots.
@@ -382,6 +391,7 @@ cudaError_t launch_raygen(const Launch& l, const DevCamera& c, const RenderParam
 cudaError_t launch_extend(const Launch& l, const DevScene& s, const WfBuffers& w, int in, const RenderParams& p) {
     SingleSrc src{s, DevCamera{}, p};
     if (s.tlas) k_extend<SingleSrc, true><<<l.grid, l.block, 0, l.st>>>(src, w, in);
+    else if (p.count_trav) k_extend<SingleSrc, false, 0, true><<<l.grid, l.block, 0, l.st>>>(src, w, in);
     else if (p.short_stack)
         k_extend<SingleSrc, false, kShortStack><<<l.grid, l.block, stack_smem_bytes(kShortStack, l.block), l.st>>>(src, w, in);
     else k_extend<SingleSrc, false><<<l.grid, l.block, 0, l.st>>>(src, w, in);
@@ -421,7 +431,9 @@ cudaError_t launch_shadow(const Launch& l, const DevScene& s, const RenderParams
         else k_shadow<SingleSrc, false, true><<<l.grid, l.block, 0, l.st>>>(src, w, bounce);
     } else {
         const size_t sm = stack_smem_bytes(kShortStack, l.block);
-        if (p.short_stack) {
+        if (p.count_trav && !w.sig) {
+            k_shadow<SingleSrc, false, false, 0, true><<<l.grid, l.block, 0, l.st>>>(src, w, bounce);
+        } else if (p.short_stack) {
             if (w.sig) k_shadow<SingleSrc, true, false, kShortStack><<<l.grid, l.block, sm, l.st>>>(src, w, bounce);
             else k_shadow<SingleSrc, false, false, kShortStack><<<l.grid, l.block, sm, l.st>>>(src, w, bounce);
         } else {

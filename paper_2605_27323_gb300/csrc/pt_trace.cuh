@@ -162,9 +162,21 @@ struct StackOf<0, T> {
     using type = LocalStack<T>;
 };
 
+// Traversal counters of one thread (the counting instantiations): internal nodes visited and
+// triangles tested.  NoCount compiles to nothing.
+struct NoCount {
+    __device__ __forceinline__ void node() {}
+    __device__ __forceinline__ void tri() {}
+};
+struct TravCount {
+    uint32_t nodes = 0, tris = 0;
+    __device__ __forceinline__ void node() { ++nodes; }
+    __device__ __forceinline__ void tri() { ++tris; }
+};
+
 // Closest hit: one loop that takes a node step or a leaf step per iteration.
-template <class Stk>
-__device__ __forceinline__ Hit trace_closest_plain(const DevScene& s, float3 o, float3 d, Stk& stk) {
+template <class Stk, class C = NoCount>
+__device__ __forceinline__ Hit trace_closest_plain(const DevScene& s, float3 o, float3 d, Stk& stk, C& cnt) {
     float3 id = ray_rcp(d);
     float tbest = __int_as_float(0x7f800000);
     uint32_t best = kMiss, bprim = kMiss;
@@ -175,6 +187,7 @@ __device__ __forceinline__ Hit trace_closest_plain(const DevScene& s, float3 o, 
             float4 n0, n1, n2;
             uint2 r;
             load_node(s.nodes, ref, n0, n1, n2, r);
+            cnt.node();
             float t0, t1;
             bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tbest, t0);
             bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tbest, t1);
@@ -188,10 +201,11 @@ __device__ __forceinline__ Hit trace_closest_plain(const DevScene& s, float3 o, 
                 if (++steps < kMaxSteps) continue;
             }
         } else {
-            uint32_t first = (ref & 0x7FFFFFFFu) >> 3, cnt = (ref & 7u) + 1u;
-            for (uint32_t k = 0; k < cnt; ++k) {
+            uint32_t first = (ref & 0x7FFFFFFFu) >> 3, n_leaf = (ref & 7u) + 1u;
+            for (uint32_t k = 0; k < n_leaf; ++k) {
                 float t;
                 uint32_t prim;
+                cnt.tri();
                 if (tri_test(s.tris, first + k, o, d, t, prim) && t > 0.0f &&
                     (t < tbest || (t == tbest && prim < bprim))) {
                     tbest = t;
@@ -224,8 +238,8 @@ __device__ __forceinline__ Hit trace_closest_plain(const DevScene& s, float3 o, 
 }
 
 // Any hit with 0 < t < tmax.
-template <class Stk>
-__device__ __forceinline__ bool trace_any_plain(const DevScene& s, float3 o, float3 d, float tmax, Stk& stk) {
+template <class Stk, class C = NoCount>
+__device__ __forceinline__ bool trace_any_plain(const DevScene& s, float3 o, float3 d, float tmax, Stk& stk, C& cnt) {
     float3 id = ray_rcp(d);
     uint32_t ref = 0;
     uint32_t steps = 0;
@@ -234,6 +248,7 @@ __device__ __forceinline__ bool trace_any_plain(const DevScene& s, float3 o, flo
             float4 n0, n1, n2;
             uint2 r;
             load_node(s.nodes, ref, n0, n1, n2, r);
+            cnt.node();
             float t0, t1;
             bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tmax, t0);
             bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tmax, t1);
@@ -247,10 +262,11 @@ __device__ __forceinline__ bool trace_any_plain(const DevScene& s, float3 o, flo
                 if (++steps < kMaxSteps) continue;
             }
         } else {
-            uint32_t first = (ref & 0x7FFFFFFFu) >> 3, cnt = (ref & 7u) + 1u;
-            for (uint32_t k = 0; k < cnt; ++k) {
+            uint32_t first = (ref & 0x7FFFFFFFu) >> 3, n_leaf = (ref & 7u) + 1u;
+            for (uint32_t k = 0; k < n_leaf; ++k) {
                 float t;
                 uint32_t prim;
+                cnt.tri();
                 if (tri_test(s.tris, first + k, o, d, t, prim) && t > 0.0f && t < tmax) return true;
             }
         }
@@ -502,23 +518,35 @@ __device__ __forceinline__ bool trace_any_inst(const DevScene& s, float3 o, floa
 // single-level kernels carry none of its registers).  SK > 0: the single-level walks keep their top
 // SK stack entries in shared memory (the kernel supplies stack_smem_bytes(SK, blockDim.x) of dynamic
 // shared memory); the two-level walks keep the local stack.
-template <bool INST = false, int SK = 0>
-__device__ __forceinline__ Hit trace_closest(const DevScene& s, float3 o, float3 d) {
+// `cnt` (TravCount) counts the single-level walks' node visits and triangle tests; the two-level
+// walks are not counted.
+template <bool INST = false, int SK = 0, class C = NoCount>
+__device__ __forceinline__ Hit trace_closest(const DevScene& s, float3 o, float3 d, C& cnt) {
     if constexpr (INST) {
         return trace_closest_inst(s, o, d);
     } else {
         typename StackOf<SK, true>::type stk;
-        return trace_closest_plain(s, o, d, stk);
+        return trace_closest_plain(s, o, d, stk, cnt);
     }
 }
 template <bool INST = false, int SK = 0>
-__device__ __forceinline__ bool trace_any(const DevScene& s, float3 o, float3 d, float tmax) {
+__device__ __forceinline__ Hit trace_closest(const DevScene& s, float3 o, float3 d) {
+    NoCount c;
+    return trace_closest<INST, SK>(s, o, d, c);
+}
+template <bool INST = false, int SK = 0, class C = NoCount>
+__device__ __forceinline__ bool trace_any(const DevScene& s, float3 o, float3 d, float tmax, C& cnt) {
     if constexpr (INST) {
         return trace_any_inst(s, o, d, tmax);
     } else {
         typename StackOf<SK, false>::type stk;
-        return trace_any_plain(s, o, d, tmax, stk);
+        return trace_any_plain(s, o, d, tmax, stk, cnt);
     }
+}
+template <bool INST = false, int SK = 0>
+__device__ __forceinline__ bool trace_any(const DevScene& s, float3 o, float3 d, float tmax) {
+    NoCount c;
+    return trace_any<INST, SK>(s, o, d, tmax, c);
 }
 
 }  // namespace pt

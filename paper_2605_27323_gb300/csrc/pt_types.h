@@ -34,6 +34,9 @@ struct DevScene {
     // is 0 (the mesh's materials) or (material + 1) | (material emitted at creation) << 31.
     const float4* __restrict__ tlas = nullptr;
     const float4* __restrict__ inst = nullptr;
+    // traversal counters of the counting instantiations (PT_FLAG_COUNT_TRAVERSAL): [0] internal
+    // nodes visited and [1] triangles tested by closest-hit walks, [2] and [3] by any-hit walks
+    unsigned long long* trav = nullptr;
 };
 
 struct DevCamera {         // U = u * tan(fov/2) * aspect, V = v * tan(fov/2), Wd = w (view -> eye)
@@ -55,6 +58,7 @@ struct RenderParams {
     uint32_t sampler = 0;         // pixel jitter: 0 PCG uniforms, 1 Halton (2,3) + Cranley-Patterson
     uint32_t mis = 0;             // 1: NEE and BSDF-sampled light hits combined by the power heuristic
     uint32_t short_stack = 0;     // 1: single-level walks keep their top stack entries in shared memory
+    uint32_t count_trav = 0;      // 1: single-level walks count visited nodes and tested triangles
 };
 
 enum : uint32_t { MAT_LAMBERT = 0, MAT_GGX = 1, MAT_DIELECTRIC = 2 };

@@ -28,3 +28,25 @@ def test_traffic_only_for_the_current_kernel_sources(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "kernel_hash", lambda: "0" * 16)
     assert bench.load_traffic("extend") is None
 
+
+
+def test_traversal_ceilings_arithmetic():
+    """The traversal kernels' ceilings: fetched node/triangle records against the L1 data path, and
+    (with committed ncu counts) warp instructions against the issue rate and L2 bytes against the L2
+    peak; achieved = work per unit x units per launch / live launch time."""
+    prof = {"inst_per_unit": 100.0, "l2_bytes_per_unit": 500.0, "l2_peak_gbs": 20000.0,
+            "utilisation": {"l1tex_throughput": 0.5}}
+    c = bench.traversal_ceilings(1e6, 0.5, nodes_per_unit=40.0, tris_per_unit=10.0, sms=152, sm_mhz=2000.0,
+                                 prof=prof)
+    clk_s = 2000e6
+    f = c["traversal_fetch"]
+    assert f["bytes_per_unit"] == 40 * 64 + 10 * 48
+    assert abs(f["achieved"] - (40 * 64 + 10 * 48) * 1e6 / 0.5e-3 / 1e9) < 1e-9
+    assert abs(f["peak"] - 152 * 128 * clk_s / 1e9) < 1e-9 and abs(f["frac"] - f["achieved"] / f["peak"]) < 1e-12
+    i = c["issue"]
+    assert abs(i["peak"] - 152 * 4 * clk_s / 1e9) < 1e-9
+    assert abs(i["achieved"] - 100.0 * 1e6 / 0.5e-3 / 1e9) < 1e-9
+    assert abs(c["l2"]["frac"] - 500.0 * 1e6 / 0.5e-3 / 1e9 / 20000.0) < 1e-12
+    assert c["ncu_utilisation"] == {"l1tex_throughput": 0.5}
+    # without committed counts only the device-counted fetch ceiling remains
+    assert set(bench.traversal_ceilings(1e6, 0.5, 40.0, 10.0, 152, 2000.0, None)) == {"traversal_fetch"}

@@ -65,3 +65,23 @@ def test_numbers_hang_together(line):
     c = line["cpu_baseline"]
     assert c["kind"] == "oracle" and c["cores"] >= 1 and c["value"] > 0 and c["unit"] == line["unit"]
     assert line["clocks"]["sm_mhz"] > 0
+
+
+def test_ceilings_and_extra_workloads(line):
+    """The traversal ceilings (device-counted node and triangle fetches against the L1 data path, for
+    extend and the megakernel), the device counters' agreement between the two integrators, and the
+    batched and inverse-rendering summaries the default run carries."""
+    r = line["roofline"]
+    t = r["traversal_per_ray"]
+    assert t["megakernel_counts_equal_wavefront"] is True
+    assert t["extension_ray"]["nodes"] >= 1 and t["shadow_ray"]["nodes"] >= 1
+    for k in ("extend", "megakernel"):
+        f = r["ceilings"][k]["traversal_fetch"]
+        assert f["unit"] == "GB/s" and 0.0 < f["frac"] < 2.0 and abs(f["frac"] - f["achieved"] / f["peak"]) < 1e-9
+    d = line["inverse_rendering"]
+    assert d["paths"] == 512 * 512 * 64 and d["forward_ms"] > 0 and d["backward_ms"] > 0
+    assert abs(d["bwd_over_fwd"] - d["backward_ms"] / d["forward_ms"]) < 1e-9 and d["bwd_over_fwd"] <= 3.0
+    b = line["batch"]
+    assert b["paths"] > 0 and b["batched_ms"] > 0 and b["separate_ms"] > 0
+    assert abs(b["batched_over_separate"] - b["separate_ms"] / b["batched_ms"]) < 1e-9
+    assert b["small_renders"]["scenes"] > 0 and b["ratio_bound_if_small_renders_were_free"] > 1.0
