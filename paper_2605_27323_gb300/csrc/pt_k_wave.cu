@@ -143,7 +143,91 @@ __global__ void __launch_bounds__(256) k_sort_scatter(WfBuffers w) {
     }
 }
 
-// Shade: emission, NEE sample (-> shadow queue), BSDF sample, roulette, compaction of survivors.
+// Shading of one queue entry (emission, NEE sample, BSDF sample, roulette): the records of its
+// continuation ray and shadow ray, if any.
+struct ShadeOut {
+    bool want_ray = false, want_shadow = false;
+    float4 ro, rd, rtp, so, sd, sc;
+};
+
+template <class Src, bool SIG, bool INST>
+__device__ __forceinline__ ShadeOut shade_entry(const Src& src, const WfBuffers& w, int in, uint32_t b, bool sorted,
+                                                uint64_t base, uint32_t j) {
+    ShadeOut r;
+    const uint32_t slot = sorted ? w.perm[j] : j;
+    const float4 o4 = w.q_o[in][slot], d4 = w.q_d[in][slot], tp4 = w.q_tp[in][slot];
+    const float2 hh = w.hit[slot];
+    const uint32_t pid = __float_as_uint(o4.w);
+    const PathLoc l = src.locate_in(base, pid, src.sid_from_ray(d4.w, base, pid));
+    const DevScene s = src.scene(l.sid);
+    const float3 tp = xyz(tp4);
+    const uint32_t tri = __float_as_uint(hh.y);
+    if (tri == kMiss) {
+        float3 L = add_rn(xyz(w.L[pid]), mul_rn(tp, f3(s.env_r, s.env_g, s.env_b)));
+        w.L[pid] = f4(L, 0.f);
+        if (SIG) w.sig[l.path] ^= sig_event(b, 0, kMiss);
+        return r;
+    }
+    const RenderParams p = src.params(l.sid);
+    const uint32_t key = path_key(p.seed, l.pixel, l.sample);
+    Vertex V = shade_vertex<true, INST>(s, p, key, b, xyz(o4), xyz(d4), tp, (__float_as_uint(d4.w) & 1u) != 0u, tp4.w,
+                                        hh.x, tri, INST ? w.hit_inst[slot] : kMiss);
+    if (V.emit_counted) {
+        float3 L = add_rn(xyz(w.L[pid]), V.emit);
+        w.L[pid] = f4(L, 0.f);
+    }
+    uint32_t sg = 0;
+    if (SIG) sg = sig_event(b, 0, V.prim);
+    if (!V.last) {
+        if (V.nee) {
+            if (V.cast) {
+                r.want_shadow = true;
+                r.so = f4(V.s_o, V.s_tmax);
+                r.sd = f4(V.s_d, __uint_as_float(pid));
+                r.sc = f4(V.contrib, __uint_as_float(src.shadow_tag(V.light_j, l.sid)));
+            } else if (SIG) {
+                sg ^= sig_event(b, 1, V.light_j << 2);
+            }
+        }
+        if (SIG) {
+            sg ^= sig_event(b, 2, V.bsdf_code);
+            if (V.rr >= 0) sg ^= sig_event(b, 3, (uint32_t)V.rr);
+        }
+        if (V.cont) {
+            r.want_ray = true;
+            r.ro = f4(V.no, __uint_as_float(pid));
+            r.rd = f4(V.nd, __uint_as_float(src.ray_tag(l.sid, V.delta ? 1u : 0u)));
+            r.rtp = f4(V.ntp, V.pdf);
+        }
+    }
+    if (SIG) w.sig[l.path] ^= sg;
+    return r;
+}
+
+template <class Src>
+__device__ __forceinline__ void put_shadow(const Src& src, const WfBuffers& w, uint32_t k, const ShadeOut& r) {
+    if (k < w.capacity) {
+        w.s_o[k] = r.so;
+        w.s_d[k] = r.sd;
+        w.s_c[k] = r.sc;
+    } else {
+        atomicOr(src.scene(0).status, ST_QUEUE);
+    }
+}
+
+template <class Src>
+__device__ __forceinline__ void put_ray(const Src& src, const WfBuffers& w, int out, uint32_t q, const ShadeOut& r) {
+    if (q < w.capacity) {
+        w.q_o[out][q] = r.ro;
+        w.q_d[out][q] = r.rd;
+        w.q_tp[out][q] = r.rtp;
+    } else {
+        atomicOr(src.scene(0).status, ST_QUEUE);
+    }
+}
+
+// Shade: emission, NEE sample (-> shadow queue), BSDF sample, roulette, compaction of survivors: each
+// warp appends its survivors with one atomic per queue (warp-aggregated).
 template <class Src, bool SIG, bool INST>
 __global__ void __launch_bounds__(256, 3) k_shade(Src src, WfBuffers w, int in, uint32_t b, bool sorted) {
     const uint32_t n = min(w.counts[0], w.capacity);
@@ -153,78 +237,12 @@ __global__ void __launch_bounds__(256, 3) k_shade(Src src, WfBuffers w, int in, 
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t wb = warp * 32u; wb < n; wb += n_warps * 32u) {
         const uint32_t j = wb + lane_id();
-        bool want_ray = false, want_shadow = false;
-        float4 ro, rd, rtp, so, sd, sc;
-        if (j < n) {
-            const uint32_t slot = sorted ? w.perm[j] : j;
-            const float4 o4 = w.q_o[in][slot], d4 = w.q_d[in][slot], tp4 = w.q_tp[in][slot];
-            const float2 hh = w.hit[slot];
-            const uint32_t pid = __float_as_uint(o4.w);
-            const PathLoc l = src.locate_in(base, pid, src.sid_from_ray(d4.w, base, pid));
-            const DevScene s = src.scene(l.sid);
-            const float3 tp = xyz(tp4);
-            const uint32_t tri = __float_as_uint(hh.y);
-            if (tri == kMiss) {
-                float3 L = add_rn(xyz(w.L[pid]), mul_rn(tp, f3(s.env_r, s.env_g, s.env_b)));
-                w.L[pid] = f4(L, 0.f);
-                if (SIG) w.sig[l.path] ^= sig_event(b, 0, kMiss);
-            } else {
-                const RenderParams p = src.params(l.sid);
-                const uint32_t key = path_key(p.seed, l.pixel, l.sample);
-                Vertex V = shade_vertex<true, INST>(s, p, key, b, xyz(o4), xyz(d4), tp,
-                                                    (__float_as_uint(d4.w) & 1u) != 0u, tp4.w, hh.x, tri,
-                                                    INST ? w.hit_inst[slot] : kMiss);
-                if (V.emit_counted) {
-                    float3 L = add_rn(xyz(w.L[pid]), V.emit);
-                    w.L[pid] = f4(L, 0.f);
-                }
-                uint32_t sg = 0;
-                if (SIG) sg = sig_event(b, 0, V.prim);
-                if (!V.last) {
-                    if (V.nee) {
-                        if (V.cast) {
-                            want_shadow = true;
-                            so = f4(V.s_o, V.s_tmax);
-                            sd = f4(V.s_d, __uint_as_float(pid));
-                            sc = f4(V.contrib, __uint_as_float(src.shadow_tag(V.light_j, l.sid)));
-                        } else if (SIG) {
-                            sg ^= sig_event(b, 1, V.light_j << 2);
-                        }
-                    }
-                    if (SIG) {
-                        sg ^= sig_event(b, 2, V.bsdf_code);
-                        if (V.rr >= 0) sg ^= sig_event(b, 3, (uint32_t)V.rr);
-                    }
-                    if (V.cont) {
-                        want_ray = true;
-                        ro = f4(V.no, __uint_as_float(pid));
-                        rd = f4(V.nd, __uint_as_float(src.ray_tag(l.sid, V.delta ? 1u : 0u)));
-                        rtp = f4(V.ntp, V.pdf);
-                    }
-                }
-                if (SIG) w.sig[l.path] ^= sg;
-            }
-        }
-        const uint32_t k = warp_append(&w.counts[2], want_shadow);
-        if (want_shadow) {
-            if (k < w.capacity) {
-                w.s_o[k] = so;
-                w.s_d[k] = sd;
-                w.s_c[k] = sc;
-            } else {
-                atomicOr(src.scene(0).status, ST_QUEUE);
-            }
-        }
-        const uint32_t q = warp_append(&w.counts[1], want_ray);
-        if (want_ray) {
-            if (q < w.capacity) {
-                w.q_o[out][q] = ro;
-                w.q_d[out][q] = rd;
-                w.q_tp[out][q] = rtp;
-            } else {
-                atomicOr(src.scene(0).status, ST_QUEUE);
-            }
-        }
+        ShadeOut r;
+        if (j < n) r = shade_entry<Src, SIG, INST>(src, w, in, b, sorted, base, j);
+        const uint32_t k = warp_append(&w.counts[2], r.want_shadow);
+        if (r.want_shadow) put_shadow(src, w, k, r);
+        const uint32_t q = warp_append(&w.counts[1], r.want_ray);
+        if (r.want_ray) put_ray(src, w, out, q, r);
     }
 }
 
