@@ -21,8 +21,8 @@ __global__ void __launch_bounds__(256, 3) k_shade_adj(SingleSrc src, WfBuffers w
         bool want_ray = false, want_shadow = false;
         float4 ro, rd, rtp, so, sd;
         if (j < n) {
-            const float4 o4 = w.q_o[in][j], d4 = w.q_d[in][j], tp4 = w.q_tp[in][j];
-            const float2 hh = w.hit[j];
+            const float4 o4 = __ldcs(&w.q_o[in][j]), d4 = __ldcs(&w.q_d[in][j]), tp4 = __ldcs(&w.q_tp[in][j]);
+            const float2 hh = __ldcs(&w.hit[j]);
             const uint32_t pid = __float_as_uint(o4.w);
             const uint32_t tri = __float_as_uint(hh.y);
             if (tri == kMiss) {
@@ -56,19 +56,19 @@ __global__ void __launch_bounds__(256, 3) k_shade_adj(SingleSrc src, WfBuffers w
                         rtp = f4(V.ntp, V.pdf);
                     }
                 }
-                float4* r = a.rec + 4 * ((size_t)b * cap + pid);
-                r[0] = make_float4(tp4.x, tp4.y, tp4.z, __uint_as_float(V.mat));
-                r[1] = r1;
-                r[2] = r2;
-                r[3] = make_float4(Le, Lj, V.emit_w, __uint_as_float(flags | (V.light_mat << 4)));
+                float4* r = a.rec + 4 * ((size_t)b * cap + pid);   // streamed: read back by the reverse pass
+                __stcs(r, make_float4(tp4.x, tp4.y, tp4.z, __uint_as_float(V.mat)));
+                __stcs(r + 1, r1);
+                __stcs(r + 2, r2);
+                __stcs(r + 3, make_float4(Le, Lj, V.emit_w, __uint_as_float(flags | (V.light_mat << 4))));
                 if (!V.cont || V.last) a.pend[pid] = b + 1u;
             }
         }
         const uint32_t k = warp_append(&w.counts[2], want_shadow);
         if (want_shadow) {
             if (k < w.capacity) {
-                w.s_o[k] = so;
-                w.s_d[k] = sd;
+                __stcs(&w.s_o[k], so);
+                __stcs(&w.s_d[k], sd);
             } else {
                 atomicOr(src.s.status, ST_QUEUE);
             }
@@ -76,9 +76,9 @@ __global__ void __launch_bounds__(256, 3) k_shade_adj(SingleSrc src, WfBuffers w
         const uint32_t q = warp_append(&w.counts[1], want_ray);
         if (want_ray) {
             if (q < w.capacity) {
-                w.q_o[out][q] = ro;
-                w.q_d[out][q] = rd;
-                w.q_tp[out][q] = rtp;
+                __stcs(&w.q_o[out][q], ro);
+                __stcs(&w.q_d[out][q], rd);
+                __stcs(&w.q_tp[out][q], rtp);
             } else {
                 atomicOr(src.s.status, ST_QUEUE);
             }
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) k_shadow_adj(SingleSrc src, WfBuffers w, 
     for (uint32_t b0 = warp_claim32(&w.counts[5]); b0 < n; b0 = warp_claim32(&w.counts[5])) {
         const uint32_t j = b0 + lane_id();
         if (j >= n) continue;
-        const float4 so = w.s_o[j], sd = w.s_d[j];
+        const float4 so = __ldcs(&w.s_o[j]), sd = __ldcs(&w.s_d[j]);
         if (!trace_any<INST>(src.s, xyz(so), xyz(sd), so.w)) {
             const uint32_t pid = __float_as_uint(sd.w);
             float* fl = reinterpret_cast<float*>(a.rec + 4 * ((size_t)b * cap + pid) + 3) + 3;

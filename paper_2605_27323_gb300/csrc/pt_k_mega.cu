@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(128, 8) k_finish(SingleSrc src, WfBuffers w, i
             if (want) {
                 const uint64_t j = first + (uint64_t)__popc(m & ((1u << lane_id()) - 1u));
                 if (j < n) {
-                    const float4 o4 = w.q_o[in][j], d4 = w.q_d[in][j], tp4 = w.q_tp[in][j];
+                    const float4 o4 = __ldcs(&w.q_o[in][j]), d4 = __ldcs(&w.q_d[in][j]), tp4 = __ldcs(&w.q_tp[in][j]);
                     pid = __float_as_uint(o4.w);
                     const PathLoc l = src.locate(p.path_begin, pid);
                     path = l.path;

