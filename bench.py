@@ -53,6 +53,7 @@ BYTES_PER_UNIT = {
     "raygen": 64,      # per path: ray + throughput (48 B) and radiance (16 B) written
     "reduce": 16,      # per path: radiance read (the image, 12 B per pixel, is added per pixel)
 }
+ADJ_SHADOW_BYTES = 40  # per shadow walk of the adjoint replay: ray (32 B) read, record flag (8 B) rw
 
 
 def wavefront_frame_bytes(st: dict, n_paths: int, n_pixels: int) -> float:
@@ -372,25 +373,36 @@ def run_gpu(args):
     units = {"extend": 2 * sum(r[3]["extension_rays"] for r in recs),
              "shadow": 2 * sum(r[3]["shadow_rays"] for r in recs),
              "shade": 2 * sum(r[3]["extension_rays"] for r in recs), "megakernel": n_paths * args.steps}
-    # The roofline is reported for k_extend, the wavefront's top kernel (forward + adjoint replay):
-    # its algorithmic bytes are the queue records it moves.  The megakernel, whose total time is
-    # similar, keeps each path's state in registers (12 B of radiance written per path), so an HBM
-    # roofline does not bound it; every kernel's share of the step is listed beside the roofline.
+    # The roofline is reported for the wavefront's extend-stage launches (forward + adjoint replay):
+    # k_extend at bounce 0 and k_trace after it, which in the default fused order also walks the
+    # shadow rays of the previous bounce.  Their algorithmic bytes are the queue records they move:
+    # 40 B per extension walk and 80 B per shadow walk; the unit is one walk.  The megakernel, whose
+    # total time is similar, keeps each path's state in registers (12 B of radiance written per path),
+    # so an HBM roofline does not bound it; every kernel's share of the step is listed beside the
+    # roofline, and the traversal ceilings of both kernels next to it.
     dom = "extend"
+    fused = launches["shadow"] == 0
+    shd_fwd = sum(r[3]["shadow_rays"] for r in recs)
+    shd_adj = sum(r[5]["shadow_rays"] for r in recs)
+    walks = units["extend"] + ((shd_fwd + shd_adj) if fused else 0)
+    # an adjoint shadow walk reads its ray (32 B) and sets the record's visibility flag (8 B)
+    alg_bytes = (BYTES_PER_UNIT["extend"] * units["extend"]
+                 + ((BYTES_PER_UNIT["shadow"] * shd_fwd + ADJ_SHADOW_BYTES * shd_adj) if fused else 0))
     kernel_ms = {k: stage[k] for k in ("extend", "shadow", "shade", "megakernel", "sort", "raygen", "reduce")}
     kernel_ms["adjoint_other"] = max(0.0, stage["adjoint_total"] - sum(r[5][k] for r in recs for k in
                                                                      ("ms_extend", "ms_shade", "ms_shadow",
                                                                       "ms_raygen", "ms_reduce")))
     shares = {k: v / max(1e-9, sum(kernel_ms.values())) for k, v in kernel_ms.items()}
     peak, peak_src = load_peaks()
-    alg_bytes = BYTES_PER_UNIT[dom] * units[dom]
     achieved = alg_bytes / (stage[dom] * 1e-3) / 1e9
     tr = load_traffic(dom)
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+    roofline = {"bound": "hbm", "kernel": "extend" + (" + previous bounce's shadow walks (fused)" if fused else ""),
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src,
-                "traffic": (float(tr["dram_bytes_per_unit"]) * units[dom] / launches[dom]) if tr else None,
+                "traffic": (float(tr["dram_bytes_per_unit"]) * walks / launches[dom]) if tr else None,
                 # what does bound it: ncu's unit utilisations for the same kernel sources
                 "ncu_counters": tr.get("counters") if tr else None,
+                "walks_per_launch": walks / launches[dom],
                 "algorithmic_bytes_per_launch": alg_bytes / launches[dom],
                 "avg_launch_ms": stage[dom] / launches[dom],
                 "share_of_step_kernel_time": {k: round(v, 4) for k, v in shares.items()}}
@@ -478,9 +490,11 @@ def run_gpu(args):
                                                      ("nodes_closest", "tris_closest", "nodes_any", "tris_any"))}
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    walk_nodes = (cw["nodes_closest"] + (cw["nodes_any"] if fused else 0)) / (cw["extension_rays"] + (cw["shadow_rays"] if fused else 0))
+    walk_tris = (cw["tris_closest"] + (cw["tris_any"] if fused else 0)) / (cw["extension_rays"] + (cw["shadow_rays"] if fused else 0))
     roofline["ceilings"] = {
-        "extend": traversal_ceilings(units["extend"] / launches["extend"], stage["extend"] / launches["extend"],
-                                     trav["extension_ray"]["nodes"], trav["extension_ray"]["tris"], sms, sm_mhz, tr),
+        "extend": traversal_ceilings(walks / launches["extend"], stage["extend"] / launches["extend"],
+                                     walk_nodes, walk_tris, sms, sm_mhz, tr),
         "megakernel": traversal_ceilings(n_paths, stage["megakernel"] / args.steps,
                                          (cm["nodes_closest"] + cm["nodes_any"]) / n_paths,
                                          (cm["tris_closest"] + cm["tris_any"]) / n_paths, sms, sm_mhz,

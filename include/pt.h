@@ -89,6 +89,13 @@ enum {
                                    memory (per-warp short stacks, 64 bytes per thread), the rest in local
                                    memory.  Same hits and images; slower than the default local-memory
                                    stack on GB300, whose L1 already holds it.  Ignored elsewhere. */
+    PT_FLAG_SEPARATE_SHADOW = 128u, /* wavefront (pt_render, pt_render_progressive, pt_render_backward's
+                                   wavefront replay, pt_render_batch): run the shadow stage as its own
+                                   launch after shading, as the paper's stage list orders it, instead of
+                                   walking each bounce's shadow rays in the next bounce's extend launch.
+                                   Same image and gradients; the default fused order has one stage boundary
+                                   fewer per bounce.  The hybrid continuation, PT_FLAG_SHORT_STACK and
+                                   pt_render_wavefront_static always use the separate order. */
     PT_FLAG_COUNT_TRAVERSAL = 64u  /* pt_render / pt_render_progressive on single-level scenes without
                                    d_path_sig: the extend and shadow stages and the regenerating
                                    megakernel run instantiations that count the BVH nodes visited and the

@@ -20,6 +20,7 @@ MODE = {"megakernel": 0, "wavefront": 1}
 SORT = {"none": 0, "type": 1, "material": 2}
 FLAG_PROFILE, FLAG_NO_GRAPH, FLAG_MK_STATIC, FLAG_HALTON, FLAG_MIS, FLAG_SHORT_STACK, FLAG_COUNT_TRAVERSAL = (
     1, 2, 4, 8, 16, 32, 64)
+FLAG_SEPARATE_SHADOW = 128
 
 # Every function that include/pt.h declares (the symbol-export test checks this list against the
 # header and the shared object).

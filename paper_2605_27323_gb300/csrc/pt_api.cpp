@@ -396,8 +396,35 @@ pt_status run_wavefront(pt_scene* sc, const pt::DevCamera& cam, const pt::Render
         PT_CUDA(pt::launch_raygen(simple_launch(sc, st, n), cam, p, n, w));
         PT_TRY(sc->ev_end(ev, st));
         sc->launches += 1;
+        // fused: each bounce's extend launch also walks the shadow rays the previous shading cast
+        // (no stage boundary between them); the hybrid and the short-stack variant keep the stages apart
+        const bool fused = !(o.flags & PT_FLAG_SEPARATE_SHADOW) && !o.hybrid_threshold && !p.short_stack;
         for (uint32_t b = 0; b < p.max_depth; ++b) {
             const int in = (int)(b & 1u);
+            if (fused) {
+                PT_TRY(sc->ev_begin(ST_EXTEND, st, ev));
+                if (b == 0) {     // no shadow rays are pending before the first shading
+                    PT_CUDA(pt::launch_extend(launch_for(sc, pt::K_EXTEND, o.block_size, 256, st, n), ds, w, in, p));
+                } else {
+                    pt::Launch lt = launch_for(sc, sc->instanced ? pt::K_TRACE_INST : pt::K_TRACE, o.block_size, 256, st,
+                                               2ull * n);
+                    PT_CUDA(pt::launch_trace(lt, ds, p, w, in, b));
+                }
+                PT_TRY(sc->ev_end(ev, st));
+                bool sorted_f = n_keys > 0;
+                if (sorted_f) {
+                    PT_TRY(sc->ev_begin(ST_SORT, st, ev));
+                    PT_CUDA(pt::launch_sort(simple_launch(sc, st, n), ds, w, in, sort_mode, n_keys, p));
+                    PT_TRY(sc->ev_end(ev, st));
+                }
+                pt::Launch ls = launch_for(sc, pt::K_SHADE, o.block_size, 256, st, n);
+                PT_TRY(sc->ev_begin(ST_SHADE, st, ev));
+                PT_CUDA(pt::launch_shade(ls, ds, p, w, in, b, sorted_f));
+                PT_TRY(sc->ev_end(ev, st));
+                PT_CUDA(pt::launch_prepare_fused(st, w, b));
+                sc->launches += 3 + (sorted_f ? 3 : 0);
+                continue;
+            }
             pt::Launch le = launch_for(sc, short_stack_kernel(sc, pt::K_EXTEND, p.short_stack), o.block_size, 256, st, n);
             PT_TRY(sc->ev_begin(ST_EXTEND, st, ev));
             PT_CUDA(pt::launch_extend(le, ds, w, in, p));
@@ -657,17 +684,18 @@ pt_status batch_render(pt_scene* const* scenes, const pt_camera* cams, const uin
         l.st = s_;
         return l;
     };
+    const bool fused = !(o.flags & PT_FLAG_SEPARATE_SHADOW);
     auto bounce_loop = [&](cudaStream_t s_) -> pt_status {
         for (uint32_t b = 0; b < max_depth; ++b)
             PT_CUDA(pt::launch_bounce_batch(persistent(pt::K_EXTEND_BATCH, s_), persistent(pt::K_SHADE_BATCH, s_),
-                                            persistent(pt::K_SHADOW_BATCH, s_), plain(cap, s_), t, p, w, b, sort_mode,
-                                            n_keys));
+                                            persistent(fused ? pt::K_TRACE_BATCH : pt::K_SHADOW_BATCH, s_),
+                                            plain(cap, s_), t, p, w, b, sort_mode, n_keys, fused));
         return PT_OK;
     };
     const bool use_graph = !(o.flags & PT_FLAG_NO_GRAPH);
     if (use_graph) {
         // the captured loop depends only on these; tables and counters are read from device memory
-        std::vector<uint64_t> key = {cap, max_depth, n_keys, sort_mode, block, o.rr_start,
+        std::vector<uint64_t> key = {cap, max_depth, n_keys, sort_mode, block, o.rr_start, (uint64_t)fused,
                                      (uint64_t)__builtin_bit_cast(uint32_t, o.rr_fixed),
                                      (uint64_t)(uintptr_t)ctx->tables.p, (uint64_t)(uintptr_t)ctx->wf.p, n};
         if (!ctx->graph || ctx->graph_key != key) {
@@ -1365,14 +1393,26 @@ pt_status pt_render_backward(pt_scene* sc, const pt_camera* cam, uint32_t spp, u
             PT_TRY(sc->ev_begin(ST_RAYGEN, st, e2));
             PT_CUDA(pt::launch_raygen(simple_launch(sc, st, n), dc, pw, n, w));
             PT_TRY(sc->ev_end(e2, st));
+            // fused as the forward wavefront: each bounce's extend launch also walks the shadow rays of
+            // the previous bounce (marking their records), unless the separate order is asked for
+            const bool fused = !(o.flags & PT_FLAG_SEPARATE_SHADOW);
             for (uint32_t b = 0; b < max_depth; ++b) {
                 const int in = (int)(b & 1u);
                 PT_TRY(sc->ev_begin(ST_EXTEND, st, e2));
-                PT_CUDA(pt::launch_extend(launch_for(sc, pt::K_EXTEND, o.block_size, 256, st, n), ds, w, in, pw));
+                if (fused && b > 0)
+                    PT_CUDA(pt::launch_trace_adj(launch_for(sc, sc->instanced ? pt::K_TRACE_INST : pt::K_TRACE,
+                                                            o.block_size, 256, st, 2ull * n),
+                                                 ds, pw, w, ab, in, b));
+                else
+                    PT_CUDA(pt::launch_extend(launch_for(sc, pt::K_EXTEND, o.block_size, 256, st, n), ds, w, in, pw));
                 PT_TRY(sc->ev_end(e2, st));
                 PT_TRY(sc->ev_begin(ST_SHADE, st, e2));
                 PT_CUDA(pt::launch_shade_adj(launch_for(sc, pt::K_SHADE_ADJ, o.block_size, 256, st, n), ds, pw, w, ab, in, b));
                 PT_TRY(sc->ev_end(e2, st));
+                if (fused) {
+                    PT_CUDA(pt::launch_prepare_fused(st, w, b));
+                    continue;
+                }
                 PT_TRY(sc->ev_begin(ST_SHADOW, st, e2));
                 PT_CUDA(pt::launch_shadow_adj(launch_for(sc, pt::K_SHADOW_ADJ, o.block_size, 256, st, n), ds, pw, w, ab, b));
                 PT_TRY(sc->ev_end(e2, st));
@@ -1382,7 +1422,7 @@ pt_status pt_render_backward(pt_scene* sc, const pt_camera* cam, uint32_t spp, u
             PT_CUDA(pt::launch_adjoint_reverse(simple_launch(sc, st, n), ds, pw, w, ab, n, grad, d_grad_albedo,
                                                d_grad_emission));
             PT_TRY(sc->ev_end(e2, st));
-            sc->launches += 2 + 4 * max_depth;
+            sc->launches += 2 + (fused ? 3 : 4) * max_depth;
         }
     }
     PT_TRY(sc->ev_end(ev, st));

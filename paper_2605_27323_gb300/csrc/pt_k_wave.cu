@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(256) k_raygen(Src src, uint64_t base, uint32_t
         w.counts[2] = 0u;
         w.counts[4] = 0u;
         w.counts[5] = 0u;
+        w.counts[6] = 0u;      // no shadow rays pending for the first trace launch
         if (wave_base_dev) *wave_base_dev = base;
     }
 }
@@ -278,6 +279,77 @@ __global__ void __launch_bounds__(256) k_shadow(Src src, WfBuffers w, uint32_t b
     flush_count(src.scene(0), cnt, 2);
 }
 
+// Trace (the extend stage of bounce b fused with the shadow stage of bounce b - 1): one launch walks
+// the BVH for the continuation rays of bounce b (closest hit, queue `in`, counts[0] entries) and for
+// the shadow rays that shading cast at bounce b - 1 (any hit, the shadow queue, counts[6] entries).
+// The two sets are independent -- a shadow ray only adds its contribution to its path's radiance, and
+// only the next shading reads that radiance -- so each path still adds its terms in the order
+// emission(b - 1), NEE(b - 1), emission(b), as in the megakernel.  Warps claim 32 continuation rays
+// at a time until none is left and then 32 shadow rays at a time (two loops, so each walk keeps the
+// registers it has in its own stage); a launch therefore ends when both sets are done, and the shadow
+// walks fill the extension walks' tail instead of running after a stage boundary.
+// ADJ: the adjoint replay's variant, whose shadow walks mark the vertex record's NEE sample visible
+// (flag 2 of record 3 of bounce b - 1) instead of adding a contribution.
+template <class Src, bool SIG, bool INST, bool CNT = false, bool ADJ = false>
+__global__ void __launch_bounds__(256, INST ? 4 : 6) k_trace(Src src, WfBuffers w, AdjBuffers a, int in, uint32_t b) {
+    const uint32_t n_ext = min(w.counts[0], w.capacity), n_shd = min(w.counts[6], w.capacity);
+    if (n_ext + n_shd == 0u) return;       // the same for every thread
+    const uint64_t base = src.base();
+    typename std::conditional<CNT, TravCount, NoCount>::type cc, ca;
+    {
+        const float4* __restrict__ qo = w.q_o[in];
+        const float4* __restrict__ qd = w.q_d[in];
+        for (uint32_t b0 = warp_claim32(&w.counts[4]); b0 < n_ext; b0 = warp_claim32(&w.counts[4])) {
+            const uint32_t j = b0 + lane_id();
+            if (j >= n_ext) continue;
+            const float4 o4 = __ldcs(&qo[j]), d4 = __ldcs(&qd[j]);
+            Hit h = trace_closest<INST, 0>(src.scene(src.sid_from_ray(d4.w, base, __float_as_uint(o4.w))), xyz(o4),
+                                           xyz(d4), cc);
+            w.hit[j] = make_float2(h.t, __uint_as_float(h.tri));
+            if (INST) w.hit_inst[j] = h.inst;
+        }
+    }
+    for (uint32_t b0 = warp_claim32(&w.counts[5]); b0 < n_shd; b0 = warp_claim32(&w.counts[5])) {
+        const uint32_t k = b0 + lane_id();
+        if (k >= n_shd) continue;
+        const float4 so = __ldcs(&w.s_o[k]), sd = __ldcs(&w.s_d[k]);
+        const uint32_t pid = __float_as_uint(sd.w);
+        if constexpr (ADJ) {
+            if (!trace_any<INST, 0>(src.scene(0), xyz(so), xyz(sd), so.w, ca)) {
+                float* fl = reinterpret_cast<float*>(a.rec + 4 * ((size_t)(b - 1u) * w.capacity + pid) + 3) + 3;
+                *fl = __uint_as_float(__float_as_uint(*fl) | 2u);
+            }
+        } else {
+            const float4 sc = __ldcs(&w.s_c[k]);
+            const bool occ =
+                trace_any<INST, 0>(src.scene(src.sid_from_shadow(sc.w, base, pid)), xyz(so), xyz(sd), so.w, ca);
+            if (!occ) {
+                float3 L = add_rn(xyz(w.L[pid]), xyz(sc));
+                w.L[pid] = f4(L, 0.f);
+            }
+            if (SIG) {
+                const uint32_t lj = __float_as_uint(sc.w);
+                w.sig[base + pid] ^= sig_event(b - 1u, 1, (lj << 2) | 2u | (occ ? 0u : 1u));
+            }
+        }
+    }
+    flush_count(src.scene(0), cc, 0);
+    flush_count(src.scene(0), ca, 2);
+}
+
+// Prepare after shading in the fused pipeline: record this bounce's counts, promote the next count,
+// and hand the shadow rays shading just cast to the next trace launch (counts[2] -> counts[6]).
+__global__ void k_prepare_fused(WfBuffers w, uint32_t b) {
+    w.hist[b] += w.counts[0];
+    w.hist[64 + b] += w.counts[2];
+    w.counts[0] = w.counts[1];
+    w.counts[1] = 0u;
+    w.counts[6] = w.counts[2];
+    w.counts[2] = 0u;
+    w.counts[4] = 0u;
+    w.counts[5] = 0u;
+}
+
 // Prepare (Sec. 3.1): record this bounce's counts, promote the next count, reset the slots.
 __global__ void k_prepare(WfBuffers w, uint32_t b) {
     w.hist[b] += w.counts[0];
@@ -476,10 +548,13 @@ cudaError_t launch_raygen_batch(const Launch& l, const BatchTables& t, const Ren
 
 cudaError_t launch_bounce_batch(const Launch& le, const Launch& ls, const Launch& lw, const Launch& lk,
                                 const BatchTables& t, const RenderParams& p, const WfBuffers& w, uint32_t b,
-                                uint32_t sort_mode, uint32_t n_keys) {
+                                uint32_t sort_mode, uint32_t n_keys, bool fused) {
     TableSrc src{t, p};
     const int in = (int)(b & 1u);
-    k_extend<TableSrc, false><<<le.grid, le.block, 0, le.st>>>(src, w, in);
+    if (fused && b > 0)   // lw: the fused launch (this bounce's extension and the last bounce's shadow walks)
+        k_trace<TableSrc, false, false><<<lw.grid, lw.block, 0, lw.st>>>(src, w, AdjBuffers{}, in, b);
+    else
+        k_extend<TableSrc, false><<<le.grid, le.block, 0, le.st>>>(src, w, in);
     if (n_keys) {
         cudaError_t e = cudaMemsetAsync(w.bucket, 0, sizeof(uint32_t) * n_keys, lk.st);
         if (e != cudaSuccess) return e;
@@ -488,8 +563,12 @@ cudaError_t launch_bounce_batch(const Launch& le, const Launch& ls, const Launch
         k_sort_scatter<<<lk.grid, lk.block, 0, lk.st>>>(w);
     }
     k_shade<TableSrc, false, false><<<ls.grid, ls.block, 0, ls.st>>>(src, w, in, b, n_keys > 0);
-    k_shadow<TableSrc, false, false><<<lw.grid, lw.block, 0, lw.st>>>(src, w, b);
-    k_prepare<<<1, 1, 0, le.st>>>(w, b);
+    if (fused) {
+        k_prepare_fused<<<1, 1, 0, le.st>>>(w, b);
+    } else {
+        k_shadow<TableSrc, false, false><<<lw.grid, lw.block, 0, lw.st>>>(src, w, b);
+        k_prepare<<<1, 1, 0, le.st>>>(w, b);
+    }
     return cudaGetLastError();
 }
 
@@ -503,6 +582,35 @@ cudaError_t launch_reduce_batch(const Launch& l, const BatchTables& t, const flo
 cudaError_t launch_scale_batch(const Launch& l, const BatchTables& t, const unsigned long long* px_off, uint64_t total) {
     if (total == 0) return cudaSuccess;
     k_scale_batch<<<l.grid, l.block, 0, l.st>>>(t, px_off, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w, int in,
+                         uint32_t bounce) {
+    SingleSrc src{s, DevCamera{}, p};
+    const AdjBuffers a{};
+    if (s.tlas) {
+        if (w.sig) k_trace<SingleSrc, true, true><<<l.grid, l.block, 0, l.st>>>(src, w, a, in, bounce);
+        else k_trace<SingleSrc, false, true><<<l.grid, l.block, 0, l.st>>>(src, w, a, in, bounce);
+    } else if (p.count_trav && !w.sig) {
+        k_trace<SingleSrc, false, false, true><<<l.grid, l.block, 0, l.st>>>(src, w, a, in, bounce);
+    } else {
+        if (w.sig) k_trace<SingleSrc, true, false><<<l.grid, l.block, 0, l.st>>>(src, w, a, in, bounce);
+        else k_trace<SingleSrc, false, false><<<l.grid, l.block, 0, l.st>>>(src, w, a, in, bounce);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_adj(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w,
+                             const AdjBuffers& a, int in, uint32_t bounce) {
+    SingleSrc src{s, DevCamera{}, p};
+    if (s.tlas) k_trace<SingleSrc, false, true, false, true><<<l.grid, l.block, 0, l.st>>>(src, w, a, in, bounce);
+    else k_trace<SingleSrc, false, false, false, true><<<l.grid, l.block, 0, l.st>>>(src, w, a, in, bounce);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prepare_fused(cudaStream_t st, const WfBuffers& w, uint32_t bounce) {
+    k_prepare_fused<<<1, 1, 0, st>>>(w, bounce);
     return cudaGetLastError();
 }
 
@@ -543,6 +651,9 @@ int occupancy_wave(int which, int block) {
         case K_SHADOW_SS:
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (k_shadow<SingleSrc, false, false, kShortStack>), block, sm);
             break;
+        case K_TRACE: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (k_trace<SingleSrc, false, false>), block, 0); break;
+        case K_TRACE_INST: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (k_trace<SingleSrc, false, true>), block, 0); break;
+        case K_TRACE_BATCH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (k_trace<TableSrc, false, false>), block, 0); break;
         case K_EXTEND_BATCH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_extend<TableSrc, false>, block, 0); break;
         case K_SHADE_BATCH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (k_shade<TableSrc, false, false>), block, 0); break;
         case K_SHADOW_BATCH: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (k_shadow<TableSrc, false, false>), block, 0); break;

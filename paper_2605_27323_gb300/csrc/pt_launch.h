@@ -40,15 +40,25 @@ cudaError_t launch_shade(const Launch& l, const DevScene& s, const RenderParams&
 cudaError_t launch_shadow(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w,
                           uint32_t bounce);
 cudaError_t launch_prepare(cudaStream_t st, const WfBuffers& w, uint32_t bounce);
+// The fused pipeline: the extend stage of bounce b and the shadow stage of bounce b - 1 in one launch
+// (the shadow rays pending in counts[6]), and the prepare step that hands shading's new shadow rays on.
+cudaError_t launch_trace(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w, int in,
+                         uint32_t bounce);
+cudaError_t launch_prepare_fused(cudaStream_t st, const WfBuffers& w, uint32_t bounce);
+// The adjoint replay's fused launch: its shadow walks mark the records of bounce - 1.
+cudaError_t launch_trace_adj(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w,
+                             const AdjBuffers& a, int in, uint32_t bounce);
 
 // Batched wavefront over device scene tables (TableSrc): raygen of one wave (publishes the wave
 // base), one bounce of extend/(sort)/shade/shadow/prepare (capturable: no host-varying arguments),
 // accumulation of a wave into the scenes' running sums, and the final sums -> means.
 cudaError_t launch_raygen_batch(const Launch& l, const BatchTables& t, const RenderParams& p, uint64_t base, uint32_t n,
                                 const WfBuffers& w);
+// fused: the shadow walks of bounce b - 1 run in bounce b's extend launch (lw configures that launch);
+// otherwise lw configures a shadow stage after shading.
 cudaError_t launch_bounce_batch(const Launch& le, const Launch& ls, const Launch& lw, const Launch& lk,
                                 const BatchTables& t, const RenderParams& p, const WfBuffers& w, uint32_t b,
-                                uint32_t sort_mode, uint32_t n_keys);
+                                uint32_t sort_mode, uint32_t n_keys, bool fused);
 cudaError_t launch_reduce_batch(const Launch& l, const BatchTables& t, const float4* L, const BatchSegment* seg,
                                 uint32_t n_seg, uint64_t w0, uint64_t w1, uint64_t n_flat);
 cudaError_t launch_scale_batch(const Launch& l, const BatchTables& t, const unsigned long long* px_off, uint64_t total);
@@ -102,6 +112,7 @@ enum { K_MEGA = 0, K_EXTEND = 1, K_SHADE = 2, K_SHADOW = 3, K_ADJOINT = 4, K_EXT
        K_MEGA_REGEN = 10, K_FINISH = 11, K_MEGA_REGEN_INST = 12, K_FINISH_INST = 13,
        K_EXTEND_INST = 14, K_SHADE_INST = 15, K_SHADOW_INST = 16, K_SHADE_ADJ_INST = 17, K_SHADOW_ADJ_INST = 18,
        // the single-level instantiations whose walks keep a shared-memory short stack
-       K_EXTEND_SS = 19, K_SHADOW_SS = 20, K_MEGA_REGEN_SS = 21, K_FINISH_SS = 22 };
+       K_EXTEND_SS = 19, K_SHADOW_SS = 20, K_MEGA_REGEN_SS = 21, K_FINISH_SS = 22,
+       K_TRACE = 23, K_TRACE_INST = 24, K_TRACE_BATCH = 25 };
 
 }  // namespace pt

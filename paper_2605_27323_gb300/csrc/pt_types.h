@@ -84,7 +84,8 @@ struct WfBuffers {
     float4* s_d;             // shadow ray: d.xyz | path index bits
     float4* s_c;             // shadow ray: contribution.rgb | light index bits
     float4* L;               // per path (wave-local): radiance.rgb | -
-    uint32_t* counts;        // [0] active, [1] next, [2] shadow, [3] sort key count
+    uint32_t* counts;        // [0] active, [1] next, [2] shadow, [3] sort key count, [4] [5] work claims,
+                             // [6] shadow rays pending for the fused trace launch
     unsigned long long* hist;  // [b] extension rays of bounce b, [64 + b] shadow rays of bounce b
     uint32_t* sig;           // per path (global id) branch signature, or null
     uint32_t capacity;

@@ -39,7 +39,7 @@ def make_camera(cam: dict) -> capi.Camera:
 
 def make_opts(mode="wavefront", rr_start=3, rr_fixed=0.0, sort="none", block_size=0, queue_capacity=0,
               profile=False, sig=None, graph=True, mk_static=False, hybrid=0, sampler="pcg",
-              mis=False, short_stack=False, count_traversal=False) -> capi.RenderOpts:
+              mis=False, short_stack=False, count_traversal=False, separate_shadow=False) -> capi.RenderOpts:
     o = capi.RenderOpts()
     o.mode = capi.MODE[mode] if isinstance(mode, str) else int(mode)
     o.rr_start = int(rr_start)
@@ -49,7 +49,8 @@ def make_opts(mode="wavefront", rr_start=3, rr_fixed=0.0, sort="none", block_siz
     o.flags = ((capi.FLAG_PROFILE if profile else 0) | (0 if graph else capi.FLAG_NO_GRAPH)
                | (capi.FLAG_MK_STATIC if mk_static else 0) | (capi.FLAG_HALTON if sampler == "halton" else 0)
                | (capi.FLAG_MIS if mis else 0) | (capi.FLAG_SHORT_STACK if short_stack else 0)
-               | (capi.FLAG_COUNT_TRAVERSAL if count_traversal else 0))
+               | (capi.FLAG_COUNT_TRAVERSAL if count_traversal else 0)
+               | (capi.FLAG_SEPARATE_SHADOW if separate_shadow else 0))
     if sampler not in ("pcg", "halton"):
         raise ValueError("sampler must be 'pcg' or 'halton'")
     o.queue_capacity = int(queue_capacity)

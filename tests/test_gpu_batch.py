@@ -44,7 +44,7 @@ def _standalone(batch, depth, seed, **kw):
 
 
 @pytest.mark.parametrize("kw", [{}, {"graph": False}, {"queue_capacity": 997}, {"queue_capacity": 5000, "sort": "material"},
-                                {"sort": "type", "block_size": 128}])
+                                {"sort": "type", "block_size": 128}, {"separate_shadow": True, "queue_capacity": 2000}])
 def test_batch_equals_standalone_renders(torch, batch, kw):
     import paper_2605_27323_gb300 as pt
     depth, seed = 6, 11

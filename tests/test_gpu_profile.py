@@ -1,10 +1,12 @@
 """The per-stage timings the library records when asked (`profile=True`): stages are the intervals
 between events on the launch stream, consecutive stages sharing the event between them.
 
-* a wavefront frame's stage times are positive, one extend and one shadow interval per bounce
-  launched (the bounce loop runs to the maximum depth; counts stay on the device), and they add
-  up to the frame as timed by events around the call (the stages tile the frame; only the work
-  before the first stage lies outside them);
+* a wavefront frame's stage times are positive and add up to the frame as timed by events around
+  the call (the stages tile the frame; only the work before the first stage lies outside them): in
+  the default (fused) order one extend interval per bounce, each holding the previous bounce's shadow
+  walks, and no separate shadow interval; in the separate order (PT_FLAG_SEPARATE_SHADOW) one extend
+  and one shadow interval per bounce (the bounce loop runs to the maximum depth; counts stay on the
+  device);
 * a megakernel frame is one megakernel interval; an adjoint pass is one adjoint interval that
   contains its replay's stages;
 * profiling does not change the image.
@@ -41,17 +43,19 @@ def _timed(torch, fn):
     return r, a.elapsed_time(b)
 
 
-def test_wavefront_stages_tile_the_frame(torch, setup):
+@pytest.mark.parametrize("separate", [False, True])
+def test_wavefront_stages_tile_the_frame(torch, setup, separate):
     sc, g = setup
     cam = sc["camera"]
     plain = g.render(cam, 4, 6, 11, mode="wavefront")
-    img, outer = _timed(torch, lambda: g.render(cam, 4, 6, 11, mode="wavefront", profile=True))
+    img, outer = _timed(torch, lambda: g.render(cam, 4, 6, 11, mode="wavefront", profile=True,
+                                                separate_shadow=separate))
     s = g.stats()
     assert np.array_equal(plain.cpu().numpy(), img.cpu().numpy())
-    for k in ("ms_raygen", "ms_extend", "ms_shade", "ms_shadow", "ms_reduce"):
+    for k in ("ms_raygen", "ms_extend", "ms_shade", "ms_reduce") + (("ms_shadow",) if separate else ()):
         assert s[k] > 0.0, k
     assert s["ms_megakernel"] == 0.0 and s["ms_adjoint"] == 0.0
-    assert s["launches_extend"] == 6 and s["launches_shadow"] == 6 and s["bounces"] >= 4
+    assert s["launches_extend"] == 6 and s["launches_shadow"] == (6 if separate else 0) and s["bounces"] >= 4
     staged = s["ms_raygen"] + s["ms_extend"] + s["ms_sort"] + s["ms_shade"] + s["ms_shadow"] + s["ms_reduce"]
     assert abs(s["ms_total"] - staged) <= 1e-3 * staged
     assert staged <= outer * 1.001 + 1e-3
