@@ -12,6 +12,8 @@ the device.  Prints one JSON line (rank 0).
   python bench.py --workload large      # ~10M-triangle scene, 3840x2160, 4 spp, depth 8
   python bench.py --workload diff       # inverse rendering, 512x512, 64 spp, 256 materials
   python bench.py --workload instanced  # the 1080p scene as a two-level (instanced) scene vs flat
+  python bench.py --workload single [--separate-shadow] [--two-level] [--sort M] [--short-stack]
+                                        # one untimed frame of each integrator (what ncu captures)
 Under torchrun (N > 1) each rank renders its own frames (seed offset by rank, no collective on the
 data path: weak scaling); the barrier and max-over-ranks timing are the only communication.
 """
@@ -311,8 +313,10 @@ def run_gpu(args):
     rng = np.random.default_rng(123)
     grad = torch.from_numpy(rng.uniform(-1, 1, size=(H, W, 3)).astype(np.float32)).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    wf_opts = dict(mode="wavefront", rr_start=3, sort=args.sort, profile=True)
-    mk_opts = dict(mode="megakernel", rr_start=3, profile=True)
+    ss = dict(short_stack=True) if args.short_stack else {}
+    sep = dict(separate_shadow=True) if args.separate_shadow else {}
+    wf_opts = dict(mode="wavefront", rr_start=3, sort=args.sort, profile=True, **ss, **sep)
+    mk_opts = dict(mode="megakernel", rr_start=3, profile=True, **ss)
     mk_static_opts = dict(mode="megakernel", rr_start=3, mk_static=True)
 
     def step(seed, timing):
@@ -328,7 +332,7 @@ def run_gpu(args):
         s_mk = g.stats() if timing else None
         ev_bw = torch.cuda.Event(enable_timing=True)
         ev_bw.record(stream)
-        g.backward(cam, spp, depth, seed, grad, rr_start=3, profile=True)
+        g.backward(cam, spp, depth, seed, grad, rr_start=3, profile=True, **sep)
         ev[3].record(stream)
         s_bw = g.stats() if timing else None
         flush.fill_(seed & 0xFF)                     # L2 flush, outside the timed events
@@ -437,8 +441,8 @@ def run_gpu(args):
     for name, kw in (("mis_wavefront", dict(mode="wavefront", mis=True)),
                      ("mis_megakernel", dict(mode="megakernel", mis=True)),
                      ("halton_wavefront", dict(mode="wavefront", sampler="halton")),
-                     ("wavefront_no_stage_events", dict(mode="wavefront", sort=args.sort)),
-                     ("megakernel_no_stage_events", dict(mode="megakernel"))):
+                     ("wavefront_no_stage_events", dict(mode="wavefront", sort=args.sort, **ss, **sep)),
+                     ("megakernel_no_stage_events", dict(mode="megakernel", **ss))):
         g.render(cam, spp, depth, 900, rr_start=3, **kw)
         ms = []
         for k in range(max(3, args.steps // 2)):
@@ -517,6 +521,8 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "resolution": [W, H], "spp": spp, "max_depth": depth,
                        "triangles": int(g.info()["n_tris"]), "sort": args.sort,
+                       "traversal_stack": "shared-memory short stack" if args.short_stack else "local memory",
+                       "stage_order": "separate" if args.separate_shadow or args.short_stack else "fused",
                        "l2": "flushed between steps (256 MiB write), outside the timed events"},
             "wavefront": {"mrays_s": float(np.sum(wf_rays)) / (np.sum(wf_ms) * 1e-3) / 1e6, "ms_per_frame": wf_frame,
                           "ms_per_frame_median": float(np.median(wf_ms)), "rays_per_frame": float(np.mean(wf_rays)),
@@ -581,7 +587,8 @@ def measure_e2e(g, cam, spp, depth, grad, args, wf_opts, mk_opts):
         g.render(cam, spp, depth, s, out=h_mk, **mk)
         r2 = g.stats()
         d_grad = h_grad.to("cuda", non_blocking=True)
-        ga, ge = g.backward(cam, spp, depth, s, d_grad, rr_start=3)
+        ga, ge = g.backward(cam, spp, depth, s, d_grad, rr_start=3,
+                            **({"separate_shadow": True} if args.separate_shadow else {}))
         h_ga.copy_(ga, non_blocking=True)
         h_ge.copy_(ge, non_blocking=True)
         e1.record(stream)
@@ -676,7 +683,10 @@ def measure_diff(steps: int, warmup: int, adam_steps: bool = True) -> dict:
     0.9): each step renders the image with the current albedos and emissions, takes the L2 loss
     against a target rendered with hidden parameters (another seed), back-propagates through the
     path-replay adjoint and applies an Adam update.  Returns forward and backward device times,
-    their ratio, and the loss and parameter error along the way."""
+    their ratio, and the loss and parameter error along the way.  Each step renders at a fresh seed,
+    so its loss includes both images' Monte Carlo noise, whose size depends on the parameters; the
+    loss rendered with the target's own seed (`loss_same_seed`, 0 at the hidden parameters) and the
+    albedo error measure progress without that noise."""
     import torch
 
     import paper_2605_27323_gb300 as pt
@@ -693,6 +703,7 @@ def measure_diff(steps: int, warmup: int, adam_steps: bool = True) -> dict:
     target = g.render(cam, spp, depth, 999_999, **kw).clone()
     alb = torch.tensor(np.asarray(sc["mat_albedo"], np.float32), device="cuda").reshape(-1, 3).requires_grad_()
     em = torch.tensor(np.asarray(sc["mat_emission"], np.float32), device="cuda").requires_grad_()
+    emissive = (em.detach() > 0).float()      # emission is fitted on the materials that emit
     opt = torch.optim.Adam([{"params": [alb], "lr": 0.02}, {"params": [em], "lr": 0.2}])
     stream = torch.cuda.current_stream()
     n_paths = W * H * spp
@@ -710,7 +721,7 @@ def measure_diff(steps: int, warmup: int, adam_steps: bool = True) -> dict:
         ev[2].record(stream)
         ga, ge = g.backward(cam, spp, depth, seed, grad_img, **kw)
         ev[3].record(stream)
-        alb.grad, em.grad = ga, ge
+        alb.grad, em.grad = ga, ge * emissive
         opt.step()
         with torch.no_grad():
             alb.clamp_(0.0, 1.0)
@@ -718,8 +729,16 @@ def measure_diff(steps: int, warmup: int, adam_steps: bool = True) -> dict:
         ev[4].record(stream)
         return ev, loss.detach()
 
+    def loss_same_seed():
+        # the loss with the target's own seed (common random numbers): 0 at the hidden parameters,
+        # so unlike the per-step losses it carries no Monte Carlo noise term
+        with torch.no_grad():
+            g.set_materials(alb, em)
+            return float(((g.render(cam, spp, depth, 999_999, **kw) - target) ** 2).mean())
+
     lam = torch.from_numpy(np.asarray(sc["mat_type"]) == scenes.LAMBERT).cuda()
     alb_err0 = float((alb.detach() - alb_t)[lam].abs().mean())
+    loss_ss0 = loss_same_seed()
     for w in range(warmup):
         step(50_000 + w)
     torch.cuda.synchronize()
@@ -733,6 +752,7 @@ def measure_diff(steps: int, warmup: int, adam_steps: bool = True) -> dict:
     st = g.stats()
     rays_fwd = st["extension_rays"] + st["shadow_rays"]
     alb_err = float((alb.detach() - alb_t)[lam].abs().mean())
+    loss_ss1 = loss_same_seed()
     # the adjoint's one-thread-per-path replay (mode="megakernel") on the same gradient, for comparison
     grad_img = torch.ones_like(target) * (1.0 / target.numel())
     g.backward(cam, spp, depth, 1, grad_img, mode="megakernel", **kw)
@@ -744,13 +764,14 @@ def measure_diff(steps: int, warmup: int, adam_steps: bool = True) -> dict:
     bwd_mk = e0.elapsed_time(e1)
     return {"workload": "procedural spheres geometry, 256 shared materials, 512x512, 64 spp, depth 6, roulette "
                         "from bounce 3 with q = 0.9; L2 loss to a target from hidden parameters (seed 7); Adam on "
-                        "albedo and emission",
+                        "every albedo and on the emissive material's emission",
             "paths": n_paths, "steps": steps, "warmup": warmup, "scene_setup_s": setup_s,
             "forward_ms": float(np.median(fwd)), "backward_ms": float(np.median(bwd)),
             "bwd_over_fwd": float(np.median(bwd) / np.median(fwd)), "step_ms": float(np.mean(tot)),
             "backward_one_thread_per_path_ms": bwd_mk,
             "forward_mrays_s": rays_fwd / (np.median(fwd) * 1e-3) / 1e6,
             "loss_first": losses[0], "loss_last": losses[-1],
+            "loss_same_seed": {"start": loss_ss0, "end": loss_ss1, "steps": warmup + steps},
             "lambert_albedo_mean_abs_error": {"start": alb_err0, "end": alb_err, "steps": warmup + steps}}
 
 
@@ -916,16 +937,50 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_single(args):
+    """One untimed wavefront frame (1920x1080, 1 spp, depth 5, seed 7) of the ~1.15M-triangle procedural
+    scene -- or, with --two-level, of its two-level build -- followed, on the flat scene, by one megakernel
+    frame of the same paths: the launches the per-kernel ncu captures select from.  --separate-shadow
+    renders the wavefront frame in the separate stage order, --sort with that key sort, --short-stack
+    both frames with the shared-memory short stack.  Prints the per-bounce counts."""
+    import torch
+
+    import paper_2605_27323_gb300 as pt
+    from paper_2605_27323_gb300 import scenes
+    sc = scenes.instanced_spheres_scene(seed=0) if args.two_level else scenes.spheres_scene(seed=0)
+    g = pt.Scene.from_dict(sc)
+    cam = sc["camera"]
+    g.render(cam, 1, 5, 7, mode="wavefront", separate_shadow=args.separate_shadow, sort=args.sort,
+             short_stack=args.short_stack)
+    st = g.stats()
+    out = {"workload": ("two-level" if args.two_level else "flat") + " 1080p procedural scene, 1 spp, depth 5, seed 7",
+           "order": "separate" if args.separate_shadow or args.short_stack else "fused", "sort": args.sort,
+           "short_stack": args.short_stack, "status": st["status"],
+           "active": st["active"], "shadow_queued": st["shadow_queued"],
+           "extension_rays": st["extension_rays"], "shadow_rays": st["shadow_rays"]}
+    if not args.two_level:
+        g.render(cam, 1, 5, 7, mode="megakernel", short_stack=args.short_stack)
+        sm = g.stats()
+        out.update(megakernel_extension_rays=sm["extension_rays"], megakernel_shadow_rays=sm["shadow_rays"])
+    torch.cuda.synchronize()
+    print(json.dumps(out), flush=True)
+    if st["status"] != 0:
+        sys.exit(1)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="frame", choices=["frame", "batch", "large", "diff", "instanced"])
+    ap.add_argument("--workload", default="frame", choices=["frame", "batch", "large", "diff", "instanced", "single"])
     ap.add_argument("--sort", default="none", choices=["none", "type", "material"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and inverse-rendering summaries")
+    ap.add_argument("--separate-shadow", action="store_true", help="separate shadow stage order (frame, single)")
+    ap.add_argument("--two-level", action="store_true", help="--workload single: the two-level scene")
+    ap.add_argument("--short-stack", action="store_true", help="shared-memory short traversal stack (frame, single)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -943,6 +998,9 @@ def main():
         return
     if args.workload == "instanced":
         run_instanced(args)
+        return
+    if args.workload == "single":
+        run_single(args)
         return
     run_gpu(args)
 

@@ -139,6 +139,11 @@ typedef struct {
     /* PT_FLAG_COUNT_TRAVERSAL: internal BVH nodes visited and triangles tested by the closest-hit
        (extension) and any-hit (shadow) walks of the last call; 0 otherwise. */
     uint64_t nodes_closest, tris_closest, nodes_any, tris_any;
+    uint64_t shadow_queued[64]; /* wavefront: shadow rays queued by shading at each bounce (all waves);
+                                   entries [0, bounces) are valid and sum to shadow_rays */
+    uint64_t group_walks[5];    /* walks (extension + shadow rays) that the fused trace stage traced
+                                   with groups of 2, 4, 8, 16, 32 lanes per ray (launches with few
+                                   walks, single-level scenes); the others took one lane each */
 } pt_stats;
 
 typedef struct pt_scene pt_scene;

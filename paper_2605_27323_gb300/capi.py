@@ -58,7 +58,8 @@ class Stats(C.Structure):
                 ("active", u64 * 64), ("ms_raygen", f32), ("ms_extend", f32), ("ms_sort", f32), ("ms_shade", f32),
                 ("ms_shadow", f32), ("ms_reduce", f32), ("ms_megakernel", f32), ("ms_adjoint", f32),
                 ("launches_extend", u32), ("launches_shadow", u32), ("launches_total", u32), ("ms_total", f32),
-                ("nodes_closest", u64), ("tris_closest", u64), ("nodes_any", u64), ("tris_any", u64)]
+                ("nodes_closest", u64), ("tris_closest", u64), ("nodes_any", u64), ("tris_any", u64),
+                ("shadow_queued", u64 * 64), ("group_walks", u64 * 5)]
 
 
 class PtError(RuntimeError):

@@ -188,7 +188,7 @@ struct pt_scene {
     unsigned long long* hist() const { return reinterpret_cast<unsigned long long*>(counters.as<char>() + 256); }
     unsigned long long* rays() const { return hist() + 128; }
 
-    pt_status ensure_counters() { return counters.ensure(256 + 8 * 136); }
+    pt_status ensure_counters() { return counters.ensure(256 + 8 * pt::kHistWords); }
     unsigned long long* trav() const { return hist() + 132; }   // 4 traversal counters
     unsigned long long* next_path() const { return hist() + 130; }
     unsigned long long* finish_claim() const { return hist() + 131; }
@@ -578,7 +578,7 @@ pt_status batch_render(pt_scene* const* scenes, const pt_camera* cams, const uin
         PT_TRY(carve_wavefront(ctx->wf, cap, ctx->wfb));
         ctx->capacity = cap;
     }
-    PT_TRY(ctx->counters.ensure(256 + 8 * 130));
+    PT_TRY(ctx->counters.ensure(256 + 8 * pt::kHistWords));
     // wave segments: runs of pixels of one scene inside each wave
     std::vector<pt::BatchSegment> segs;
     struct Wave {
@@ -1487,9 +1487,9 @@ pt_status pt_get_stats(pt_scene* sc, pt_stats* out) {
     PT_TRY(set_device(sc));
     PT_CUDA(cudaStreamSynchronize(sc->last_stream));
     std::memset(out, 0, sizeof(*out));
-    std::vector<unsigned long long> h(136);
+    std::vector<unsigned long long> h(pt::kHistWords);
     uint32_t status = 0;
-    PT_CUDA(cudaMemcpy(h.data(), sc->hist(), 136 * 8, cudaMemcpyDeviceToHost));
+    PT_CUDA(cudaMemcpy(h.data(), sc->hist(), pt::kHistWords * 8, cudaMemcpyDeviceToHost));
     PT_CUDA(cudaMemcpy(&status, sc->status.p, 4, cudaMemcpyDeviceToHost));
     out->paths = sc->last_paths;
     out->launches_total = sc->launches;
@@ -1501,6 +1501,7 @@ pt_status pt_get_stats(pt_scene* sc, pt_stats* out) {
             out->extension_rays += h[b];
             out->shadow_rays += h[64 + b];
             out->active[b] = h[b];
+            out->shadow_queued[b] = h[64 + b];
             if (h[b]) out->bounces = b + 1;
         }
     }
@@ -1508,6 +1509,7 @@ pt_status pt_get_stats(pt_scene* sc, pt_stats* out) {
     out->tris_closest = h[133];
     out->nodes_any = h[134];
     out->tris_any = h[135];
+    for (int i = 0; i < 5; ++i) out->group_walks[i] = h[pt::kHistGroupWalks + i];
     out->status = status & pt::ST_TRAVERSAL ? PT_ERR_TRAVERSAL_LIMIT
                 : status & pt::ST_QUEUE     ? PT_ERR_QUEUE_OVERFLOW
                 : status & pt::ST_TIMEOUT   ? PT_ERR_TIMEOUT

@@ -25,14 +25,16 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool want) {
     return base + (uint32_t)__popc(mask & ((1u << lane_id()) - 1u));
 }
 
-// Warp-granular dynamic work: each warp claims the next 32 queue slots with one atomic, so warps
-// that drew cheap rays take more batches and the grid ends together (a static grid-stride split
-// leaves the SMs waiting on the warps that drew the longest rays).
-__device__ __forceinline__ uint32_t warp_claim32(uint32_t* counter) {
+// Warp-granular dynamic work: each warp claims its next queue slots (32, one per lane; 32 / G when
+// groups of G lanes share a ray) with one atomic, so warps that drew cheap rays take more batches
+// and the grid ends together (a static grid-stride split leaves the SMs waiting on the warps that
+// drew the longest rays).
+__device__ __forceinline__ uint32_t warp_claim(uint32_t* counter, uint32_t k) {
     uint32_t b = 0u;
-    if (lane_id() == 0u) b = atomicAdd(counter, 32u);
+    if (lane_id() == 0u) b = atomicAdd(counter, k);
     return __shfl_sync(0xFFFFFFFFu, b, 0);
 }
+__device__ __forceinline__ uint32_t warp_claim32(uint32_t* counter) { return warp_claim(counter, 32u); }
 
 __device__ __forceinline__ void warp_add_u64(unsigned long long* dst, unsigned long long v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);

@@ -279,6 +279,69 @@ __global__ void __launch_bounds__(256) k_shadow(Src src, WfBuffers w, uint32_t b
     flush_count(src.scene(0), cnt, 2);
 }
 
+// The cooperative form of the fused trace stage (single-level scenes): each group of G lanes takes
+// one extension ray, then one shadow ray, per claim (trace_closest_group, trace_any_group); the
+// group's first lane writes the result exactly as the one-lane form does.
+constexpr uint32_t kCoopMinLanes = 2u;
+
+template <class Src, bool SIG, bool ADJ>
+__device__ __noinline__ void trace_groups(const Src& src, const WfBuffers& w, const AdjBuffers& a, int in,
+                                             uint32_t b, uint32_t n_ext, uint32_t n_shd, uint32_t G) {
+    const uint64_t base = src.base();
+    const uint32_t per = 32u / G, sub = lane_id() / G;
+    const bool lead = (lane_id() & (G - 1u)) == 0u;
+    unsigned long long led = 0;      // walks this lane's group traced, counted once per group
+    const float4* __restrict__ qo = w.q_o[in];
+    const float4* __restrict__ qd = w.q_d[in];
+    for (uint32_t b0 = warp_claim(&w.counts[4], per); b0 < n_ext; b0 = warp_claim(&w.counts[4], per)) {
+        const uint32_t j = b0 + sub;
+        const bool valid = j < n_ext;
+        float4 o4 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = make_float4(0.f, 0.f, 1.f, 0.f);
+        if (valid) {
+            o4 = __ldcs(&qo[j]);
+            d4 = __ldcs(&qd[j]);
+        }
+        const uint32_t sid = valid ? src.sid_from_ray(d4.w, base, __float_as_uint(o4.w)) : 0u;
+        const Hit h = trace_closest_group(src.scene(sid), xyz(o4), xyz(d4), valid, G);
+        if (valid && lead) {
+            w.hit[j] = make_float2(h.t, __uint_as_float(h.tri));
+            ++led;
+        }
+    }
+    for (uint32_t b0 = warp_claim(&w.counts[5], per); b0 < n_shd; b0 = warp_claim(&w.counts[5], per)) {
+        const uint32_t k = b0 + sub;
+        const bool valid = k < n_shd;
+        float4 so = make_float4(0.f, 0.f, 0.f, 0.f), sd = make_float4(0.f, 0.f, 1.f, 0.f);
+        float4 sc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid) {
+            so = __ldcs(&w.s_o[k]);
+            sd = __ldcs(&w.s_d[k]);
+            if (!ADJ) sc = __ldcs(&w.s_c[k]);
+        }
+        const uint32_t pid = __float_as_uint(sd.w);
+        const uint32_t sid = (valid && !ADJ) ? src.sid_from_shadow(sc.w, base, pid) : 0u;
+        const bool occ = trace_any_group(src.scene(sid), xyz(so), xyz(sd), so.w, valid, G);
+        if (!valid || !lead) continue;
+        ++led;
+        if constexpr (ADJ) {
+            if (!occ) {
+                float* fl = reinterpret_cast<float*>(a.rec + 4 * ((size_t)(b - 1u) * w.capacity + pid) + 3) + 3;
+                *fl = __uint_as_float(__float_as_uint(*fl) | 2u);
+            }
+        } else {
+            if (!occ) {
+                float3 L = add_rn(xyz(w.L[pid]), xyz(sc));
+                w.L[pid] = f4(L, 0.f);
+            }
+            if (SIG) {
+                const uint32_t lj = __float_as_uint(sc.w);
+                w.sig[base + pid] ^= sig_event(b - 1u, 1, (lj << 2) | 2u | (occ ? 0u : 1u));
+            }
+        }
+    }
+    warp_add_u64(&w.hist[kHistGroupWalks + __ffs((int)G) - 2], led);
+}
+
 // Trace (the extend stage of bounce b fused with the shadow stage of bounce b - 1): one launch walks
 // the BVH for the continuation rays of bounce b (closest hit, queue `in`, counts[0] entries) and for
 // the shadow rays that shading cast at bounce b - 1 (any hit, the shadow queue, counts[6] entries).
@@ -295,6 +358,20 @@ __global__ void __launch_bounds__(256, INST ? 4 : 6) k_trace(Src src, WfBuffers 
     const uint32_t n_ext = min(w.counts[0], w.capacity), n_shd = min(w.counts[6], w.capacity);
     if (n_ext + n_shd == 0u) return;       // the same for every thread
     const uint64_t base = src.base();
+    // Lanes per walk: 1 while the walks fill the grid; once they are few (the sparse late bounces),
+    // the largest power of two G <= 32 with walks x G <= the grid's threads (cooperative walks,
+    // single-level scenes; the counting instantiations keep the one-lane walk their counts describe).
+    // The same for every thread: the counts are fixed during the launch.
+    uint32_t G = 1u;
+    if constexpr (!INST && !CNT) {
+        const uint64_t threads = (uint64_t)gridDim.x * blockDim.x;
+        while (G < 32u && (uint64_t)(n_ext + n_shd) * (2u * G) <= threads) G *= 2u;
+        if (G < kCoopMinLanes) G = 1u;
+    }
+    if (G > 1u) {
+        trace_groups<Src, SIG, ADJ>(src, w, a, in, b, n_ext, n_shd, G);
+        return;
+    }
     typename std::conditional<CNT, TravCount, NoCount>::type cc, ca;
     {
         const float4* __restrict__ qo = w.q_o[in];

@@ -30,7 +30,7 @@ bool static_is_device_ptr(const void* p);
 namespace {
 
 constexpr size_t kStaticScratchBytes = 32ull << 20;
-constexpr size_t kHeaderBytes = 256 + 8 * 128;  // counters (incl. this call's status word) and histories
+constexpr size_t kHeaderBytes = 256 + 8 * pt::kHistWords;  // counters (incl. this call's status word), totals
 constexpr uint32_t kStatusWord = 16;            // counts[16]: device status word of this call
 constexpr int kMaxDevices = 64;
 

@@ -237,6 +237,210 @@ __device__ __forceinline__ Hit trace_closest_plain(const DevScene& s, float3 o, 
     return h;
 }
 
+// ------------------------------------------------------------------ cooperative walks
+// A trace launch with few walks leaves most of the GPU idle, and it then lasts as long as its
+// longest walk: a chain of dependent node loads.  Such a launch gives each ray a group of G lanes
+// (an aligned power-of-two group of a warp, G <= 32).  Every lane walks depth first as above and
+// defers far children to a ring of kStack entries; a lane left without work takes the oldest entry
+// (the deferred subtree nearest the root) of a lane in its group that holds one, so the subtrees of
+// one ray are walked side by side.  Boxes are culled against the smallest best distance in the
+// group, which is never below the final one, so the culling stays conservative and the result --
+// the smallest (t, prim) over the group -- is the hit of the single-lane walk.  An any-hit walk ends
+// as soon as one lane of the group finds an occluder.  All 32 lanes of the warp run these loops
+// together with the same G (shuffles over the full warp); lanes of a group without a ray pass
+// valid = false and stay idle.
+struct RingStack {
+    uint32_t ref[kStack];
+    float t[kStack];
+    uint32_t bot = 0, top = 0;     // entries [bot, top), indexed modulo kStack
+    __device__ __forceinline__ bool empty() const { return bot == top; }
+    __device__ __forceinline__ bool push(uint32_t r, float tt) {
+        if (top - bot >= (uint32_t)kStack) return false;
+        ref[top & (kStack - 1)] = r;
+        t[top & (kStack - 1)] = tt;
+        ++top;
+        return true;
+    }
+    // the newest entry (the lane's own depth-first order)
+    __device__ __forceinline__ void pop(uint32_t& r, float& tt) {
+        --top;
+        r = ref[top & (kStack - 1)];
+        tt = t[top & (kStack - 1)];
+    }
+    // the oldest entry, handed to an idle lane
+    __device__ __forceinline__ void take_bottom(uint32_t& r, float& tt) {
+        r = ref[bot & (kStack - 1)];
+        tt = t[bot & (kStack - 1)];
+        ++bot;
+    }
+    __device__ __forceinline__ void clear() { bot = top; }
+};
+static_assert((kStack & (kStack - 1)) == 0, "the ring indexes modulo kStack");
+
+__device__ __forceinline__ uint32_t group_mask(uint32_t G, uint32_t lane) {
+    return G == 32u ? 0xFFFFFFFFu : ((1u << G) - 1u) << (lane & ~(G - 1u));
+}
+__device__ __forceinline__ float group_min(float v, uint32_t G) {
+    for (uint32_t o = G >> 1; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    return v;
+}
+__device__ __forceinline__ uint32_t group_min(uint32_t v, uint32_t G) {
+    for (uint32_t o = G >> 1; o; o >>= 1) v = min(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    return v;
+}
+
+// One work-sharing step of a group (mask gm): its idle lanes and the lanes that hold deferred
+// entries are paired in lane order, and each paired donor moves its oldest entry to its idle lane,
+// which takes it up unless its entry distance is beyond `tcull` (closest-hit walks; any-hit walks
+// defer entries at distance 0).  Returns whether the whole group is idle with nothing deferred.
+__device__ __forceinline__ bool group_share(uint32_t gm, uint32_t lane, bool& busy, uint32_t& ref, RingStack& rs,
+                                            float tcull) {
+    const uint32_t idle = __ballot_sync(0xFFFFFFFFu, !busy) & gm;
+    const uint32_t donors = __ballot_sync(0xFFFFFFFFu, busy && !rs.empty()) & gm;
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t pairs = min((uint32_t)__popc(idle), (uint32_t)__popc(donors));
+    uint32_t give_r = 0u;
+    float give_t = 0.f;
+    if (((donors >> lane) & 1u) && (uint32_t)__popc(donors & below) < pairs) rs.take_bottom(give_r, give_t);
+    uint32_t from = lane;
+    const uint32_t k = (uint32_t)__popc(idle & below);
+    if (((idle >> lane) & 1u) && k < pairs) {
+        uint32_t m = donors;                  // the k-th donor, counting from the lowest lane
+        for (uint32_t i = 0; i < k; ++i) m &= m - 1u;
+        from = (uint32_t)__ffs(m) - 1u;
+    }
+    const uint32_t got_r = __shfl_sync(0xFFFFFFFFu, give_r, from);
+    const float got_t = __shfl_sync(0xFFFFFFFFu, give_t, from);
+    if (from != lane && got_t <= tcull * 1.0000005f) {
+        busy = true;
+        ref = got_r;
+    }
+    return idle == gm;
+}
+
+__device__ __forceinline__ Hit trace_closest_group(const DevScene& s, float3 o, float3 d, bool valid, uint32_t G) {
+    const uint32_t lane = threadIdx.x & 31u, gm = group_mask(G, lane);
+    const float3 id = ray_rcp(d);
+    float tbest = __int_as_float(0x7f800000);
+    uint32_t best = kMiss, bprim = kMiss;
+    bool busy = valid && (lane & (G - 1u)) == 0u;    // the group's first lane starts at the root
+    uint32_t ref = 0u;
+    RingStack rs;
+    uint32_t steps = 0;
+    while (true) {
+        const float tg = group_min(tbest, G);
+        if (busy) {
+            if (!(ref & kLeafBit)) {
+                float4 n0, n1, n2;
+                uint2 r;
+                load_node(s.nodes, ref, n0, n1, n2, r);
+                float t0, t1;
+                const bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tg, t0);
+                const bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tg, t1);
+                if (h0 && h1) {
+                    const bool first0 = t0 <= t1;
+                    if (!rs.push(first0 ? r.y : r.x, first0 ? t1 : t0)) atomicOr(s.status, ST_TRAVERSAL);
+                    ref = first0 ? r.x : r.y;
+                } else if (h0 || h1) {
+                    ref = h0 ? r.x : r.y;
+                } else {
+                    busy = false;
+                }
+            } else {
+                const uint32_t first = (ref & 0x7FFFFFFFu) >> 3, n_leaf = (ref & 7u) + 1u;
+                for (uint32_t k = 0; k < n_leaf; ++k) {
+                    float t;
+                    uint32_t prim;
+                    if (tri_test(s.tris, first + k, o, d, t, prim) && t > 0.0f &&
+                        (t < tbest || (t == tbest && prim < bprim))) {
+                        tbest = t;
+                        best = first + k;
+                        bprim = prim;
+                    }
+                }
+                busy = false;
+            }
+            if (++steps >= kMaxSteps) {
+                atomicOr(s.status, ST_TRAVERSAL);
+                busy = false;
+                rs.clear();
+            }
+        }
+        const float tc = fminf(tg, tbest);
+        while (!busy && !rs.empty()) {       // the next own subtree whose entry is not beyond the best hit
+            float t;
+            rs.pop(ref, t);
+            busy = t <= tc * 1.0000005f;
+        }
+        const bool over = group_share(gm, lane, busy, ref, rs, tc);
+        if (__all_sync(0xFFFFFFFFu, over)) break;
+    }
+    // the group's hit: the smallest t, then the smallest original id among equal t
+    Hit h;
+    h.t = group_min(tbest, G);
+    h.prim = group_min(tbest == h.t ? bprim : kMiss, G);
+    const uint32_t own = __ballot_sync(0xFFFFFFFFu, tbest == h.t && bprim == h.prim) & gm;
+    h.tri = __shfl_sync(0xFFFFFFFFu, best, own ? (uint32_t)__ffs(own) - 1u : lane);
+    h.inst = kMiss;
+    return h;
+}
+
+__device__ __forceinline__ bool trace_any_group(const DevScene& s, float3 o, float3 d, float tmax, bool valid,
+                                                uint32_t G) {
+    const uint32_t lane = threadIdx.x & 31u, gm = group_mask(G, lane);
+    const float3 id = ray_rcp(d);
+    bool busy = valid && (lane & (G - 1u)) == 0u, hit = false;
+    uint32_t ref = 0u;
+    RingStack rs;
+    uint32_t steps = 0;
+    while (true) {
+        if (busy) {
+            if (!(ref & kLeafBit)) {
+                float4 n0, n1, n2;
+                uint2 r;
+                load_node(s.nodes, ref, n0, n1, n2, r);
+                float t0, t1;
+                const bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tmax, t0);
+                const bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tmax, t1);
+                if (h0 && h1) {
+                    const bool first0 = t0 <= t1;
+                    if (!rs.push(first0 ? r.y : r.x, 0.f)) atomicOr(s.status, ST_TRAVERSAL);
+                    ref = first0 ? r.x : r.y;
+                } else if (h0 || h1) {
+                    ref = h0 ? r.x : r.y;
+                } else {
+                    busy = false;
+                }
+            } else {
+                const uint32_t first = (ref & 0x7FFFFFFFu) >> 3, n_leaf = (ref & 7u) + 1u;
+                for (uint32_t k = 0; k < n_leaf && !hit; ++k) {
+                    float t;
+                    uint32_t prim;
+                    hit = tri_test(s.tris, first + k, o, d, t, prim) && t > 0.0f && t < tmax;
+                }
+                busy = false;
+            }
+            if (++steps >= kMaxSteps) {
+                atomicOr(s.status, ST_TRAVERSAL);
+                busy = false;
+                rs.clear();
+            }
+        }
+        if (__ballot_sync(0xFFFFFFFFu, hit) & gm) {      // an occluder anywhere ends the group's walk
+            busy = false;
+            rs.clear();
+        }
+        if (!busy && !rs.empty()) {
+            float t;
+            rs.pop(ref, t);
+            busy = true;
+        }
+        const bool over = group_share(gm, lane, busy, ref, rs, 0.f);
+        if (__all_sync(0xFFFFFFFFu, over)) break;
+    }
+    return (__ballot_sync(0xFFFFFFFFu, hit) & gm) != 0u;
+}
+
 // Any hit with 0 < t < tmax.
 template <class Stk, class C = NoCount>
 __device__ __forceinline__ bool trace_any_plain(const DevScene& s, float3 o, float3 d, float tmax, Stk& stk, C& cnt) {

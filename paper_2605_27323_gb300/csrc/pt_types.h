@@ -86,7 +86,7 @@ struct WfBuffers {
     float4* L;               // per path (wave-local): radiance.rgb | -
     uint32_t* counts;        // [0] active, [1] next, [2] shadow, [3] sort key count, [4] [5] work claims,
                              // [6] shadow rays pending for the fused trace launch
-    unsigned long long* hist;  // [b] extension rays of bounce b, [64 + b] shadow rays of bounce b
+    unsigned long long* hist;  // kHistWords per-call totals (layout at kHistWords)
     uint32_t* sig;           // per path (global id) branch signature, or null
     uint32_t capacity;
 };
@@ -131,6 +131,13 @@ constexpr uint32_t kMaxEvents = 64;     // event-log capacity per path (testing 
 // Device bytes of one wave's records per path: two ping-pong ray queues of three float4 arrays, the
 // hit record (float2), the hit instance, sort key and permutation (u32 each), the shadow queue (three
 // float4 arrays) and the radiance (float4).
+// Per-call device totals (64-bit words after the 256-byte count block): [b] extension rays of bounce
+// b, [64 + b] shadow rays of bounce b, [128] [129] megakernel ray totals, [130] next path to start,
+// [131] hybrid claim, [132, 136) traversal counters, [136, 141) walks the fused trace stage traced
+// with groups of 2, 4, 8, 16, 32 lanes per ray.
+constexpr int kHistWords = 144;
+constexpr int kHistGroupWalks = 136;
+
 constexpr size_t kWfBytesPerPath = 2 * 3 * 16 + 8 + 3 * 4 + 3 * 16 + 16;
 static_assert(kWfBytesPerPath == 180, "wavefront record layout changed: update the documented sizes");
 

@@ -258,8 +258,10 @@ class Scene:
     def stats(self) -> dict:
         s = capi.Stats()
         capi.check(self._lib.pt_get_stats(self.h, C.byref(s)))
-        d = {k: getattr(s, k) for k, _ in capi.Stats._fields_ if k != "active"}
+        d = {k: getattr(s, k) for k, _ in capi.Stats._fields_ if k not in ("active", "shadow_queued", "group_walks")}
+        d["group_walks"] = list(s.group_walks)
         d["active"] = list(s.active)[: s.bounces]
+        d["shadow_queued"] = list(s.shadow_queued)[: s.bounces]
         return d
 
 

@@ -107,7 +107,8 @@ def test_struct_layouts_match_a_compiled_header(tmp_path):
                                                 "queue_capacity", "d_path_sig", "hybrid_threshold"]),
               "pt_instance": ("Instance", ["xform", "mesh", "material", "reserved"]),
               "pt_stats": ("Stats", ["extension_rays", "shadow_rays", "paths", "bounces", "status", "active",
-                                     "ms_raygen", "ms_adjoint", "launches_extend", "launches_total", "ms_total"])}
+                                     "ms_raygen", "ms_adjoint", "launches_extend", "launches_total", "ms_total",
+                                     "nodes_closest", "tris_any", "shadow_queued", "group_walks"])}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pt.h"', "int main(void) {"]
     for cname, (_, fs) in fields.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')

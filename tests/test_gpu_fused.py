@@ -1,9 +1,9 @@
 """The fused stage order of the wavefront (each bounce's extend launch also walks the shadow rays the
 previous shading cast; the default) against the paper's separate order (PT_FLAG_SEPARATE_SHADOW,
 a shadow stage after each shading): the same walks and the same additions to each path's radiance
-in the same order, so images, per-path radiance, signatures and ray counts are bit-identical -- on
-single-level and two-level scenes, with MIS and the Halton jitter, in waves, with the key sort, and
-through the adjoint replay.  The default order is the one every oracle-parity test exercises."""
+in the same order, so images, per-path radiance, signatures and ray counts (per bounce too) are
+bit-identical -- on single-level and two-level scenes, with MIS and the Halton jitter, in waves,
+with the key sort, and through the adjoint replay.  The default order is the one every oracle-parity test exercises."""
 import numpy as np
 import pytest
 
@@ -45,7 +45,8 @@ def test_fused_and_separate_orders_agree_bitwise(torch, k):
         st = g.stats()
         assert st["status"] == 0
         out[sep] = (r["img"].cpu().numpy(), r["path_L"].cpu().numpy(), r["sig"].cpu().numpy(),
-                    st["extension_rays"], st["shadow_rays"], st["active"])
+                    st["extension_rays"], st["shadow_rays"], st["active"], st["shadow_queued"])
+        assert sum(st["shadow_queued"]) == st["shadow_rays"] and sum(st["active"]) == st["extension_rays"]
     a, b = out[False], out[True]
     for x, y in zip(a[:3], b[:3]):
         assert np.array_equal(x, y), name
