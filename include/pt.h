@@ -90,12 +90,13 @@ enum {
                                    memory.  Same hits and images; slower than the default local-memory
                                    stack on GB300, whose L1 already holds it.  Ignored elsewhere. */
     PT_FLAG_SEPARATE_SHADOW = 128u, /* wavefront (pt_render, pt_render_progressive, pt_render_backward's
-                                   wavefront replay, pt_render_batch): run the shadow stage as its own
-                                   launch after shading, as the paper's stage list orders it, instead of
-                                   walking each bounce's shadow rays in the next bounce's extend launch.
-                                   Same image and gradients; the default fused order has one stage boundary
-                                   fewer per bounce.  The hybrid continuation, PT_FLAG_SHORT_STACK and
-                                   pt_render_wavefront_static always use the separate order. */
+                                   wavefront replay, pt_render_batch, pt_render_wavefront_static): run the
+                                   shadow stage as its own launch after shading, as the paper's stage list
+                                   orders it, instead of walking each bounce's shadow rays in the next
+                                   bounce's extend launch.  Same image and gradients; the default fused
+                                   order has one stage boundary fewer per bounce, and its trace launches
+                                   give each ray a group of lanes when they hold few walks.  The hybrid
+                                   continuation and PT_FLAG_SHORT_STACK always use the separate order. */
     PT_FLAG_COUNT_TRAVERSAL = 64u  /* pt_render / pt_render_progressive on single-level scenes without
                                    d_path_sig: the extend and shadow stages and the regenerating
                                    megakernel run instantiations that count the BVH nodes visited and the
@@ -259,17 +260,19 @@ pt_status pt_trace_closest(pt_scene* scene, const float* d_rays, uint32_t n, flo
  * variant of pt_render (mode = wavefront) for callers that cannot allocate device memory or let a
  * library do it -- an application whose own memory manager owns the whole device, or a real-time
  * loop that cannot absorb the implicit synchronisation of cudaMalloc/cudaFree.  Its queues live in
- * one 32 MiB file-scope device array that every GPU loading libpt.so holds until the process exits;
- * frames are rendered in waves of whole pixels that fit it (about 186,000 paths per wave), with the
+ * one 384 MiB file-scope device array, which a GPU holds from the first call on it (when CUDA loads
+ * that part of the library) until the process exits; frames
+ * are rendered in waves of whole pixels that fit it (2,236,954 paths per wave: a 1-spp 1920x1080
+ * frame is one wave), with the
  * same kernels and random numbers, so the image equals pt_render's.  Arguments as for pt_render,
  * except: d_out_rgb (and opts->d_path_sig, if set) must be device memory (nothing is staged), there
  * is no per-path output, and of opts only rr_start, rr_fixed, sort_mode, block_size, d_path_sig and
- * the flags PT_FLAG_HALTON and PT_FLAG_MIS are used (queue_capacity and the other flags are
- * ignored).  Device-side faults of the call (the traversal step cap, a queue overflow) are recorded
+ * the flags PT_FLAG_HALTON, PT_FLAG_MIS and PT_FLAG_SEPARATE_SHADOW are used (queue_capacity and the
+ * other flags are ignored).  Device-side faults of the call (the traversal step cap, a queue overflow) are recorded
  * in a status word inside the array, which the call clears when it starts; they are not reported
  * (pt_get_stats does not see this call and keeps describing the scene's last pt_render call).
  * Errors: PT_ERR_INVALID_ARG also when one pixel's spp samples need more than the array
- * (spp x 180 bytes > 32 MiB), for opts->mode other than PT_MODE_WAVEFRONT and for a nonzero
+ * (spp x 180 bytes > 384 MiB), for opts->mode other than PT_MODE_WAVEFRONT and for a nonzero
  * opts->hybrid_threshold.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share the
  * array and it keeps the last call's contents: each call clears its own counters, and calls that

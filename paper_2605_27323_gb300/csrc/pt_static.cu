@@ -3,8 +3,10 @@
 // library do it (an application whose memory manager owns every byte of the device, or a
 // real-time loop that cannot absorb the implicit synchronisation of cudaMalloc/cudaFree).
 //
-// The array is kStaticScratchBytes (32 MiB) and lives on every GPU that loads this library until
-// the process exits.  Frames larger than one array's worth of paths are rendered in waves of whole
+// The array is kStaticScratchBytes (384 MiB, 0.13% of a GB300's memory: room for 2.2 million paths,
+// so a 1-spp 1920x1080 frame renders in one wave); a GPU holds it from the first call on it (CUDA
+// loads this file's module, and the array with it, when the call looks up its address) until the
+// process exits.  Frames larger than one array's worth of paths are rendered in waves of whole
 // pixels.  Every call shares the array: it keeps the previous call's contents, this file clears the
 // counters and the call's status word that must start at zero on every call, and calls that overlap
 // on the GPU (other streams, other threads) race on it.  The first call on a device looks up the
@@ -29,7 +31,7 @@ bool static_is_device_ptr(const void* p);
 
 namespace {
 
-constexpr size_t kStaticScratchBytes = 32ull << 20;
+constexpr size_t kStaticScratchBytes = 384ull << 20;
 constexpr size_t kHeaderBytes = 256 + 8 * pt::kHistWords;  // counters (incl. this call's status word), totals
 constexpr uint32_t kStatusWord = 16;            // counts[16]: device status word of this call
 constexpr int kMaxDevices = 64;
@@ -138,9 +140,13 @@ extern "C" pt_status pt_render_wavefront_static(pt_scene* scene, const pt_camera
     // resident blocks per SM of the three persistent stages, looked up once per call (the two-level
     // instantiations have their own register counts)
     const bool inst = ds.tlas != nullptr;
+    // the fused order of pt_render (each bounce's trace launch also walks the shadow rays of the
+    // previous shading) unless PT_FLAG_SEPARATE_SHADOW asks for the separate shadow stage
+    const bool fused = !(o.flags & PT_FLAG_SEPARATE_SHADOW);
     const int per_extend = pt::max_blocks_per_sm(inst ? pt::K_EXTEND_INST : pt::K_EXTEND, block);
     const int per_shade = pt::max_blocks_per_sm(inst ? pt::K_SHADE_INST : pt::K_SHADE, block);
-    const int per_shadow = pt::max_blocks_per_sm(inst ? pt::K_SHADOW_INST : pt::K_SHADOW, block);
+    const int per_shadow = fused ? 0 : pt::max_blocks_per_sm(inst ? pt::K_SHADOW_INST : pt::K_SHADOW, block);
+    const int per_trace = fused ? pt::max_blocks_per_sm(inst ? pt::K_TRACE_INST : pt::K_TRACE, block) : 0;
     auto persistent = [&](int per, uint64_t work) {
         pt::Launch l;
         l.block = block;
@@ -171,14 +177,23 @@ extern "C" pt_status pt_render_wavefront_static(pt_scene* scene, const pt_camera
     for (uint64_t w0 = 0; w0 < n_paths; w0 += cap) {
         const uint32_t n = (uint32_t)std::min<uint64_t>(cap, n_paths - w0);
         p.path_begin = w0;
-        const pt::Launch le = persistent(per_extend, n), ls = persistent(per_shade, n), lw = persistent(per_shadow, n);
+        const pt::Launch le = persistent(per_extend, n), ls = persistent(per_shade, n);
+        const pt::Launch lw = persistent(per_shadow, n), lt = persistent(per_trace, 2ull * n);
         if ((e = pt::launch_raygen(plain(n), dc, p, n, w)) != cudaSuccess) return cuda_fail(e, "raygen");
         for (uint32_t b = 0; b < max_depth; ++b) {
             const int in = (int)(b & 1u);
-            if ((e = pt::launch_extend(le, ds, w, in, p)) != cudaSuccess) return cuda_fail(e, "extend");
+            if (!fused || b == 0) {          // no shadow rays are pending before the first shading
+                if ((e = pt::launch_extend(le, ds, w, in, p)) != cudaSuccess) return cuda_fail(e, "extend");
+            } else if ((e = pt::launch_trace(lt, ds, p, w, in, b)) != cudaSuccess) {
+                return cuda_fail(e, "trace");
+            }
             if (n_keys && (e = pt::launch_sort(plain(n), ds, w, in, sort_mode, n_keys, p)) != cudaSuccess)
                 return cuda_fail(e, "sort");
             if ((e = pt::launch_shade(ls, ds, p, w, in, b, n_keys > 0)) != cudaSuccess) return cuda_fail(e, "shade");
+            if (fused) {
+                if ((e = pt::launch_prepare_fused(st, w, b)) != cudaSuccess) return cuda_fail(e, "prepare");
+                continue;
+            }
             if ((e = pt::launch_shadow(lw, ds, p, w, b)) != cudaSuccess) return cuda_fail(e, "shadow");
             if ((e = pt::launch_prepare(st, w, b)) != cudaSuccess) return cuda_fail(e, "prepare");
         }

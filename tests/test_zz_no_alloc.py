@@ -1,6 +1,6 @@
 """pt_render_wavefront_static: the wavefront render for callers that cannot allocate device memory
 (an application whose memory manager owns the whole device, or a real-time loop that cannot absorb
-cudaMalloc's implicit synchronisation).  Its queues live in a fixed 32 MiB device array inside the
+cudaMalloc's implicit synchronisation).  Its queues live in a fixed 384 MiB device array inside the
 library, so it renders in waves; its images must equal pt_render's (wavefront) bit for bit -- the
 tolerance every wavefront variant is held to in these tests -- on two calls in a row, sharing the
 array.  This file is collected last on purpose."""
@@ -35,14 +35,16 @@ def test_static_scratch_render_equals_pt_render_on_two_calls():
     box = _mixed_box(96, 72)
     spheres = scenes.spheres_scene(seed=2, n_spheres=30, level=3, ground_quads=64, width=480, height=270,
                                    extent=20.0)
-    # call 1: one wave; call 2: 2.07 M paths, about eleven waves of the static array
-    cases = [(box, box["camera"], 4, 8, 3, "none"), (spheres, spheres["camera"], 16, 5, 9, "material")]
-    for sc, cam, spp, depth, seed, sort in cases:
+    # call 1: one wave; calls 2 and 3: 4.15 M paths, two waves of the static array, in the default
+    # fused stage order and in the separate one
+    cases = [(box, box["camera"], 4, 8, 3, "none", False), (spheres, spheres["camera"], 32, 5, 9, "material", False),
+             (spheres, spheres["camera"], 32, 5, 9, "material", True)]
+    for sc, cam, spp, depth, seed, sort, sep in cases:
         g = pt.Scene.from_dict(sc)
         ref = g.render(cam, spp, depth, seed, mode="wavefront", sort=sort)
         out = torch.full_like(ref, float("nan"))
         c = make_camera(cam)
-        o = make_opts(mode="wavefront", sort=sort)
+        o = make_opts(mode="wavefront", sort=sort, separate_shadow=sep)
         st = lib.pt_render_wavefront_static(g.h, C.byref(c), spp, depth, seed, C.byref(o), C.c_void_p(out.data_ptr()),
                                             stream)
         assert st == 0, lib.pt_last_error()
@@ -89,8 +91,8 @@ def test_static_scratch_rejects_what_it_cannot_hold():
     c = make_camera(sc["camera"])
     o = make_opts()
     out = torch.zeros((2, 2, 3), device="cuda")
-    # one pixel's samples must fit the array: 200,000 x 180 B > 32 MiB
-    assert lib.pt_render_wavefront_static(g.h, C.byref(c), 200_000, 4, 0, C.byref(o), C.c_void_p(out.data_ptr()),
+    # one pixel's samples must fit the array: 3,000,000 x 180 B > 384 MiB
+    assert lib.pt_render_wavefront_static(g.h, C.byref(c), 3_000_000, 4, 0, C.byref(o), C.c_void_p(out.data_ptr()),
                                           stream) == 1
     assert b"static scratch" in lib.pt_last_error()
     host = np.zeros((2, 2, 3), np.float32)
