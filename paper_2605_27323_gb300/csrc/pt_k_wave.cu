@@ -279,12 +279,12 @@ __global__ void __launch_bounds__(256) k_shadow(Src src, WfBuffers w, uint32_t b
     flush_count(src.scene(0), cnt, 2);
 }
 
-// The cooperative form of the fused trace stage (single-level scenes): each group of G lanes takes
-// one extension ray, then one shadow ray, per claim (trace_closest_group, trace_any_group); the
+// The cooperative form of the fused trace stage: each group of G lanes takes one extension ray, then
+// one shadow ray, per claim (trace_closest_group / trace_any_group, or their two-level forms); the
 // group's first lane writes the result exactly as the one-lane form does.
 constexpr uint32_t kCoopMinLanes = 2u;
 
-template <class Src, bool SIG, bool ADJ>
+template <class Src, bool SIG, bool INST, bool ADJ>
 __device__ __noinline__ void trace_groups(const Src& src, const WfBuffers& w, const AdjBuffers& a, int in,
                                              uint32_t b, uint32_t n_ext, uint32_t n_shd, uint32_t G) {
     const uint64_t base = src.base();
@@ -302,9 +302,11 @@ __device__ __noinline__ void trace_groups(const Src& src, const WfBuffers& w, co
             d4 = __ldcs(&qd[j]);
         }
         const uint32_t sid = valid ? src.sid_from_ray(d4.w, base, __float_as_uint(o4.w)) : 0u;
-        const Hit h = trace_closest_group(src.scene(sid), xyz(o4), xyz(d4), valid, G);
+        const Hit h = INST ? trace_closest_group_inst(src.scene(sid), xyz(o4), xyz(d4), valid, G)
+                           : trace_closest_group(src.scene(sid), xyz(o4), xyz(d4), valid, G);
         if (valid && lead) {
             w.hit[j] = make_float2(h.t, __uint_as_float(h.tri));
+            if (INST) w.hit_inst[j] = h.inst;
             ++led;
         }
     }
@@ -320,7 +322,8 @@ __device__ __noinline__ void trace_groups(const Src& src, const WfBuffers& w, co
         }
         const uint32_t pid = __float_as_uint(sd.w);
         const uint32_t sid = (valid && !ADJ) ? src.sid_from_shadow(sc.w, base, pid) : 0u;
-        const bool occ = trace_any_group(src.scene(sid), xyz(so), xyz(sd), so.w, valid, G);
+        const bool occ = INST ? trace_any_group_inst(src.scene(sid), xyz(so), xyz(sd), so.w, valid, G)
+                              : trace_any_group(src.scene(sid), xyz(so), xyz(sd), so.w, valid, G);
         if (!valid || !lead) continue;
         ++led;
         if constexpr (ADJ) {
@@ -359,17 +362,17 @@ __global__ void __launch_bounds__(256, INST ? 4 : 6) k_trace(Src src, WfBuffers 
     if (n_ext + n_shd == 0u) return;       // the same for every thread
     const uint64_t base = src.base();
     // Lanes per walk: 1 while the walks fill the grid; once they are few (the sparse late bounces),
-    // the largest power of two G <= 32 with walks x G <= the grid's threads (cooperative walks,
-    // single-level scenes; the counting instantiations keep the one-lane walk their counts describe).
+    // the largest power of two G <= 32 with walks x G <= the grid's threads (cooperative walks; the
+    // counting instantiations keep the one-lane walk their counts describe).
     // The same for every thread: the counts are fixed during the launch.
     uint32_t G = 1u;
-    if constexpr (!INST && !CNT) {
+    if constexpr (!CNT) {
         const uint64_t threads = (uint64_t)gridDim.x * blockDim.x;
         while (G < 32u && (uint64_t)(n_ext + n_shd) * (2u * G) <= threads) G *= 2u;
         if (G < kCoopMinLanes) G = 1u;
     }
     if (G > 1u) {
-        trace_groups<Src, SIG, ADJ>(src, w, a, in, b, n_ext, n_shd, G);
+        trace_groups<Src, SIG, INST, ADJ>(src, w, a, in, b, n_ext, n_shd, G);
         return;
     }
     typename std::conditional<CNT, TravCount, NoCount>::type cc, ca;

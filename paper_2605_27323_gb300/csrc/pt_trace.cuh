@@ -714,6 +714,250 @@ __device__ __forceinline__ bool trace_any_inst(const DevScene& s, float3 o, floa
     }
 }
 
+// Two-level scenes, cooperatively: the same group walk over the top-level tree and, inside each
+// instance the ray enters, over the mesh's tree.  A deferred entry also names its instance (kMiss for
+// a top-level subtree); a lane that takes up an entry of another instance first takes the ray to
+// that instance's object space.  t is the world parameter at both levels, so the group's best
+// distance culls both, and the hit -- the smallest (t, original id) with its instance -- is the
+// one-lane walk's.
+struct RingStackInst {
+    uint32_t ref[kStack];
+    float t[kStack];
+    uint32_t inst[kStack];
+    uint32_t bot = 0, top = 0;
+    __device__ __forceinline__ bool empty() const { return bot == top; }
+    __device__ __forceinline__ bool push(uint32_t r, float tt, uint32_t k) {
+        if (top - bot >= (uint32_t)kStack) return false;
+        ref[top & (kStack - 1)] = r;
+        t[top & (kStack - 1)] = tt;
+        inst[top & (kStack - 1)] = k;
+        ++top;
+        return true;
+    }
+    __device__ __forceinline__ void pop(uint32_t& r, float& tt, uint32_t& k) {
+        --top;
+        r = ref[top & (kStack - 1)];
+        tt = t[top & (kStack - 1)];
+        k = inst[top & (kStack - 1)];
+    }
+    __device__ __forceinline__ void take_bottom(uint32_t& r, float& tt, uint32_t& k) {
+        r = ref[bot & (kStack - 1)];
+        tt = t[bot & (kStack - 1)];
+        k = inst[bot & (kStack - 1)];
+        ++bot;
+    }
+    __device__ __forceinline__ void clear() { bot = top; }
+};
+
+// group_share for two-level walks: a paired idle lane also receives the entry's instance (`k`).
+__device__ __forceinline__ bool group_share_inst(uint32_t gm, uint32_t lane, bool& busy, uint32_t& ref, uint32_t& k,
+                                                 bool& moved, RingStackInst& rs, float tcull) {
+    const uint32_t idle = __ballot_sync(0xFFFFFFFFu, !busy) & gm;
+    const uint32_t donors = __ballot_sync(0xFFFFFFFFu, busy && !rs.empty()) & gm;
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t pairs = min((uint32_t)__popc(idle), (uint32_t)__popc(donors));
+    uint32_t give_r = 0u, give_k = kMiss;
+    float give_t = 0.f;
+    if (((donors >> lane) & 1u) && (uint32_t)__popc(donors & below) < pairs) rs.take_bottom(give_r, give_t, give_k);
+    uint32_t from = lane;
+    const uint32_t n = (uint32_t)__popc(idle & below);
+    if (((idle >> lane) & 1u) && n < pairs) {
+        uint32_t m = donors;
+        for (uint32_t i = 0; i < n; ++i) m &= m - 1u;
+        from = (uint32_t)__ffs(m) - 1u;
+    }
+    const uint32_t got_r = __shfl_sync(0xFFFFFFFFu, give_r, from);
+    const float got_t = __shfl_sync(0xFFFFFFFFu, give_t, from);
+    const uint32_t got_k = __shfl_sync(0xFFFFFFFFu, give_k, from);
+    moved = false;
+    if (from != lane && got_t <= tcull * 1.0000005f) {
+        busy = true;
+        ref = got_r;
+        k = got_k;
+        moved = true;
+    }
+    return idle == gm;
+}
+
+// One step of a two-level group walk at `ref` (level `cur`: kMiss = top level, else an instance,
+// whose object-space ray is r with reciprocal direction idr): internal nodes push their far child and
+// descend; a top-level leaf sets `cur` to its (first) instance and defers the others; a mesh leaf is
+// tested by `leaf`.  Returns whether the lane is still busy.
+template <class Leaf>
+__device__ __forceinline__ bool inst_group_step(const DevScene& s, float3 o, float3 id, uint32_t& cur, const InstRay& r,
+                                                float3 idr, uint32_t& ref, float tcull, bool push_t,
+                                                RingStackInst& rs, Leaf leaf) {
+    if (!(ref & kLeafBit)) {
+        float4 n0, n1, n2;
+        uint2 c;
+        const bool top = cur == kMiss;
+        load_node(top ? s.tlas : s.nodes, ref, n0, n1, n2, c);
+        const float3 ro = top ? o : r.o, ri = top ? id : idr;
+        float t0, t1;
+        const bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, ro, ri, tcull, t0);
+        const bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, ro, ri, tcull, t1);
+        if (h0 && h1) {
+            const bool first0 = t0 <= t1;
+            if (!rs.push(first0 ? c.y : c.x, push_t ? (first0 ? t1 : t0) : 0.f, cur)) atomicOr(s.status, ST_TRAVERSAL);
+            ref = first0 ? c.x : c.y;
+            return true;
+        }
+        if (h0 || h1) {
+            ref = h0 ? c.x : c.y;
+            return true;
+        }
+        return false;
+    }
+    if (cur == kMiss) {                       // a top-level leaf: its instances
+        const uint32_t first = (ref & 0x7FFFFFFFu) >> 3, cnt = (ref & 7u) + 1u;
+        for (uint32_t q = 1; q < cnt; ++q)
+            if (!rs.push(kLeafBit | ((first + q) << 3), 0.f, kMiss)) atomicOr(s.status, ST_TRAVERSAL);
+        cur = first;                          // the caller takes the ray into it and starts at its root
+        return true;
+    }
+    leaf(ref);
+    return false;
+}
+
+__device__ __forceinline__ Hit trace_closest_group_inst(const DevScene& s, float3 o, float3 d, bool valid,
+                                                        uint32_t G) {
+    const uint32_t lane = threadIdx.x & 31u, gm = group_mask(G, lane);
+    const float3 id = ray_rcp(d);
+    float tbest = __int_as_float(0x7f800000);
+    uint32_t best = kMiss, bprim = kMiss, binst = kMiss;
+    bool busy = valid && (lane & (G - 1u)) == 0u;
+    uint32_t ref = 0u, cur = kMiss;
+    InstRay r;
+    r.o = o;
+    r.d = d;
+    r.root = 0u;
+    r.prim_base = 0u;
+    float3 idr = id;
+    auto enter = [&](uint32_t k) {
+        cur = k;
+        if (k != kMiss) {
+            r = instance_ray(s, k, o, d);
+            idr = ray_rcp(r.d);
+        }
+    };
+    RingStackInst rs;
+    uint32_t steps = 0;
+    while (true) {
+        const float tg = group_min(tbest, G);
+        if (busy) {
+            const uint32_t was = cur;
+            busy = inst_group_step(s, o, id, cur, r, idr, ref, tg, true, rs, [&](uint32_t lr) {
+                const uint32_t first = (lr & 0x7FFFFFFFu) >> 3, cnt = (lr & 7u) + 1u;
+                for (uint32_t q = 0; q < cnt; ++q) {
+                    float t;
+                    uint32_t prim;
+                    if (tri_test(s.tris, first + q, r.o, r.d, t, prim) && t > 0.0f) {
+                        const uint32_t gp = r.prim_base + prim;
+                        if (t < tbest || (t == tbest && gp < bprim)) {
+                            tbest = t;
+                            best = first + q;
+                            bprim = gp;
+                            binst = cur;
+                        }
+                    }
+                }
+            });
+            if (was == kMiss && cur != kMiss) {   // entered an instance: its object-space ray, its root
+                enter(cur);
+                ref = r.root;
+            }
+            if (++steps >= kMaxSteps) {
+                atomicOr(s.status, ST_TRAVERSAL);
+                busy = false;
+                rs.clear();
+            }
+        }
+        const float tc = fminf(tg, tbest);
+        while (!busy && !rs.empty()) {
+            float t;
+            uint32_t k;
+            rs.pop(ref, t, k);
+            busy = t <= tc * 1.0000005f;
+            if (busy && k != cur) enter(k);
+        }
+        uint32_t k = cur;
+        bool moved = false;
+        const bool over = group_share_inst(gm, lane, busy, ref, k, moved, rs, tc);
+        if (moved && k != cur) enter(k);
+        if (__all_sync(0xFFFFFFFFu, over)) break;
+    }
+    Hit h;
+    h.t = group_min(tbest, G);
+    h.prim = group_min(tbest == h.t ? bprim : kMiss, G);
+    const uint32_t own = __ballot_sync(0xFFFFFFFFu, tbest == h.t && bprim == h.prim) & gm;
+    const uint32_t from = own ? (uint32_t)__ffs(own) - 1u : lane;
+    h.tri = __shfl_sync(0xFFFFFFFFu, best, from);
+    h.inst = __shfl_sync(0xFFFFFFFFu, binst, from);
+    return h;
+}
+
+__device__ __forceinline__ bool trace_any_group_inst(const DevScene& s, float3 o, float3 d, float tmax, bool valid,
+                                                     uint32_t G) {
+    const uint32_t lane = threadIdx.x & 31u, gm = group_mask(G, lane);
+    const float3 id = ray_rcp(d);
+    bool busy = valid && (lane & (G - 1u)) == 0u, hit = false;
+    uint32_t ref = 0u, cur = kMiss;
+    InstRay r;
+    r.o = o;
+    r.d = d;
+    r.root = 0u;
+    r.prim_base = 0u;
+    float3 idr = id;
+    auto enter = [&](uint32_t k) {
+        cur = k;
+        if (k != kMiss) {
+            r = instance_ray(s, k, o, d);
+            idr = ray_rcp(r.d);
+        }
+    };
+    RingStackInst rs;
+    uint32_t steps = 0;
+    while (true) {
+        if (busy) {
+            const uint32_t was = cur;
+            busy = inst_group_step(s, o, id, cur, r, idr, ref, tmax, false, rs, [&](uint32_t lr) {
+                const uint32_t first = (lr & 0x7FFFFFFFu) >> 3, cnt = (lr & 7u) + 1u;
+                for (uint32_t q = 0; q < cnt && !hit; ++q) {
+                    float t;
+                    uint32_t prim;
+                    hit = tri_test(s.tris, first + q, r.o, r.d, t, prim) && t > 0.0f && t < tmax;
+                }
+            });
+            if (was == kMiss && cur != kMiss) {
+                enter(cur);
+                ref = r.root;
+            }
+            if (++steps >= kMaxSteps) {
+                atomicOr(s.status, ST_TRAVERSAL);
+                busy = false;
+                rs.clear();
+            }
+        }
+        if (__ballot_sync(0xFFFFFFFFu, hit) & gm) {
+            busy = false;
+            rs.clear();
+        }
+        if (!busy && !rs.empty()) {
+            float t;
+            uint32_t k;
+            rs.pop(ref, t, k);
+            busy = true;
+            if (k != cur) enter(k);
+        }
+        uint32_t k = cur;
+        bool moved = false;
+        const bool over = group_share_inst(gm, lane, busy, ref, k, moved, rs, 0.f);
+        if (moved && k != cur) enter(k);
+        if (__all_sync(0xFFFFFFFFu, over)) break;
+    }
+    return (__ballot_sync(0xFFFFFFFFu, hit) & gm) != 0u;
+}
+
 // The extend and shadow queries.  (A "while-while" variant that voted across the warp with
 // __any_sync(__activemask(), ...) was tried and removed: its result depended on which paths shared a
 // warp -- lanes that are not converged may pass different masks to the vote -- so one path in 33M

@@ -3,7 +3,8 @@ sparse late bounces), groups of G = 2, 4, ..., 32 lanes share each ray, walking 
 side and culling against the group's best distance.  The hit is the smallest (t, original id) over
 the group, which is the one-lane walk's hit, so a render must be bit-identical to the separate stage
 order (one lane per walk in every launch) and to the megakernel: images, per-path radiance, branch
-signatures and ray counts.  The scenes are rendered deep enough that most group sizes run
+signatures and ray counts -- on single-level scenes and on a two-level scene, whose group walks carry
+each deferred subtree's instance.  The scenes are rendered deep enough that most group sizes run
 (`group_walks` counts the walks of each size); the dense soup makes long walks whose deferred
 subtrees move between lanes.  Cooperative paths are tied to brute force too: the default render's
 paths are compared with the FP64 oracle walking every triangle (no BVH)."""
@@ -33,8 +34,11 @@ def _soup():
 
 def _cases():
     sph = scenes.spheres_scene(seed=4, n_spheres=40, level=3, ground_quads=32, extent=20.0, width=96, height=64)
+    inst = scenes.instanced_spheres_scene(seed=2, n_spheres=20, level=2, ground_quads=16, extent=15.0, width=96,
+                                          height=64, n_materials=10)
     return [("soup", _soup(), 4, 14, {}), ("spheres", sph, 8, 16, {}),
-            ("spheres_mis_halton", sph, 2, 12, {"mis": True, "sampler": "halton"})]
+            ("spheres_mis_halton", sph, 2, 12, {"mis": True, "sampler": "halton"}),
+            ("two_level", inst, 4, 12, {})]
 
 
 def test_cooperative_walks_are_bit_identical(torch):
@@ -61,7 +65,7 @@ def test_cooperative_walks_are_bit_identical(torch):
             (sb["extension_rays"], sb["shadow_rays"], sb["active"], sb["shadow_queued"]), name
         mk = g.render(cam, spp, depth, 3, mode="megakernel", rr_start=3, **kw)
         assert torch.equal(mk, a["img"]), name
-    # groups of 2, 4, 8, 16, 32 lanes: most sizes ran over the three renders
+    # groups of 2, 4, 8, 16, 32 lanes: most sizes ran over the four renders
     assert int((sizes > 0).sum()) >= 4, sizes.tolist()
 
 
@@ -82,14 +86,9 @@ def test_cooperative_walks_match_brute_force_oracle(torch):
                         label="cooperative walks vs brute force")
 
 
-def test_group_walks_off_where_the_one_lane_walk_is_kept(torch):
-    """Two-level scenes and the traversal-counting pass keep one lane per walk."""
+def test_group_walks_off_in_the_counting_pass(torch):
+    """The traversal-counting pass keeps one lane per walk (its counts describe that walk)."""
     import paper_2605_27323_gb300 as pt
-    inst = scenes.instanced_spheres_scene(seed=2, n_spheres=20, level=2, ground_quads=16, extent=15.0, width=64,
-                                          height=48, n_materials=10)
-    g = pt.Scene.from_dict(inst)
-    g.render(inst["camera"], 4, 12, 1, mode="wavefront")
-    assert sum(g.stats()["group_walks"]) == 0
     sph = scenes.spheres_scene(seed=4, n_spheres=40, level=3, ground_quads=32, extent=20.0, width=64, height=48)
     g = pt.Scene.from_dict(sph)
     a = g.render(sph["camera"], 4, 12, 1, mode="wavefront", count_traversal=True)
