@@ -368,6 +368,12 @@ pt_status set_device(const pt_scene* sc) {
     return PT_OK;
 }
 
+// The fused wavefront's stage kernels (forward and the adjoint's replay) are launched as programmatic
+// dependents of the kernel before them (sm_90+): each may become resident while its predecessor
+// drains and waits for it on the device (stage_prologue), which hides the launch gap between
+// dependent stages.
+constexpr bool kStagePdl = true;
+
 // The wavefront pipeline over one scene and camera, waves of `cap` paths (a multiple of spp).  With
 // `accum`, each wave's samples continue the per-pixel running sums and img = sum / count.
 pt_status run_wavefront(pt_scene* sc, const pt::DevCamera& cam, const pt::RenderParams& p0, const pt_render_opts& o,
@@ -404,10 +410,13 @@ pt_status run_wavefront(pt_scene* sc, const pt::DevCamera& cam, const pt::Render
             if (fused) {
                 PT_TRY(sc->ev_begin(ST_EXTEND, st, ev));
                 if (b == 0) {     // no shadow rays are pending before the first shading
-                    PT_CUDA(pt::launch_extend(launch_for(sc, pt::K_EXTEND, o.block_size, 256, st, n), ds, w, in, p));
+                    pt::Launch le = launch_for(sc, pt::K_EXTEND, o.block_size, 256, st, n);
+                    le.pdl = kStagePdl;
+                    PT_CUDA(pt::launch_extend(le, ds, w, in, p));
                 } else {
                     pt::Launch lt = launch_for(sc, sc->instanced ? pt::K_TRACE_INST : pt::K_TRACE, o.block_size, 256, st,
                                                2ull * n);
+                    lt.pdl = kStagePdl;
                     PT_CUDA(pt::launch_trace(lt, ds, p, w, in, b));
                 }
                 PT_TRY(sc->ev_end(ev, st));
@@ -418,10 +427,11 @@ pt_status run_wavefront(pt_scene* sc, const pt::DevCamera& cam, const pt::Render
                     PT_TRY(sc->ev_end(ev, st));
                 }
                 pt::Launch ls = launch_for(sc, pt::K_SHADE, o.block_size, 256, st, n);
+                ls.pdl = kStagePdl && !sorted_f;
                 PT_TRY(sc->ev_begin(ST_SHADE, st, ev));
                 PT_CUDA(pt::launch_shade(ls, ds, p, w, in, b, sorted_f));
                 PT_TRY(sc->ev_end(ev, st));
-                PT_CUDA(pt::launch_prepare_fused(st, w, b));
+                PT_CUDA(pt::launch_prepare_fused(st, w, b, kStagePdl));
                 sc->launches += 3 + (sorted_f ? 3 : 0);
                 continue;
             }
@@ -461,9 +471,11 @@ pt_status run_wavefront(pt_scene* sc, const pt::DevCamera& cam, const pt::Render
         if (accum)
             PT_CUDA(pt::launch_accumulate(simple_launch(sc, st, n / p.spp), reinterpret_cast<const float*>(w.L), 4,
                                           w0 / p.spp, n / p.spp, p.spp, accum, count, img));
-        else
-            PT_CUDA(pt::launch_reduce(simple_launch(sc, st, n / p.spp), reinterpret_cast<const float*>(w.L), 4,
-                                      w0 / p.spp, n / p.spp, p.spp, img));
+        else {
+            pt::Launch lr = simple_launch(sc, st, n / p.spp);
+            lr.pdl = kStagePdl;
+            PT_CUDA(pt::launch_reduce(lr, reinterpret_cast<const float*>(w.L), 4, w0 / p.spp, n / p.spp, p.spp, img));
+        }
         if (path_L) PT_CUDA(pt::launch_copy_L(simple_launch(sc, st, n), w.L, n, path_L + 3 * w0));
         PT_TRY(sc->ev_end(ev, st));
         sc->launches += path_L ? 2 : 1;
@@ -1399,18 +1411,24 @@ pt_status pt_render_backward(pt_scene* sc, const pt_camera* cam, uint32_t spp, u
             for (uint32_t b = 0; b < max_depth; ++b) {
                 const int in = (int)(b & 1u);
                 PT_TRY(sc->ev_begin(ST_EXTEND, st, e2));
-                if (fused && b > 0)
-                    PT_CUDA(pt::launch_trace_adj(launch_for(sc, sc->instanced ? pt::K_TRACE_INST : pt::K_TRACE,
-                                                            o.block_size, 256, st, 2ull * n),
-                                                 ds, pw, w, ab, in, b));
-                else
-                    PT_CUDA(pt::launch_extend(launch_for(sc, pt::K_EXTEND, o.block_size, 256, st, n), ds, w, in, pw));
+                if (fused && b > 0) {
+                    pt::Launch lt = launch_for(sc, sc->instanced ? pt::K_TRACE_INST : pt::K_TRACE, o.block_size, 256,
+                                               st, 2ull * n);
+                    lt.pdl = kStagePdl;
+                    PT_CUDA(pt::launch_trace_adj(lt, ds, pw, w, ab, in, b));
+                } else {
+                    pt::Launch le = launch_for(sc, pt::K_EXTEND, o.block_size, 256, st, n);
+                    le.pdl = fused && kStagePdl;
+                    PT_CUDA(pt::launch_extend(le, ds, w, in, pw));
+                }
                 PT_TRY(sc->ev_end(e2, st));
                 PT_TRY(sc->ev_begin(ST_SHADE, st, e2));
-                PT_CUDA(pt::launch_shade_adj(launch_for(sc, pt::K_SHADE_ADJ, o.block_size, 256, st, n), ds, pw, w, ab, in, b));
+                pt::Launch ls = launch_for(sc, pt::K_SHADE_ADJ, o.block_size, 256, st, n);
+                ls.pdl = fused && kStagePdl;
+                PT_CUDA(pt::launch_shade_adj(ls, ds, pw, w, ab, in, b));
                 PT_TRY(sc->ev_end(e2, st));
                 if (fused) {
-                    PT_CUDA(pt::launch_prepare_fused(st, w, b));
+                    PT_CUDA(pt::launch_prepare_fused(st, w, b, kStagePdl));
                     continue;
                 }
                 PT_TRY(sc->ev_begin(ST_SHADOW, st, e2));
@@ -1419,8 +1437,9 @@ pt_status pt_render_backward(pt_scene* sc, const pt_camera* cam, uint32_t spp, u
                 PT_CUDA(pt::launch_prepare(st, w, b));
             }
             PT_TRY(sc->ev_begin(ST_REDUCE, st, e2));
-            PT_CUDA(pt::launch_adjoint_reverse(simple_launch(sc, st, n), ds, pw, w, ab, n, grad, d_grad_albedo,
-                                               d_grad_emission));
+            pt::Launch lr = simple_launch(sc, st, n);
+            lr.pdl = fused && kStagePdl;
+            PT_CUDA(pt::launch_adjoint_reverse(lr, ds, pw, w, ab, n, grad, d_grad_albedo, d_grad_emission));
             PT_TRY(sc->ev_end(e2, st));
             sc->launches += 2 + (fused ? 3 : 4) * max_depth;
         }

@@ -13,6 +13,37 @@ namespace pt {
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
+// Programmatic dependent launch (sm_90+): a stage kernel that the host launches with the
+// programmatic-serialization attribute may begin while the previous kernel of its stream drains.
+// It first waits until that kernel has finished and its writes are visible (a no-op when launched
+// normally), then lets the next kernel of the stream begin its own launch, whose blocks become
+// resident as this kernel's blocks exit and wait in the same way.
+__device__ __forceinline__ void stage_prologue() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch through cudaLaunchKernelEx with the programmatic-serialization attribute when l.pdl is set
+// (the kernel must begin with stage_prologue()), else as an ordinary launch.
+template <class... KArgs, class... Args>
+cudaError_t launch_k(const Launch& l, size_t smem, void (*k)(KArgs...), Args... args) {
+    if (!l.pdl) {
+        k<<<l.grid, l.block, smem, l.st>>>(args...);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)l.grid);
+    cfg.blockDim = dim3((unsigned)l.block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = l.st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // Warp-aggregated append (stream compaction, Sec. 3.1): every lane of the warp calls it; lanes with
 // `want` receive consecutive slots from a single atomicAdd issued by the lowest such lane.
 __device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool want) {

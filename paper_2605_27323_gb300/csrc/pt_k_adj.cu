@@ -10,6 +10,7 @@ namespace pt {
 // radiance (the same shade_vertex decisions, so the replay follows the forward paths exactly).
 template <bool INST>
 __global__ void __launch_bounds__(256, 3) k_shade_adj(SingleSrc src, WfBuffers w, AdjBuffers a, int in, uint32_t b) {
+    stage_prologue();
     const uint32_t n = min(w.counts[0], w.capacity);
     const uint64_t base = src.base();
     const int out = in ^ 1;
@@ -270,6 +271,7 @@ __global__ void __launch_bounds__(256) k_adjoint_reverse(DevScene s, RenderParam
                                                          uint32_t n, const float* __restrict__ grad,
                                                          float* __restrict__ g_alb, float* __restrict__ g_em,
                                                          int smem) {
+    stage_prologue();
     extern __shared__ float acc[];
     if (smem)
         for (uint32_t k = threadIdx.x; k < 4 * s.n_mats; k += blockDim.x) acc[k] = 0.f;
@@ -358,9 +360,8 @@ cudaError_t launch_adjoint(const Launch& l, const DevScene& s, const DevCamera& 
 cudaError_t launch_shade_adj(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w,
                              const AdjBuffers& a, int in, uint32_t bounce) {
     SingleSrc src{s, DevCamera{}, p};
-    if (s.tlas) k_shade_adj<true><<<l.grid, l.block, 0, l.st>>>(src, w, a, in, bounce);
-    else k_shade_adj<false><<<l.grid, l.block, 0, l.st>>>(src, w, a, in, bounce);
-    return cudaGetLastError();
+    if (s.tlas) return launch_k(l, 0, k_shade_adj<true>, src, w, a, in, bounce);
+    return launch_k(l, 0, k_shade_adj<false>, src, w, a, in, bounce);
 }
 
 cudaError_t launch_shadow_adj(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w,
@@ -376,8 +377,7 @@ cudaError_t launch_adjoint_reverse(const Launch& l, const DevScene& s, const Ren
                                    float* g_emission) {
     size_t smem_bytes = sizeof(float) * 4 * (size_t)s.n_mats;
     int smem = smem_bytes <= 32 * 1024 ? 1 : 0;
-    k_adjoint_reverse<<<l.grid, l.block, smem ? smem_bytes : 0, l.st>>>(s, p, w, a, n, grad, g_albedo, g_emission, smem);
-    return cudaGetLastError();
+    return launch_k(l, smem ? smem_bytes : 0, k_adjoint_reverse, s, p, w, a, n, grad, g_albedo, g_emission, smem);
 }
 
 // Resident blocks per SM of this unit's kernels (0: not one of them).

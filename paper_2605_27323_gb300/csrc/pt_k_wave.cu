@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(256) k_raygen(Src src, uint64_t base, uint32_t
 // CNT: count the walks' node visits and triangle tests into the scene's traversal counters.
 template <class Src, bool INST, int SK = 0, bool CNT = false>
 __global__ void __launch_bounds__(256, INST ? 4 : 6) k_extend(Src src, WfBuffers w, int in) {
+    stage_prologue();
     const uint32_t n = min(w.counts[0], w.capacity);
     if (n == 0u) return;       // an emptied queue: no claims (the same for every thread)
     const uint64_t base = src.base();
@@ -236,6 +237,7 @@ __device__ __forceinline__ void put_ray(const Src& src, const WfBuffers& w, int 
 // warp appends its survivors with one atomic per queue (warp-aggregated).
 template <class Src, bool SIG, bool INST>
 __global__ void __launch_bounds__(256, 3) k_shade(Src src, WfBuffers w, int in, uint32_t b, bool sorted) {
+    stage_prologue();
     const uint32_t n = min(w.counts[0], w.capacity);
     const uint64_t base = src.base();
     const int out = in ^ 1;
@@ -358,6 +360,7 @@ __device__ __noinline__ void trace_groups(const Src& src, const WfBuffers& w, co
 // (flag 2 of record 3 of bounce b - 1) instead of adding a contribution.
 template <class Src, bool SIG, bool INST, bool CNT = false, bool ADJ = false>
 __global__ void __launch_bounds__(256, INST ? 4 : 6) k_trace(Src src, WfBuffers w, AdjBuffers a, int in, uint32_t b) {
+    stage_prologue();
     const uint32_t n_ext = min(w.counts[0], w.capacity), n_shd = min(w.counts[6], w.capacity);
     if (n_ext + n_shd == 0u) return;       // the same for every thread
     const uint64_t base = src.base();
@@ -420,6 +423,7 @@ __global__ void __launch_bounds__(256, INST ? 4 : 6) k_trace(Src src, WfBuffers 
 // Prepare after shading in the fused pipeline: record this bounce's counts, promote the next count,
 // and hand the shadow rays shading just cast to the next trace launch (counts[2] -> counts[6]).
 __global__ void k_prepare_fused(WfBuffers w, uint32_t b) {
+    stage_prologue();
     w.hist[b] += w.counts[0];
     w.hist[64 + b] += w.counts[2];
     w.counts[0] = w.counts[1];
@@ -444,6 +448,7 @@ __global__ void k_prepare(WfBuffers w, uint32_t b) {
 // ================================================================== accumulation
 __global__ void __launch_bounds__(256) k_reduce(const float* __restrict__ L, uint32_t stride_f, uint64_t pixel_begin,
                                                 uint64_t n_pixels, uint32_t spp, float* __restrict__ img) {
+    stage_prologue();
     const float inv = 1.0f / (float)spp;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t px = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; px < n_pixels; px += stride) {
@@ -557,6 +562,7 @@ __global__ void k_scale_batch(BatchTables t, const unsigned long long* __restric
 
 
 // ------------------------------------------------------------------ launchers
+
 cudaError_t launch_raygen(const Launch& l, const DevCamera& c, const RenderParams& p, uint32_t n, const WfBuffers& w) {
     SingleSrc src{DevScene{}, c, p};
     k_raygen<SingleSrc><<<l.grid, l.block, 0, l.st>>>(src, p.path_begin, n, w, nullptr);
@@ -565,12 +571,11 @@ cudaError_t launch_raygen(const Launch& l, const DevCamera& c, const RenderParam
 
 cudaError_t launch_extend(const Launch& l, const DevScene& s, const WfBuffers& w, int in, const RenderParams& p) {
     SingleSrc src{s, DevCamera{}, p};
-    if (s.tlas) k_extend<SingleSrc, true><<<l.grid, l.block, 0, l.st>>>(src, w, in);
-    else if (p.count_trav) k_extend<SingleSrc, false, 0, true><<<l.grid, l.block, 0, l.st>>>(src, w, in);
-    else if (p.short_stack)
-        k_extend<SingleSrc, false, kShortStack><<<l.grid, l.block, stack_smem_bytes(kShortStack, l.block), l.st>>>(src, w, in);
-    else k_extend<SingleSrc, false><<<l.grid, l.block, 0, l.st>>>(src, w, in);
-    return cudaGetLastError();
+    if (s.tlas) return launch_k(l, 0, k_extend<SingleSrc, true>, src, w, in);
+    if (p.count_trav) return launch_k(l, 0, k_extend<SingleSrc, false, 0, true>, src, w, in);
+    if (p.short_stack)
+        return launch_k(l, stack_smem_bytes(kShortStack, l.block), k_extend<SingleSrc, false, kShortStack>, src, w, in);
+    return launch_k(l, 0, k_extend<SingleSrc, false>, src, w, in);
 }
 
 cudaError_t launch_sort(const Launch& l, const DevScene& s, const WfBuffers& w, int in, uint32_t mode, uint32_t n_keys,
@@ -589,13 +594,11 @@ cudaError_t launch_shade(const Launch& l, const DevScene& s, const RenderParams&
                          uint32_t bounce, bool sorted) {
     SingleSrc src{s, DevCamera{}, p};
     if (s.tlas) {
-        if (w.sig) k_shade<SingleSrc, true, true><<<l.grid, l.block, 0, l.st>>>(src, w, in, bounce, sorted);
-        else k_shade<SingleSrc, false, true><<<l.grid, l.block, 0, l.st>>>(src, w, in, bounce, sorted);
-    } else {
-        if (w.sig) k_shade<SingleSrc, true, false><<<l.grid, l.block, 0, l.st>>>(src, w, in, bounce, sorted);
-        else k_shade<SingleSrc, false, false><<<l.grid, l.block, 0, l.st>>>(src, w, in, bounce, sorted);
+        if (w.sig) return launch_k(l, 0, k_shade<SingleSrc, true, true>, src, w, in, bounce, sorted);
+        return launch_k(l, 0, k_shade<SingleSrc, false, true>, src, w, in, bounce, sorted);
     }
-    return cudaGetLastError();
+    if (w.sig) return launch_k(l, 0, k_shade<SingleSrc, true, false>, src, w, in, bounce, sorted);
+    return launch_k(l, 0, k_shade<SingleSrc, false, false>, src, w, in, bounce, sorted);
 }
 
 cudaError_t launch_shadow(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w,
@@ -670,28 +673,28 @@ cudaError_t launch_trace(const Launch& l, const DevScene& s, const RenderParams&
     SingleSrc src{s, DevCamera{}, p};
     const AdjBuffers a{};
     if (s.tlas) {
-        if (w.sig) k_trace<SingleSrc, true, true><<<l.grid, l.block, 0, l.st>>>(src, w, a, in, bounce);
-        else k_trace<SingleSrc, false, true><<<l.grid, l.block, 0, l.st>>>(src, w, a, in, bounce);
-    } else if (p.count_trav && !w.sig) {
-        k_trace<SingleSrc, false, false, true><<<l.grid, l.block, 0, l.st>>>(src, w, a, in, bounce);
-    } else {
-        if (w.sig) k_trace<SingleSrc, true, false><<<l.grid, l.block, 0, l.st>>>(src, w, a, in, bounce);
-        else k_trace<SingleSrc, false, false><<<l.grid, l.block, 0, l.st>>>(src, w, a, in, bounce);
+        if (w.sig) return launch_k(l, 0, k_trace<SingleSrc, true, true>, src, w, a, in, bounce);
+        return launch_k(l, 0, k_trace<SingleSrc, false, true>, src, w, a, in, bounce);
     }
-    return cudaGetLastError();
+    if (p.count_trav && !w.sig) return launch_k(l, 0, k_trace<SingleSrc, false, false, true>, src, w, a, in, bounce);
+    if (w.sig) return launch_k(l, 0, k_trace<SingleSrc, true, false>, src, w, a, in, bounce);
+    return launch_k(l, 0, k_trace<SingleSrc, false, false>, src, w, a, in, bounce);
 }
 
 cudaError_t launch_trace_adj(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w,
                              const AdjBuffers& a, int in, uint32_t bounce) {
     SingleSrc src{s, DevCamera{}, p};
-    if (s.tlas) k_trace<SingleSrc, false, true, false, true><<<l.grid, l.block, 0, l.st>>>(src, w, a, in, bounce);
-    else k_trace<SingleSrc, false, false, false, true><<<l.grid, l.block, 0, l.st>>>(src, w, a, in, bounce);
-    return cudaGetLastError();
+    if (s.tlas) return launch_k(l, 0, k_trace<SingleSrc, false, true, false, true>, src, w, a, in, bounce);
+    return launch_k(l, 0, k_trace<SingleSrc, false, false, false, true>, src, w, a, in, bounce);
 }
 
-cudaError_t launch_prepare_fused(cudaStream_t st, const WfBuffers& w, uint32_t bounce) {
-    k_prepare_fused<<<1, 1, 0, st>>>(w, bounce);
-    return cudaGetLastError();
+cudaError_t launch_prepare_fused(cudaStream_t st, const WfBuffers& w, uint32_t bounce, bool pdl) {
+    Launch l;
+    l.grid = 1;
+    l.block = 1;
+    l.st = st;
+    l.pdl = pdl;
+    return launch_k(l, 0, k_prepare_fused, w, bounce);
 }
 
 cudaError_t launch_prepare(cudaStream_t st, const WfBuffers& w, uint32_t bounce) {
@@ -701,8 +704,7 @@ cudaError_t launch_prepare(cudaStream_t st, const WfBuffers& w, uint32_t bounce)
 
 cudaError_t launch_reduce(const Launch& l, const float* L, uint32_t stride, uint64_t pixel_begin, uint64_t n_pixels,
                           uint32_t spp, float* img) {
-    k_reduce<<<l.grid, l.block, 0, l.st>>>(L, stride, pixel_begin, n_pixels, spp, img);
-    return cudaGetLastError();
+    return launch_k(l, 0, k_reduce, L, stride, pixel_begin, n_pixels, spp, img);
 }
 
 cudaError_t launch_accumulate(const Launch& l, const float* L, uint32_t stride, uint64_t pixel_begin, uint64_t n_pixels,

@@ -12,6 +12,7 @@ struct Launch {
     int grid;
     int block;
     cudaStream_t st;
+    bool pdl = false;   // programmatic dependent launch (the wavefront stage kernels; see stage_prologue)
 };
 
 // Megakernel (Sec. 2.2): one thread per path, whole path in one kernel.  Writes per-path radiance
@@ -44,7 +45,7 @@ cudaError_t launch_prepare(cudaStream_t st, const WfBuffers& w, uint32_t bounce)
 // (the shadow rays pending in counts[6]), and the prepare step that hands shading's new shadow rays on.
 cudaError_t launch_trace(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w, int in,
                          uint32_t bounce);
-cudaError_t launch_prepare_fused(cudaStream_t st, const WfBuffers& w, uint32_t bounce);
+cudaError_t launch_prepare_fused(cudaStream_t st, const WfBuffers& w, uint32_t bounce, bool pdl = false);
 // The adjoint replay's fused launch: its shadow walks mark the records of bounce - 1.
 cudaError_t launch_trace_adj(const Launch& l, const DevScene& s, const RenderParams& p, const WfBuffers& w,
                              const AdjBuffers& a, int in, uint32_t bounce);

@@ -177,8 +177,11 @@ extern "C" pt_status pt_render_wavefront_static(pt_scene* scene, const pt_camera
     for (uint64_t w0 = 0; w0 < n_paths; w0 += cap) {
         const uint32_t n = (uint32_t)std::min<uint64_t>(cap, n_paths - w0);
         p.path_begin = w0;
-        const pt::Launch le = persistent(per_extend, n), ls = persistent(per_shade, n);
-        const pt::Launch lw = persistent(per_shadow, n), lt = persistent(per_trace, 2ull * n);
+        pt::Launch le = persistent(per_extend, n), ls = persistent(per_shade, n);
+        const pt::Launch lw = persistent(per_shadow, n);
+        pt::Launch lt = persistent(per_trace, 2ull * n), lr = plain(n / spp);
+        // fused: the stage kernels are programmatic dependents of the kernel before them, as in pt_render
+        le.pdl = ls.pdl = lt.pdl = lr.pdl = fused && n_keys == 0;
         if ((e = pt::launch_raygen(plain(n), dc, p, n, w)) != cudaSuccess) return cuda_fail(e, "raygen");
         for (uint32_t b = 0; b < max_depth; ++b) {
             const int in = (int)(b & 1u);
@@ -191,13 +194,13 @@ extern "C" pt_status pt_render_wavefront_static(pt_scene* scene, const pt_camera
                 return cuda_fail(e, "sort");
             if ((e = pt::launch_shade(ls, ds, p, w, in, b, n_keys > 0)) != cudaSuccess) return cuda_fail(e, "shade");
             if (fused) {
-                if ((e = pt::launch_prepare_fused(st, w, b)) != cudaSuccess) return cuda_fail(e, "prepare");
+                if ((e = pt::launch_prepare_fused(st, w, b, le.pdl)) != cudaSuccess) return cuda_fail(e, "prepare");
                 continue;
             }
             if ((e = pt::launch_shadow(lw, ds, p, w, b)) != cudaSuccess) return cuda_fail(e, "shadow");
             if ((e = pt::launch_prepare(st, w, b)) != cudaSuccess) return cuda_fail(e, "prepare");
         }
-        if ((e = pt::launch_reduce(plain(n / spp), reinterpret_cast<const float*>(w.L), 4, w0 / spp, n / spp, spp,
+        if ((e = pt::launch_reduce(lr, reinterpret_cast<const float*>(w.L), 4, w0 / spp, n / spp, spp,
                                    d_out_rgb)) != cudaSuccess)
             return cuda_fail(e, "reduce");
     }
