@@ -634,20 +634,27 @@ cudaError_t launch_bounce_batch(const Launch& le, const Launch& ls, const Launch
                                 uint32_t sort_mode, uint32_t n_keys, bool fused) {
     TableSrc src{t, p};
     const int in = (int)(b & 1u);
+    // fused and unsorted: the stage kernels are programmatic dependents of the kernel before them
+    // (programmatic edges of the captured bounce graph; bounce 0's first launch opens the graph)
+    const bool pdl = fused && n_keys == 0;
+    Launch lt = lw, lsh = ls;
+    lt.pdl = pdl;
+    lsh.pdl = pdl;
+    cudaError_t e;
     if (fused && b > 0)   // lw: the fused launch (this bounce's extension and the last bounce's shadow walks)
-        k_trace<TableSrc, false, false><<<lw.grid, lw.block, 0, lw.st>>>(src, w, AdjBuffers{}, in, b);
+        e = launch_k(lt, 0, k_trace<TableSrc, false, false>, src, w, AdjBuffers{}, in, b);
     else
-        k_extend<TableSrc, false><<<le.grid, le.block, 0, le.st>>>(src, w, in);
+        e = launch_k(le, 0, k_extend<TableSrc, false>, src, w, in);
+    if (e != cudaSuccess) return e;
     if (n_keys) {
-        cudaError_t e = cudaMemsetAsync(w.bucket, 0, sizeof(uint32_t) * n_keys, lk.st);
-        if (e != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(w.bucket, 0, sizeof(uint32_t) * n_keys, lk.st)) != cudaSuccess) return e;
         k_sort_keys<TableSrc, false><<<lk.grid, lk.block, sizeof(uint32_t) * n_keys, lk.st>>>(src, w, in, sort_mode, n_keys);
         k_sort_scan<<<1, 1024, 0, lk.st>>>(w, n_keys);
         k_sort_scatter<<<lk.grid, lk.block, 0, lk.st>>>(w);
     }
-    k_shade<TableSrc, false, false><<<ls.grid, ls.block, 0, ls.st>>>(src, w, in, b, n_keys > 0);
+    if ((e = launch_k(lsh, 0, k_shade<TableSrc, false, false>, src, w, in, b, n_keys > 0)) != cudaSuccess) return e;
     if (fused) {
-        k_prepare_fused<<<1, 1, 0, le.st>>>(w, b);
+        return launch_prepare_fused(le.st, w, b, pdl);
     } else {
         k_shadow<TableSrc, false, false><<<lw.grid, lw.block, 0, lw.st>>>(src, w, b);
         k_prepare<<<1, 1, 0, le.st>>>(w, b);
