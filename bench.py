@@ -504,8 +504,8 @@ def run_gpu(args):
                                          (cm["tris_closest"] + cm["tris_any"]) / n_paths, sms, sm_mhz,
                                          load_traffic("megakernel"))}
     roofline["traversal_per_ray"] = trav
-    # the batched (64 scenes) and inverse-rendering workloads, compact: the benchmark spec's >= 1.5x and
-    # <= 3x targets are measured in every default run
+    # the batched (64 scenes) and inverse-rendering workloads, compact: the batched-over-separate
+    # ratio and the backward/forward ratio are measured in every default run
     extra = {}
     if rank == 0 and world == 1 and not args.no_extras:
         extra["inverse_rendering"] = measure_diff(3, 3)
