@@ -189,15 +189,6 @@ struct Builder {
     }
 };
 
-void put_box(float* slot_x, float* slot_y, float* slot_z, const Box& b) {
-    slot_x[0] = b.lo[0];
-    slot_x[1] = b.hi[0];
-    slot_y[0] = b.lo[1];
-    slot_y[1] = b.hi[1];
-    slot_z[0] = b.lo[2];
-    slot_z[1] = b.hi[2];
-}
-
 float f32_bits(uint32_t u) {
     float f;
     std::memcpy(&f, &u, 4);
@@ -250,8 +241,12 @@ bool build_bvh(const float* verts, const uint32_t* tris, uint32_t n_tris, BvhOut
         if (bn[i].count == 0) gpu_id[i] = n_int++;
     auto emit = [&](const Box& b0, uint32_t r0, const Box& b1, uint32_t r1) {
         float f[16];
-        put_box(&f[0], &f[2], &f[8], b0);
-        put_box(&f[4], &f[6], &f[10], b1);
+        for (int k = 0; k < 3; ++k) {      // row k: (c0.lo, c1.lo, c0.hi, c1.hi) of axis k
+            f[4 * k] = b0.lo[k];
+            f[4 * k + 1] = b1.lo[k];
+            f[4 * k + 2] = b0.hi[k];
+            f[4 * k + 3] = b1.hi[k];
+        }
         f[12] = f32_bits(r0);
         f[13] = f32_bits(r1);
         f[14] = 0.f;

@@ -4,10 +4,11 @@
 // BVH -- one over all triangles, or (two-level scenes, the paper's TLAS/BLAS structure of Sec. 2.3)
 // one over instances whose leaves lead into per-mesh BVHs.
 //
-// Node layout (64 bytes, one 128-bit load per row, both children's boxes in the parent):
-//   n0 = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
-//   n1 = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
-//   n2 = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
+// Node layout (64 bytes, one 128-bit load per row, both children's boxes in the parent; each axis
+// row pairs the two children so that one packed FP32 operation serves both):
+//   n0 = (c0.lo.x, c1.lo.x, c0.hi.x, c1.hi.x)
+//   n1 = (c0.lo.y, c1.lo.y, c0.hi.y, c1.hi.y)
+//   n2 = (c0.lo.z, c1.lo.z, c0.hi.z, c1.hi.z)
 //   n3 = (ref0, ref1, -, -)     ref: internal node index, or 0x80000000 | first << 3 | (count - 1)
 // Triangle record (48 bytes): (v0.xyz, prim id) (e1 = v1 - v0, material) (e2 = v2 - v0, is_light).
 //
@@ -39,16 +40,45 @@ __device__ __forceinline__ float3 ray_rcp(float3 d) {
     return f3(__frcp_rn(x), __frcp_rn(y), __frcp_rn(z));   // correctly rounded, as 1.0f / x
 }
 
-// Slab test of one box against [0, tmax]; returns whether it is hit and the entry distance.
-__device__ __forceinline__ bool box_test(float lox, float hix, float loy, float hiy, float loz, float hiz, float3 o,
-                                         float3 id, float tmax, float& tn) {
-    float x0 = (lox - o.x) * id.x, x1 = (hix - o.x) * id.x;
-    float y0 = (loy - o.y) * id.y, y1 = (hiy - o.y) * id.y;
-    float z0 = (loz - o.z) * id.z, z1 = (hiz - o.z) * id.z;
-    float a = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.0f));
-    float b = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tmax));
-    tn = a;
-    return a <= b * 1.0000005f;
+
+
+// Slab test of a node's two child boxes against [0, tmax]: whether each is hit and its entry distance.
+// Rows nx, ny, nz hold (c0.lo, c1.lo, c0.hi, c1.hi) of one axis, so the plane distances
+// (plane - o) * (1/d) of both children come from packed FP32 pairs (sub/mul.rn.f32x2: each half
+// rounded exactly as the scalar operation); the entry is the largest near-plane distance (at least 0),
+// the exit the smallest far-plane distance (at most tmax), and a box counts as hit when entry <= exit
+// widened by a few ulps, so that rounding cannot cull a true hit.
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpk2(unsigned long long v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long slab2(float lo0, float lo1, float o, float id) {
+    unsigned long long d, r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(lo0, lo1)), "l"(pk2(o, o)));
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(d), "l"(pk2(id, id)));
+    return r;
+}
+__device__ __forceinline__ void box_test2(float4 nx, float4 ny, float4 nz, float3 o, float3 id, float tmax,
+                                          float& t0, float& t1, bool& h0, bool& h1) {
+    float xa0, xa1, xb0, xb1, ya0, ya1, yb0, yb1, za0, za1, zb0, zb1;
+    unpk2(slab2(nx.x, nx.y, o.x, id.x), xa0, xa1);
+    unpk2(slab2(nx.z, nx.w, o.x, id.x), xb0, xb1);
+    unpk2(slab2(ny.x, ny.y, o.y, id.y), ya0, ya1);
+    unpk2(slab2(ny.z, ny.w, o.y, id.y), yb0, yb1);
+    unpk2(slab2(nz.x, nz.y, o.z, id.z), za0, za1);
+    unpk2(slab2(nz.z, nz.w, o.z, id.z), zb0, zb1);
+    const float a0 = fmaxf(fmaxf(fminf(xa0, xb0), fminf(ya0, yb0)), fmaxf(fminf(za0, zb0), 0.0f));
+    const float e0 = fminf(fminf(fmaxf(xa0, xb0), fmaxf(ya0, yb0)), fminf(fmaxf(za0, zb0), tmax));
+    const float a1 = fmaxf(fmaxf(fminf(xa1, xb1), fminf(ya1, yb1)), fmaxf(fminf(za1, zb1), 0.0f));
+    const float e1 = fminf(fminf(fmaxf(xa1, xb1), fmaxf(ya1, yb1)), fminf(fmaxf(za1, zb1), tmax));
+    t0 = a0;
+    t1 = a1;
+    h0 = a0 <= e0 * 1.0000005f;
+    h1 = a1 <= e1 * 1.0000005f;
 }
 
 // Moller-Trumbore test of one triangle record; t in (0, tmax) by the caller's rule.
@@ -189,8 +219,8 @@ __device__ __forceinline__ Hit trace_closest_plain(const DevScene& s, float3 o, 
             load_node(s.nodes, ref, n0, n1, n2, r);
             cnt.node();
             float t0, t1;
-            bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tbest, t0);
-            bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tbest, t1);
+            bool h0, h1;
+            box_test2(n0, n1, n2, o, id, tbest, t0, t1, h0, h1);
             if (h0 && h1) {
                 bool first0 = t0 <= t1;
                 if (!stk.push(first0 ? r.y : r.x, first0 ? t1 : t0)) atomicOr(s.status, ST_TRAVERSAL);
@@ -335,8 +365,8 @@ __device__ __forceinline__ Hit trace_closest_group(const DevScene& s, float3 o, 
                 uint2 r;
                 load_node(s.nodes, ref, n0, n1, n2, r);
                 float t0, t1;
-                const bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tg, t0);
-                const bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tg, t1);
+                bool h0, h1;
+                box_test2(n0, n1, n2, o, id, tg, t0, t1, h0, h1);
                 if (h0 && h1) {
                     const bool first0 = t0 <= t1;
                     if (!rs.push(first0 ? r.y : r.x, first0 ? t1 : t0)) atomicOr(s.status, ST_TRAVERSAL);
@@ -400,8 +430,8 @@ __device__ __forceinline__ bool trace_any_group(const DevScene& s, float3 o, flo
                 uint2 r;
                 load_node(s.nodes, ref, n0, n1, n2, r);
                 float t0, t1;
-                const bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tmax, t0);
-                const bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tmax, t1);
+                bool h0, h1;
+                box_test2(n0, n1, n2, o, id, tmax, t0, t1, h0, h1);
                 if (h0 && h1) {
                     const bool first0 = t0 <= t1;
                     if (!rs.push(first0 ? r.y : r.x, 0.f)) atomicOr(s.status, ST_TRAVERSAL);
@@ -454,8 +484,8 @@ __device__ __forceinline__ bool trace_any_plain(const DevScene& s, float3 o, flo
             load_node(s.nodes, ref, n0, n1, n2, r);
             cnt.node();
             float t0, t1;
-            bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tmax, t0);
-            bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tmax, t1);
+            bool h0, h1;
+            box_test2(n0, n1, n2, o, id, tmax, t0, t1, h0, h1);
             if (h0 && h1) {       // nearer child first: an occluder near the origin ends the walk sooner
                 const bool first0 = t0 <= t1;
                 if (!stk.push(first0 ? r.y : r.x, 0.f)) atomicOr(s.status, ST_TRAVERSAL);
@@ -520,8 +550,8 @@ __device__ __forceinline__ void blas_closest(const DevScene& s, const InstRay& r
             uint2 c;
             load_node(s.nodes, ref, n0, n1, n2, c);
             float t0, t1;
-            bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, r.o, id, tbest, t0);
-            bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, r.o, id, tbest, t1);
+            bool h0, h1;
+            box_test2(n0, n1, n2, r.o, id, tbest, t0, t1, h0, h1);
             if (h0 && h1) {
                 bool first0 = t0 <= t1;
                 if (sp < kStack) {
@@ -582,8 +612,8 @@ __device__ __forceinline__ bool blas_any(const DevScene& s, const InstRay& r, fl
             uint2 c;
             load_node(s.nodes, ref, n0, n1, n2, c);
             float t0, t1;
-            bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, r.o, id, tmax, t0);
-            bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, r.o, id, tmax, t1);
+            bool h0, h1;
+            box_test2(n0, n1, n2, r.o, id, tmax, t0, t1, h0, h1);
             if (h0 && h1) {       // nearer child first, as in the single-level walk
                 const bool first0 = t0 <= t1;
                 if (sp < kStack) stack_ref[sp++] = first0 ? c.y : c.x;
@@ -627,8 +657,8 @@ __device__ __forceinline__ Hit trace_closest_inst(const DevScene& s, float3 o, f
             uint2 c;
             load_node(s.tlas, ref, n0, n1, n2, c);
             float t0, t1;
-            bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tbest, t0);
-            bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tbest, t1);
+            bool h0, h1;
+            box_test2(n0, n1, n2, o, id, tbest, t0, t1, h0, h1);
             if (h0 && h1) {
                 bool first0 = t0 <= t1;
                 if (sp < kStack) {
@@ -687,8 +717,8 @@ __device__ __forceinline__ bool trace_any_inst(const DevScene& s, float3 o, floa
             uint2 c;
             load_node(s.tlas, ref, n0, n1, n2, c);
             float t0, t1;
-            bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, o, id, tmax, t0);
-            bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, o, id, tmax, t1);
+            bool h0, h1;
+            box_test2(n0, n1, n2, o, id, tmax, t0, t1, h0, h1);
             if (h0 && h1) {       // nearer child first, as in the single-level walk
                 const bool first0 = t0 <= t1;
                 if (sp < kStack) stack_ref[sp++] = first0 ? c.y : c.x;
@@ -794,8 +824,8 @@ __device__ __forceinline__ bool inst_group_step(const DevScene& s, float3 o, flo
         load_node(top ? s.tlas : s.nodes, ref, n0, n1, n2, c);
         const float3 ro = top ? o : r.o, ri = top ? id : idr;
         float t0, t1;
-        const bool h0 = box_test(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, ro, ri, tcull, t0);
-        const bool h1 = box_test(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, ro, ri, tcull, t1);
+        bool h0, h1;
+        box_test2(n0, n1, n2, ro, ri, tcull, t0, t1, h0, h1);
         if (h0 && h1) {
             const bool first0 = t0 <= t1;
             if (!rs.push(first0 ? c.y : c.x, push_t ? (first0 ? t1 : t0) : 0.f, cur)) atomicOr(s.status, ST_TRAVERSAL);
