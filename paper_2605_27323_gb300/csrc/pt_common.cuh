@@ -114,7 +114,7 @@ __device__ __forceinline__ float3 mk_path(const DevScene& s, const DevCamera& c,
     float prev_pdf = 0.f;
     for (uint32_t b = 0; b < p.max_depth; ++b) {
         ++n_ext;
-        Hit h = trace_closest<INST>(s, o, d);                  // step 2
+        Hit h = trace_closest<INST, 0, !INST>(s, o, d);        // step 2
         if (h.tri == kMiss) {
             L = add_rn(L, mul_rn(tp, env));
             rec.ev(b, 0, kMiss, __int_as_float(0x7f800000), tp.x);
@@ -128,7 +128,7 @@ __device__ __forceinline__ float3 mk_path(const DevScene& s, const DevCamera& c,
             uint32_t vis = 0;
             if (V.cast) {
                 ++n_shd;
-                vis = trace_any<INST>(s, V.s_o, V.s_d, V.s_tmax) ? 0u : 1u;
+                vis = trace_any<INST, 0, !INST>(s, V.s_o, V.s_d, V.s_tmax) ? 0u : 1u;
                 if (vis) L = add_rn(L, V.contrib);
             }
             rec.ev(b, 1, (V.light_j << 2) | ((uint32_t)V.cast << 1) | vis, V.nee_cx, V.nee_cl);
@@ -156,7 +156,7 @@ __device__ __forceinline__ bool mk_bounce(const DevScene& s, const RenderParams&
                                           float& prev_pdf, float3& L, uint32_t& sg, uint32_t& n_ext,
                                           uint32_t& n_shd, C& cc, C& ca) {
     ++n_ext;
-    Hit h = trace_closest<INST, SK>(s, o, d, cc);
+    Hit h = trace_closest<INST, SK, !INST>(s, o, d, cc);
     if (h.tri == kMiss) {
         L = add_rn(L, mul_rn(tp, env));
         if (SIG) sg ^= sig_event(b, 0, kMiss);
@@ -170,7 +170,7 @@ __device__ __forceinline__ bool mk_bounce(const DevScene& s, const RenderParams&
         uint32_t vis = 0;
         if (V.cast) {
             ++n_shd;
-            vis = trace_any<INST, SK>(s, V.s_o, V.s_d, V.s_tmax, ca) ? 0u : 1u;
+            vis = trace_any<INST, SK, !INST>(s, V.s_o, V.s_d, V.s_tmax, ca) ? 0u : 1u;
             if (vis) L = add_rn(L, V.contrib);
         }
         if (SIG) sg ^= sig_event(b, 1, (V.light_j << 2) | ((uint32_t)V.cast << 1) | vis);

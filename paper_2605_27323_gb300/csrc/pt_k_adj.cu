@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(128, 8) k_adjoint(DevScene s, DevCamera c, Ren
         if (!active) continue;
         bool end = true, end_miss = false;
         if (b < p.max_depth && b < (uint32_t)MAXD) {
-            const Hit h = trace_closest<INST>(s, o, d);
+            const Hit h = trace_closest<INST, 0, !INST>(s, o, d);
             if (h.tri == kMiss) {
                 end_miss = true;
             } else {
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(128, 8) k_adjoint(DevScene s, DevCamera c, Ren
                 r.dwa = r.nee_g;
                 r.Lj = 0.f;
                 if (!V.last) {
-                    if (V.nee && V.cast && !trace_any<INST>(s, V.s_o, V.s_d, V.s_tmax)) {
+                    if (V.nee && V.cast && !trace_any<INST, 0, !INST>(s, V.s_o, V.s_d, V.s_tmax)) {
                         r.flags |= 2u;
                         r.nee_g = V.nee_g;
                         r.nee_dfa = V.nee_dfa;

@@ -42,12 +42,28 @@ __device__ __forceinline__ float3 ray_rcp(float3 d) {
 
 
 
+// Slab test of one box against [0, tmax]: whether it is hit and its entry distance (the largest
+// near-plane distance, at least 0); hit when the entry is at most the exit (the smallest far-plane
+// distance, at most tmax) widened by a few ulps, so that rounding cannot cull a true hit.
+__device__ __forceinline__ bool box_test(float lox, float hix, float loy, float hiy, float loz, float hiz, float3 o,
+                                         float3 id, float tmax, float& tn) {
+    float x0 = (lox - o.x) * id.x, x1 = (hix - o.x) * id.x;
+    float y0 = (loy - o.y) * id.y, y1 = (hiy - o.y) * id.y;
+    float z0 = (loz - o.z) * id.z, z1 = (hiz - o.z) * id.z;
+    float a = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.0f));
+    float b = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tmax));
+    tn = a;
+    return a <= b * 1.0000005f;
+}
+
 // Slab test of a node's two child boxes against [0, tmax]: whether each is hit and its entry distance.
 // Rows nx, ny, nz hold (c0.lo, c1.lo, c0.hi, c1.hi) of one axis, so the plane distances
 // (plane - o) * (1/d) of both children come from packed FP32 pairs (sub/mul.rn.f32x2: each half
 // rounded exactly as the scalar operation); the entry is the largest near-plane distance (at least 0),
 // the exit the smallest far-plane distance (at most tmax), and a box counts as hit when entry <= exit
-// widened by a few ulps, so that rounding cannot cull a true hit.
+// widened by a few ulps, so that rounding cannot cull a true hit.  PK = false computes the same values
+// with box_test, one child at a time (for the register-bound one-thread-per-path kernels' two-level
+// walks, where the packed pairs cost spills).
 __device__ __forceinline__ unsigned long long pk2(float a, float b) {
     unsigned long long r;
     asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
@@ -62,8 +78,14 @@ __device__ __forceinline__ unsigned long long slab2(float lo0, float lo1, float 
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(d), "l"(pk2(id, id)));
     return r;
 }
+template <bool PK = true>
 __device__ __forceinline__ void box_test2(float4 nx, float4 ny, float4 nz, float3 o, float3 id, float tmax,
                                           float& t0, float& t1, bool& h0, bool& h1) {
+    if constexpr (!PK) {
+        h0 = box_test(nx.x, nx.z, ny.x, ny.z, nz.x, nz.z, o, id, tmax, t0);
+        h1 = box_test(nx.y, nx.w, ny.y, ny.w, nz.y, nz.w, o, id, tmax, t1);
+        return;
+    }
     float xa0, xa1, xb0, xb1, ya0, ya1, yb0, yb1, za0, za1, zb0, zb1;
     unpk2(slab2(nx.x, nx.y, o.x, id.x), xa0, xa1);
     unpk2(slab2(nx.z, nx.w, o.x, id.x), xb0, xb1);
@@ -537,6 +559,7 @@ __device__ __forceinline__ InstRay instance_ray(const DevScene& s, uint32_t k, f
 }
 
 // Closest hit inside one mesh (object-space ray), updating the running best over instances.
+template <bool PK = true>
 __device__ __forceinline__ void blas_closest(const DevScene& s, const InstRay& r, uint32_t k, float& tbest,
                                              uint32_t& best, uint32_t& bprim, uint32_t& binst, uint32_t& steps) {
     const float3 id = ray_rcp(r.d);
@@ -551,7 +574,7 @@ __device__ __forceinline__ void blas_closest(const DevScene& s, const InstRay& r
             load_node(s.nodes, ref, n0, n1, n2, c);
             float t0, t1;
             bool h0, h1;
-            box_test2(n0, n1, n2, r.o, id, tbest, t0, t1, h0, h1);
+            box_test2<PK>(n0, n1, n2, r.o, id, tbest, t0, t1, h0, h1);
             if (h0 && h1) {
                 bool first0 = t0 <= t1;
                 if (sp < kStack) {
@@ -601,6 +624,7 @@ __device__ __forceinline__ void blas_closest(const DevScene& s, const InstRay& r
     }
 }
 
+template <bool PK = true>
 __device__ __forceinline__ bool blas_any(const DevScene& s, const InstRay& r, float tmax, uint32_t& steps) {
     const float3 id = ray_rcp(r.d);
     uint32_t stack_ref[kStack];
@@ -613,7 +637,7 @@ __device__ __forceinline__ bool blas_any(const DevScene& s, const InstRay& r, fl
             load_node(s.nodes, ref, n0, n1, n2, c);
             float t0, t1;
             bool h0, h1;
-            box_test2(n0, n1, n2, r.o, id, tmax, t0, t1, h0, h1);
+            box_test2<PK>(n0, n1, n2, r.o, id, tmax, t0, t1, h0, h1);
             if (h0 && h1) {       // nearer child first, as in the single-level walk
                 const bool first0 = t0 <= t1;
                 if (sp < kStack) stack_ref[sp++] = first0 ? c.y : c.x;
@@ -642,6 +666,7 @@ __device__ __forceinline__ bool blas_any(const DevScene& s, const InstRay& r, fl
     }
 }
 
+template <bool PK = true>
 __device__ __forceinline__ Hit trace_closest_inst(const DevScene& s, float3 o, float3 d) {
     const float3 id = ray_rcp(d);
     float tbest = __int_as_float(0x7f800000);
@@ -658,7 +683,7 @@ __device__ __forceinline__ Hit trace_closest_inst(const DevScene& s, float3 o, f
             load_node(s.tlas, ref, n0, n1, n2, c);
             float t0, t1;
             bool h0, h1;
-            box_test2(n0, n1, n2, o, id, tbest, t0, t1, h0, h1);
+            box_test2<PK>(n0, n1, n2, o, id, tbest, t0, t1, h0, h1);
             if (h0 && h1) {
                 bool first0 = t0 <= t1;
                 if (sp < kStack) {
@@ -678,7 +703,7 @@ __device__ __forceinline__ Hit trace_closest_inst(const DevScene& s, float3 o, f
             uint32_t first = (ref & 0x7FFFFFFFu) >> 3, cnt = (ref & 7u) + 1u;
             for (uint32_t q = 0; q < cnt; ++q) {
                 const InstRay r = instance_ray(s, first + q, o, d);
-                blas_closest(s, r, first + q, tbest, best, bprim, binst, steps);
+                blas_closest<PK>(s, r, first + q, tbest, best, bprim, binst, steps);
             }
         }
         if (steps >= kMaxSteps) {
@@ -705,6 +730,7 @@ __device__ __forceinline__ Hit trace_closest_inst(const DevScene& s, float3 o, f
     return h;
 }
 
+template <bool PK = true>
 __device__ __forceinline__ bool trace_any_inst(const DevScene& s, float3 o, float3 d, float tmax) {
     const float3 id = ray_rcp(d);
     uint32_t stack_ref[kStack];
@@ -718,7 +744,7 @@ __device__ __forceinline__ bool trace_any_inst(const DevScene& s, float3 o, floa
             load_node(s.tlas, ref, n0, n1, n2, c);
             float t0, t1;
             bool h0, h1;
-            box_test2(n0, n1, n2, o, id, tmax, t0, t1, h0, h1);
+            box_test2<PK>(n0, n1, n2, o, id, tmax, t0, t1, h0, h1);
             if (h0 && h1) {       // nearer child first, as in the single-level walk
                 const bool first0 = t0 <= t1;
                 if (sp < kStack) stack_ref[sp++] = first0 ? c.y : c.x;
@@ -732,7 +758,7 @@ __device__ __forceinline__ bool trace_any_inst(const DevScene& s, float3 o, floa
         } else {
             uint32_t first = (ref & 0x7FFFFFFFu) >> 3, cnt = (ref & 7u) + 1u;
             for (uint32_t q = 0; q < cnt; ++q)
-                if (blas_any(s, instance_ray(s, first + q, o, d), tmax, steps)) return true;
+                if (blas_any<PK>(s, instance_ray(s, first + q, o, d), tmax, steps)) return true;
         }
         if (steps >= kMaxSteps) {
             atomicOr(s.status, ST_TRAVERSAL);
@@ -997,34 +1023,34 @@ __device__ __forceinline__ bool trace_any_group_inst(const DevScene& s, float3 o
 // SK stack entries in shared memory (the kernel supplies stack_smem_bytes(SK, blockDim.x) of dynamic
 // shared memory); the two-level walks keep the local stack.
 // `cnt` (TravCount) counts the single-level walks' node visits and triangle tests; the two-level
-// walks are not counted.
-template <bool INST = false, int SK = 0, class C = NoCount>
+// walks are not counted.  PK = false: the two-level walks test boxes one at a time (box_test2).
+template <bool INST = false, int SK = 0, bool PK = true, class C = NoCount>
 __device__ __forceinline__ Hit trace_closest(const DevScene& s, float3 o, float3 d, C& cnt) {
     if constexpr (INST) {
-        return trace_closest_inst(s, o, d);
+        return trace_closest_inst<PK>(s, o, d);
     } else {
         typename StackOf<SK, true>::type stk;
         return trace_closest_plain(s, o, d, stk, cnt);
     }
 }
-template <bool INST = false, int SK = 0>
+template <bool INST = false, int SK = 0, bool PK = true>
 __device__ __forceinline__ Hit trace_closest(const DevScene& s, float3 o, float3 d) {
     NoCount c;
-    return trace_closest<INST, SK>(s, o, d, c);
+    return trace_closest<INST, SK, PK>(s, o, d, c);
 }
-template <bool INST = false, int SK = 0, class C = NoCount>
+template <bool INST = false, int SK = 0, bool PK = true, class C = NoCount>
 __device__ __forceinline__ bool trace_any(const DevScene& s, float3 o, float3 d, float tmax, C& cnt) {
     if constexpr (INST) {
-        return trace_any_inst(s, o, d, tmax);
+        return trace_any_inst<PK>(s, o, d, tmax);
     } else {
         typename StackOf<SK, false>::type stk;
         return trace_any_plain(s, o, d, tmax, stk, cnt);
     }
 }
-template <bool INST = false, int SK = 0>
+template <bool INST = false, int SK = 0, bool PK = true>
 __device__ __forceinline__ bool trace_any(const DevScene& s, float3 o, float3 d, float tmax) {
     NoCount c;
-    return trace_any<INST, SK>(s, o, d, tmax, c);
+    return trace_any<INST, SK, PK>(s, o, d, tmax, c);
 }
 
 }  // namespace pt
