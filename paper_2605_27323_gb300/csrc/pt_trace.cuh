@@ -136,7 +136,8 @@ __device__ __forceinline__ void load_node(const float4* __restrict__ nodes, uint
 
 // ------------------------------------------------------------------ traversal stacks
 // The stack of deferred subtrees (far child and its entry distance) of the single-level walks.
-// LocalStack: kStack entries per thread in local memory (cached by L1).  ShortStack<K>: the top K
+// LocalStack: kStack entries per thread in local memory (cached by L1), a closest-hit entry's reference
+// and distance in one 8-byte word (one 64-bit access per push and per pop).  ShortStack<K>: the top K
 // entries per thread in shared memory -- per-warp short stacks, 32 lanes side by side in each slot
 // row, so a warp's accesses of one slot hit 32 distinct banks -- and the entries below them in
 // local memory: a push onto a full shared slice first moves the slice's bottom entry to local
@@ -147,20 +148,23 @@ extern __shared__ uint32_t g_stack_smem[];
 
 template <bool T>
 struct LocalStack {
-    uint32_t ref[kStack];
-    float t[T ? kStack : 1];
+    // closest-hit walks: (ref, t) in one 8-byte entry; any-hit walks: references only
+    uint2 e[T ? kStack : 1];
+    uint32_t ref[T ? 1 : kStack];
     int sp = 0;
     __device__ __forceinline__ bool empty() const { return sp == 0; }
     __device__ __forceinline__ bool push(uint32_t r, float tt) {
         if (sp >= kStack) return false;
-        ref[sp] = r;
-        if (T) t[sp] = tt;
+        if (T) e[sp] = make_uint2(r, __float_as_uint(tt));
+        else ref[sp] = r;
         ++sp;
         return true;
     }
-    // pop the top entry: its distance (closest-hit walks); its reference follows with top_ref()
-    __device__ __forceinline__ float pop_t() { return t[--sp]; }
-    __device__ __forceinline__ uint32_t top_ref() const { return ref[sp]; }
+    __device__ __forceinline__ void pop(uint32_t& r, float& tt) {
+        const uint2 v = e[--sp];
+        r = v.x;
+        tt = __uint_as_float(v.y);
+    }
     __device__ __forceinline__ uint32_t pop_ref() { return ref[--sp]; }
 };
 
@@ -192,6 +196,10 @@ struct ShortStack {
         return sp >= base ? __uint_as_float(g_stack_smem[tslot(sp)]) : lt[sp];
     }
     __device__ __forceinline__ uint32_t top_ref() const { return sp >= base ? g_stack_smem[slot(sp)] : lref[sp]; }
+    __device__ __forceinline__ void pop(uint32_t& r, float& tt) {
+        tt = pop_t();
+        r = top_ref();
+    }
     __device__ __forceinline__ uint32_t pop_ref() {
         --sp;
         return sp >= base ? g_stack_smem[slot(sp)] : lref[sp];
@@ -272,8 +280,11 @@ __device__ __forceinline__ Hit trace_closest_plain(const DevScene& s, float3 o, 
         }
         bool found = false;        // pop the next subtree whose entry is not beyond the best hit
         while (!stk.empty()) {
-            if (stk.pop_t() <= tbest * 1.0000005f) {
-                ref = stk.top_ref();
+            uint32_t r;
+            float t;
+            stk.pop(r, t);
+            if (t <= tbest * 1.0000005f) {
+                ref = r;
                 found = true;
                 break;
             }
